@@ -1,0 +1,205 @@
+/*
+ * ngravs — GB300-native multi-species TreePM force (C ABI).
+ *
+ * The problem (Croker, "ngravs: Distinct gravitational interactions in
+ * GADGET-2", arXiv:1502.07442):
+ *   D <= 6 gravitating species; a particle of passive species i feels a
+ *   source of active species j through its own force law f_ij (Sec. 2,
+ *   Eq. (map)), here Newtonian or Newtonian + Yukawa (Eq. (yukawa), C = 1).
+ *   The force is split TreePM-style (Sec. 2.4.1): a short-range part
+ *   evaluated by a Barnes-Hut walk whose nodes carry one monopole per species
+ *   (Sec. 2.2), plus a long-range part from a particle-mesh step that deposits
+ *   active masses per species and applies D x D Fourier kernels (Sec. 2.4).
+ *
+ * Conventions shared by every call:
+ *  - Memory: every particle array is a DEVICE pointer owned by the caller,
+ *    laid out structure-of-arrays: positions double[3][n] (x block, y block,
+ *    z block), velocities float[3][n], accelerations float[3][n], species
+ *    uint8[n] with values < D, masses float[n]. The library owns its own
+ *    scratch (tree, tables, meshes), allocated with cudaMalloc on the device
+ *    that is current when ng_create is called, and freed by ng_destroy.
+ *  - Order: outputs are in the caller's particle order; the sorted order is
+ *    exposed only through perm_out.
+ *  - Streams: work is enqueued on the stream given to ng_create (or
+ *    ng_set_stream) and is asynchronous unless a call says otherwise.
+ *  - Errors: every call returns NG_OK (0) or a negative NG_E* code; no C++
+ *    exception crosses the ABI. ng_last_error gives a message for the last
+ *    failure on that context. A context is not thread-safe.
+ *  - Coordinates: periodic box [0, L)^3; inputs outside are wrapped.
+ */
+#ifndef NGRAVS_H
+#define NGRAVS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define NG_MAX_SPECIES 6
+
+enum {
+  NG_OK = 0,
+  NG_EINVAL = -1,    /* bad argument: D, n, box, law table, pointer */
+  NG_ENOMEM = -2,    /* device allocation failed or a capacity was exceeded */
+  NG_ECUDA = -3,     /* a CUDA or cuFFT call failed */
+  NG_ETIMEOUT = -4,  /* a bounded device wait ran out */
+  NG_EBUSY = -5,     /* serving admission refused (byte budget) */
+  NG_ESTATE = -6     /* call out of order (e.g. force before build) */
+};
+
+enum { NG_NEWTON = 0, NG_YUKAWA = 1 };
+
+/*
+ * Parameters of one simulation (Sec. 2, Eq. (map); Sec. 2.4.1).
+ *  G[i][j]        coupling for passive species i and active species j.
+ *  law[i][j]      NG_NEWTON, or NG_YUKAWA for Eq. (yukawa) with C = 1:
+ *                 phi_ij(r) = -G_ij M (1 + yuk_a[i][j] exp(-r / yuk_l[i][j])) / r.
+ *  eps            Plummer softening length (> 0): the radial law is
+ *                 evaluated at sqrt(r^2 + eps^2).
+ *  box            periodic box side L.
+ *  pm_mesh        PM mesh points per side N_m (power of two, 0 = no PM).
+ *  asmth          split scale in mesh cells: r_s = asmth * L / N_m; when
+ *                 pm_mesh == 0, r_s = asmth * L (short-range law still split).
+ *  rcut_over_rs   short-range cut-off r_cut = rcut_over_rs * r_s (< L/2);
+ *                 a term contributes iff the unsoftened r < r_cut.
+ *  theta          opening angle: a node of side l is used as D monopoles when
+ *                 l < theta * d (d from the target group to the node's centre
+ *                 of mass); theta = 0 opens every node (direct summation).
+ *  leaf_size      maximum bodies per tree leaf (1..64, 0 = 8).
+ *  group_size     particles per walk group (32 or 64, 0 = 32).
+ *  table_size     short-range table entries per law (0 = automatic).
+ */
+typedef struct {
+  int32_t D;
+  int32_t pm_mesh;
+  int32_t leaf_size;
+  int32_t group_size;
+  int32_t table_size;
+  int32_t reserved0;
+  double G[NG_MAX_SPECIES][NG_MAX_SPECIES];
+  int32_t law[NG_MAX_SPECIES][NG_MAX_SPECIES];
+  double yuk_a[NG_MAX_SPECIES][NG_MAX_SPECIES];
+  double yuk_l[NG_MAX_SPECIES][NG_MAX_SPECIES];
+  double eps;
+  double box;
+  double asmth;
+  double rcut_over_rs;
+  double theta;
+} ng_params;
+
+typedef struct ng_ctx ng_ctx;
+
+/*
+ * Create a context for one simulation on the current CUDA device.
+ * stream: a cudaStream_t passed as void* (NULL = legacy default stream).
+ * Validates p (NG_EINVAL with a message on failure) and builds the
+ * short-range tables on the host in double precision. *out is owned by the
+ * caller and released with ng_destroy.
+ */
+int ng_create(ng_ctx** out, const ng_params* p, void* stream);
+int ng_destroy(ng_ctx* ctx);
+int ng_set_stream(ng_ctx* ctx, void* stream);
+
+/*
+ * Sort and tree build (Sec. 2.4 sort by Peano-Hilbert-type key and type,
+ * Sec. 2.2 tree with per-species monopoles and N_perp counts).
+ * Wraps positions into the box, forms 63-bit keys (20-bit Morton per axis,
+ * x most significant, species in the low 3 bits), stable-sorts them, builds
+ * the canonical octree (a cell is a leaf iff it holds <= leaf_size bodies or
+ * is at level 20; children in octant order; nodes numbered breadth-first) and
+ * reduces per-node per-species mass, centre of mass (double precision) and
+ * body count. n >= 1; pos/type/mass are device arrays of n entries and are
+ * only read. keys_out (uint64[n], sorted keys) and perm_out (uint32[n];
+ * perm_out[k] = caller index of the k-th sorted body) are optional device
+ * outputs. The tree stays valid until the next ng_build_tree on ctx.
+ * Synchronises the stream once to size the tree (grows capacity as needed).
+ */
+int ng_build_tree(ng_ctx* ctx, int64_t n, const double* pos, const uint8_t* type,
+                  const float* mass, uint64_t* keys_out, uint32_t* perm_out);
+
+/*
+ * Short-range tree force (Sec. 2.2 walk, Sec. 2.4.1 short-range law) on the
+ * bodies of the last build: acc_out (device float[3][n], caller order) is
+ * overwritten with the short-range acceleration. interactions_out (host,
+ * optional) receives the number of particle-term evaluations the group walk
+ * executed (synchronises the stream when non-NULL).
+ */
+int ng_tree_force(ng_ctx* ctx, float* acc_out, uint64_t* interactions_out);
+
+/*
+ * Per-particle walk interaction count (Sec. 2.2, geometric criterion with
+ * angle theta per target particle, double precision decisions): the number
+ * of (accepted node, species with mass > 0) terms plus bodies of opened
+ * leaves, the target excluded, summed over all bodies. This is the
+ * algorithm's unit of work for throughput reports; it evaluates no force.
+ * counts_out (device int64[n], caller order) is optional; *total_out (host)
+ * receives the sum. Synchronises the stream.
+ */
+int ng_count_interactions(ng_ctx* ctx, int64_t* counts_out, uint64_t* total_out);
+
+/*
+ * Long-range PM acceleration (Sec. 2.4): CIC deposit of active masses per
+ * species, D forward FFTs (cuFFT), the D x D Gaussian-filtered Green's
+ * functions (Yukawa part scaled by exp(-mu^2 r_s^2), Sec. 3.2; CIC window
+ * divided out twice; k = 0 removed), D inverse FFTs, 4-point
+ * finite-difference gradient and CIC interpolation to each passive particle.
+ * Uses the bodies of the last build; acc_out (device float[3][n], caller
+ * order) is overwritten. NG_ESTATE when pm_mesh == 0.
+ */
+int ng_pm_force(ng_ctx* ctx, float* acc_out);
+
+/*
+ * Kick-drift-kick leapfrog (Sec. 2.1.1) at fixed dt for nsteps steps:
+ *   v += a dt/2 (float); x += v dt (double); wrap; a = a_short + a_long; v += a dt/2.
+ * pos (double[3][n]) and vel (float[3][n]) are updated in place; acc
+ * (float[3][n]) must hold the acceleration at pos when acc_valid != 0,
+ * otherwise it is computed first; on return it holds the acceleration at the
+ * final positions. Each step after the first is replayed from a captured
+ * CUDA graph. Synchronises the stream at the end to report device errors.
+ */
+int ng_step(ng_ctx* ctx, int64_t n, double* pos, float* vel, const uint8_t* type,
+            const float* mass, float* acc, int acc_valid, int nsteps, double dt);
+
+/*
+ * Export the canonical tree of the last build (for inspection and tests).
+ * Returns the node count in *nnodes. Each array is optional (NULL skips it)
+ * and is a HOST array of at least *nnodes (times D where stated) entries:
+ * level int32, prefix uint64 (3*level Morton bits), first/count int64 (body
+ * range in sorted order), nchild int32 (0 = leaf), child_first int64,
+ * cnt uint32[node][D] (N_perp per species), mass double[node][D],
+ * com double[node][D][3]. Synchronises the stream.
+ */
+int ng_tree_export(ng_ctx* ctx, int64_t* nnodes, int32_t* level, uint64_t* prefix,
+                   int64_t* first, int64_t* count, int32_t* nchild, int64_t* child_first,
+                   uint32_t* cnt, double* mass, double* com);
+
+/*
+ * Type-major order of the last build (Sec. 2.4: bodies grouped by type, each
+ * type in key order): type_offsets (host int64[D+1]) and, optionally,
+ * order_out (device uint32[n]; order_out[k] = caller index of the k-th body in
+ * type-major order). Synchronises the stream.
+ */
+int ng_type_order(ng_ctx* ctx, int64_t* type_offsets, uint32_t* order_out);
+
+/*
+ * Number of CUDA kernels this context has launched so far (host-side count,
+ * library kernels only; cuFFT's own kernels are not included). A captured
+ * step counts once when it is captured; each replay of the step graph adds
+ * the kernels of one step. Used to report launches per timed region.
+ */
+int ng_launch_count(const ng_ctx* ctx, uint64_t* out);
+
+/* Message describing the last error on ctx (never NULL); with ctx == NULL,
+ * the message of the last failed ng_create on the calling thread. */
+const char* ng_last_error(const ng_ctx* ctx);
+
+/* Library version string. */
+const char* ng_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NGRAVS_H */

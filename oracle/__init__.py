@@ -81,6 +81,7 @@ def lib():
         for f in ("or_direct", "or_direct_cells"):
             getattr(L, f).argtypes = [P, i64, vp, vp, vp, i64, vp, vp]
         L.or_tree_walk.argtypes = [P, i64, vp, vp, vp, i64, vp, vp, vp]
+        L.or_tree_walk_timed.argtypes = [P, i64, vp, vp, vp, i64, vp, vp, vp, vp]
         L.or_fft1d.argtypes = [i64, vp, vp, ctypes.c_int]
         L.or_fft3d.argtypes = [i64, vp, vp, ctypes.c_int]
         L.or_pm.argtypes = [P, i64, vp, vp, vp, vp]
@@ -203,6 +204,21 @@ def tree_walk(p: OrParams, pos, typ, mass, tgt=None):
     lib().or_tree_walk(ctypes.byref(p), n, _p(pos), _p(typ), _p(mass), t.size, _p(t),
                        _p(acc), _p(cnt))
     return acc, cnt
+
+
+def tree_walk_timed(p: OrParams, pos, typ, mass, tgt):
+    """Per-particle walk of the targets; returns (acc, counts, build_s, walk_s)."""
+    pos = _soa(pos)
+    typ = np.ascontiguousarray(typ, np.uint8)
+    mass = np.ascontiguousarray(mass, np.float32)
+    n = pos.shape[1]
+    t = _targets(n, tgt)
+    acc = np.zeros((3, t.size))
+    cnt = np.zeros(t.size, np.int64)
+    times = np.zeros(2)
+    lib().or_tree_walk_timed(ctypes.byref(p), n, _p(pos), _p(typ), _p(mass), t.size, _p(t),
+                             _p(acc), _p(cnt), _p(times))
+    return acc, cnt, float(times[0]), float(times[1])
 
 
 def fft1d(x, sign=-1):

@@ -420,9 +420,30 @@ void or_direct_cells(const or_params* p, int64_t n, const double* pos,
  * number of evaluated terms: one per (accepted node, species with M > 0) and
  * one per body of an opened leaf (the target itself excluded).
  */
+static double wall_seconds() {
+#ifdef _OPENMP
+  return omp_get_wtime();
+#else
+  return 0.0;
+#endif
+}
+
+void or_tree_walk_timed(const or_params* p, int64_t n, const double* pos,
+                        const uint8_t* type, const float* mass, int64_t ntgt,
+                        const int64_t* tgt, double* acc, int64_t* counts, double* times);
+
 void or_tree_walk(const or_params* p, int64_t n, const double* pos,
                   const uint8_t* type, const float* mass, int64_t ntgt,
                   const int64_t* tgt, double* acc, int64_t* counts) {
+  or_tree_walk_timed(p, n, pos, type, mass, ntgt, tgt, acc, counts, nullptr);
+}
+
+/* The same walk; times (optional, 2 doubles) receives the wall seconds of the
+ * sort + tree build and of the walk itself. */
+void or_tree_walk_timed(const or_params* p, int64_t n, const double* pos,
+                        const uint8_t* type, const float* mass, int64_t ntgt,
+                        const int64_t* tgt, double* acc, int64_t* counts, double* times) {
+  const double t0 = wall_seconds();
   std::vector<uint64_t> skeys;
   std::vector<uint32_t> perm;
   std::vector<double> spos;
@@ -433,6 +454,7 @@ void or_tree_walk(const or_params* p, int64_t n, const double* pos,
   build_tree(p, n, skeys.data(), spos.data(), smass.data(), stype.data(), T);
   std::vector<int64_t> rank(n);
   for (int64_t k = 0; k < n; ++k) rank[perm[k]] = k;
+  const double t1 = wall_seconds();
   const double L = p->box;
   const int D = p->D;
   const double rc2 = p->rcut * p->rcut;
@@ -495,6 +517,10 @@ void or_tree_walk(const or_params* p, int64_t n, const double* pos,
     }
     for (int c = 0; c < 3; ++c) acc[c * ntgt + q] = a[c];
     if (counts) counts[q] = cntq;
+  }
+  if (times) {
+    times[0] = t1 - t0;
+    times[1] = wall_seconds() - t1;
   }
 }
 

@@ -1,0 +1,244 @@
+"""Thin ctypes binding of ``libngravs.so`` (declared in ``include/ngravs.h``).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library. Functions keep the C names. Particle arrays are torch CUDA tensors
+laid out as the header states (positions float64 [3, n], accelerations and
+velocities float32 [3, n], species uint8 [n], masses float32 [n]); their
+device pointers are handed to the library as is. The stream is torch's
+current stream unless one is given.
+
+There is no fallback: if the library was not built (``__graft_entry__.build()``
+or ``python -m paper_1502_07442_gb300.build``), loading raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+NG_MAX_SPECIES = 6
+NG_OK, NG_EINVAL, NG_ENOMEM, NG_ECUDA, NG_ETIMEOUT, NG_EBUSY, NG_ESTATE = 0, -1, -2, -3, -4, -5, -6
+NG_NEWTON, NG_YUKAWA = 0, 1
+
+_M6d = (ctypes.c_double * NG_MAX_SPECIES) * NG_MAX_SPECIES
+_M6i = (ctypes.c_int32 * NG_MAX_SPECIES) * NG_MAX_SPECIES
+
+
+class NgParams(ctypes.Structure):
+    """Mirror of ``ng_params``."""
+
+    _fields_ = [
+        ("D", ctypes.c_int32), ("pm_mesh", ctypes.c_int32), ("leaf_size", ctypes.c_int32),
+        ("group_size", ctypes.c_int32), ("table_size", ctypes.c_int32),
+        ("reserved0", ctypes.c_int32),
+        ("G", _M6d), ("law", _M6i), ("yuk_a", _M6d), ("yuk_l", _M6d),
+        ("eps", ctypes.c_double), ("box", ctypes.c_double), ("asmth", ctypes.c_double),
+        ("rcut_over_rs", ctypes.c_double), ("theta", ctypes.c_double),
+    ]
+
+
+class NgError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"ngravs error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def lib():
+    """Load the library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        path = _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError(f"libngravs.so is not built ({path}); run __graft_entry__.build()")
+        L = ctypes.CDLL(path)
+        vp, i64, i32, d = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
+        L.ng_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(NgParams), vp]
+        L.ng_destroy.argtypes = [vp]
+        L.ng_set_stream.argtypes = [vp, vp]
+        L.ng_build_tree.argtypes = [vp, i64, vp, vp, vp, vp, vp]
+        L.ng_tree_force.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_uint64)]
+        L.ng_count_interactions.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_uint64)]
+        L.ng_pm_force.argtypes = [vp, vp]
+        L.ng_step.argtypes = [vp, i64, vp, vp, vp, vp, vp, i32, i32, d]
+        L.ng_tree_export.argtypes = [vp, ctypes.POINTER(i64)] + [vp] * 9
+        L.ng_type_order.argtypes = [vp, vp, vp]
+        L.ng_launch_count.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64)]
+        L.ng_last_error.argtypes = [vp]
+        L.ng_last_error.restype = ctypes.c_char_p
+        L.ng_version.restype = ctypes.c_char_p
+        for f in ("ng_create", "ng_destroy", "ng_set_stream", "ng_build_tree", "ng_tree_force",
+                  "ng_count_interactions", "ng_pm_force", "ng_step", "ng_tree_export",
+                  "ng_type_order", "ng_launch_count"):
+            getattr(L, f).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def exported_symbols():
+    """Names the header declares (used by the ABI test)."""
+    return ["ng_create", "ng_destroy", "ng_set_stream", "ng_build_tree", "ng_tree_force",
+            "ng_count_interactions", "ng_pm_force", "ng_step", "ng_tree_export", "ng_type_order",
+            "ng_launch_count", "ng_last_error", "ng_version"]
+
+
+def _check(ctx, code):
+    if code != NG_OK:
+        msg = lib().ng_last_error(ctx)
+        raise NgError(code, msg.decode() if msg else "")
+
+
+def make_params(D, G, *, eps, box=1.0, pm_mesh=0, asmth=1.25, rcut_over_rs=4.5, theta=0.5,
+                leaf_size=8, group_size=32, table_size=0, law=None, yuk_a=None, yuk_l=None):
+    p = NgParams()
+    p.D, p.pm_mesh, p.leaf_size, p.group_size, p.table_size = (int(D), int(pm_mesh), int(leaf_size),
+                                                               int(group_size), int(table_size))
+    p.eps, p.box, p.asmth, p.rcut_over_rs, p.theta = (float(eps), float(box), float(asmth),
+                                                      float(rcut_over_rs), float(theta))
+    G = np.asarray(G, np.float64)
+    law = np.zeros((D, D), np.int32) if law is None else np.asarray(law, np.int32)
+    ya = np.zeros((D, D)) if yuk_a is None else np.asarray(yuk_a, np.float64)
+    yl = np.ones((D, D)) if yuk_l is None else np.asarray(yuk_l, np.float64)
+    for i in range(D):
+        for j in range(D):
+            p.G[i][j] = G[i, j]
+            p.law[i][j] = int(law[i, j])
+            p.yuk_a[i][j] = ya[i, j]
+            p.yuk_l[i][j] = yl[i, j]
+    return p
+
+
+def params_from_workload(w: dict, **over) -> NgParams:
+    """ng_params for a parameter dict from ``inputs.workload``."""
+    q = dict(w)
+    q.update(over)
+    mesh = int(q["pm_mesh"])
+    box = float(q["box"])
+    rs = float(q["rs"])
+    asmth = rs * mesh / box if mesh > 0 else rs / box
+    return make_params(q["D"], q["G"], eps=q["eps"], box=box, pm_mesh=mesh, asmth=asmth,
+                       rcut_over_rs=float(q["rcut"]) / rs, theta=q["theta"],
+                       leaf_size=q.get("leaf_size", 8), law=q["law"], yuk_a=q["ya"], yuk_l=q["yl"],
+                       table_size=q.get("table_size", 0))
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def ng_create(params: NgParams, stream=None):
+    ctx = ctypes.c_void_p()
+    _check(None, lib().ng_create(ctypes.byref(ctx), ctypes.byref(params), _stream(stream)))
+    return ctx
+
+
+def ng_destroy(ctx):
+    lib().ng_destroy(ctx)
+
+
+def ng_set_stream(ctx, stream=None):
+    _check(ctx, lib().ng_set_stream(ctx, _stream(stream)))
+
+
+def ng_build_tree(ctx, pos, typ, mass, keys_out=None, perm_out=None):
+    n = typ.numel()
+    _check(ctx, lib().ng_build_tree(ctx, n, _ptr(pos), _ptr(typ), _ptr(mass), _ptr(keys_out),
+                                    _ptr(perm_out)))
+
+
+def ng_tree_force(ctx, acc_out, count=False):
+    v = ctypes.c_uint64(0)
+    _check(ctx, lib().ng_tree_force(ctx, _ptr(acc_out), ctypes.byref(v) if count else None))
+    return int(v.value) if count else None
+
+
+def ng_count_interactions(ctx, counts_out=None):
+    v = ctypes.c_uint64(0)
+    _check(ctx, lib().ng_count_interactions(ctx, _ptr(counts_out), ctypes.byref(v)))
+    return int(v.value)
+
+
+def ng_pm_force(ctx, acc_out):
+    _check(ctx, lib().ng_pm_force(ctx, _ptr(acc_out)))
+
+
+def ng_step(ctx, pos, vel, typ, mass, acc, acc_valid, nsteps, dt):
+    n = typ.numel()
+    _check(ctx, lib().ng_step(ctx, n, _ptr(pos), _ptr(vel), _ptr(typ), _ptr(mass), _ptr(acc),
+                              int(bool(acc_valid)), int(nsteps), float(dt)))
+
+
+def ng_tree_export(ctx, D):
+    """Returns a dict of numpy arrays (canonical node order)."""
+    nn = ctypes.c_int64(0)
+    L = lib()
+    _check(ctx, L.ng_tree_export(ctx, ctypes.byref(nn), *([None] * 9)))
+    n = nn.value
+    out = dict(level=np.zeros(n, np.int32), prefix=np.zeros(n, np.uint64),
+               first=np.zeros(n, np.int64), count=np.zeros(n, np.int64),
+               nchild=np.zeros(n, np.int32), child_first=np.zeros(n, np.int64),
+               cnt=np.zeros((n, D), np.uint32), mass=np.zeros((n, D)), com=np.zeros((n, D, 3)))
+    keys = ("level", "prefix", "first", "count", "nchild", "child_first", "cnt", "mass", "com")
+    _check(ctx, L.ng_tree_export(ctx, ctypes.byref(nn),
+                                 *[out[k].ctypes.data_as(ctypes.c_void_p) for k in keys]))
+    return out
+
+
+def ng_type_order(ctx, D, order_out=None):
+    offs = np.zeros(D + 1, np.int64)
+    _check(ctx, lib().ng_type_order(ctx, offs.ctypes.data_as(ctypes.c_void_p), _ptr(order_out)))
+    return offs
+
+
+def ng_launch_count(ctx):
+    v = ctypes.c_uint64(0)
+    _check(ctx, lib().ng_launch_count(ctx, ctypes.byref(v)))
+    return int(v.value)
+
+
+def ng_version():
+    return lib().ng_version().decode()
+
+
+class Simulation:
+    """Owns one ng_ctx; convenience wrapper over the functions above."""
+
+    def __init__(self, params: NgParams, stream=None):
+        self.D = params.D
+        self.ctx = ng_create(params, stream)
+
+    def close(self):
+        if self.ctx is not None:
+            ng_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def force(self, pos, typ, mass, acc=None, pm=True):
+        """Short (+ long when the context has a mesh) acceleration, float32 [3, n]."""
+        import torch
+        n = typ.numel()
+        if acc is None:
+            acc = torch.empty((3, n), dtype=torch.float32, device=pos.device)
+        ng_build_tree(self.ctx, pos, typ, mass)
+        ng_tree_force(self.ctx, acc)
+        if pm:
+            long_ = torch.empty_like(acc)
+            ng_pm_force(self.ctx, long_)
+            acc += long_
+        return acc

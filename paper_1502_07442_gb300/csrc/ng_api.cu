@@ -1,0 +1,594 @@
+// C ABI of the ngravs library: validation, host-built short-range tables,
+// the pipeline entry points and the kick-drift-kick step (Sec. 2.1.1).
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "ng_internal.cuh"
+
+namespace ng {
+
+int fail(ng_ctx* c, int code, const char* fmt, ...) {
+  if (c) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    c->err = buf;
+  }
+  return code;
+}
+
+int ensure(ng_ctx* c, DevBuf& b, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  if (b.bytes >= bytes) return NG_OK;
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.bytes = 0;
+  void* p = nullptr;
+  const cudaError_t e = cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, NG_ENOMEM, "cudaMalloc of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+  }
+  b.p = p;
+  b.bytes = bytes;
+  if (c) c->alloc_gen++;
+  return NG_OK;
+}
+
+void release(DevBuf& b) {
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.bytes = 0;
+}
+
+// ------------------------------------------------------ short-range laws
+
+// Short-range force factor T(rho) of Sec. 2.4.1: the acceleration from a
+// source of active mass M is G M T(rho) d / rho^3. Newtonian part:
+// -rho^2 d/drho [erfc(rho / 2 r_s) / rho]. Yukawa part (Eq. (yukawa), C = 1,
+// Sec. 3.2 long-range kernel scaled by exp(-mu^2 r_s^2)): the remaining
+// real-space potential -a S(rho)/rho with
+//   S = [e^{-mu rho} erfc(v - mu r_s) + e^{mu rho} erfc(v + mu r_s)] / 2,
+// v = rho / 2 r_s, contributes a (S - rho dS/drho).
+double short_law_factor(int law, double a, double l, double rs, double rho) {
+  const double v = rho / (2.0 * rs);
+  const double gauss = std::exp(-v * v);
+  double T = std::erfc(v) + (2.0 / std::sqrt(M_PI)) * v * gauss;
+  if (law == NG_YUKAWA) {
+    const double mu = 1.0 / l;
+    const double lo = std::exp(-mu * rho) * std::erfc(v - mu * rs);
+    const double ec = std::erfc(v + mu * rs);
+    const double hi = ec > 0.0 ? std::exp(mu * rho + std::log(ec)) : 0.0;
+    const double S = 0.5 * (lo + hi);
+    const double dS = 0.5 * mu * (hi - lo) - gauss * std::exp(-mu * mu * rs * rs) / (rs * std::sqrt(M_PI));
+    T += a * (S - rho * dS);
+  }
+  return T;
+}
+
+// One table per distinct law; segment k (k < ncut) is the chord of T over
+// [(k - 1/2) dr, (k + 1/2) dr] (segment 0 over [0, dr/2]); the walk reads
+// c0 + t c1 with t = rho/dr - k; entry ncut is zero (beyond the cut-off,
+// which sits at rho = (ncut - 1/2) dr = sqrt(r_cut^2 + eps^2)).
+int build_tables(ng_ctx* c) {
+  const ng_params& p = c->p;
+  const int D = p.D;
+  struct Law { int kind; double a, l; };
+  std::vector<Law> laws;
+  for (int i = 0; i < D; ++i)
+    for (int j = 0; j < D; ++j) {
+      Law w{p.law[i][j], p.law[i][j] == NG_YUKAWA ? p.yuk_a[i][j] : 0.0,
+            p.law[i][j] == NG_YUKAWA ? p.yuk_l[i][j] : 0.0};
+      int id = -1;
+      for (size_t u = 0; u < laws.size(); ++u)
+        if (laws[u].kind == w.kind && laws[u].a == w.a && laws[u].l == w.l) id = (int)u;
+      if (id < 0) {
+        id = (int)laws.size();
+        laws.push_back(w);
+      }
+      c->tabid[i][j] = (int8_t)id;
+    }
+  c->nlaws = (int)laws.size();
+  int ncut = p.table_size;
+  if (ncut <= 0) {
+    const size_t budget = 96 * 1024;
+    ncut = (int)std::min<size_t>(4096, budget / (sizeof(float) * 2 * laws.size()) - 1);
+  }
+  if (ncut < 16) return fail(c, NG_EINVAL, "table_size %d too small", ncut);
+  c->ncut = ncut;
+  const double rho_cut = std::sqrt(c->rcut * c->rcut + p.eps * p.eps);
+  c->dr_phys = rho_cut / (ncut - 0.5);
+  // separations in table units must stay below 2^22 for the float-bit index
+  if (std::sqrt(3.0) * c->L / c->dr_phys > 4.0e6)
+    return fail(c, NG_EINVAL, "box too large relative to the table spacing (box/dr = %.3g)",
+                c->L / c->dr_phys);
+  std::vector<float> h((size_t)c->nlaws * (ncut + 1) * 2, 0.f);
+  for (int u = 0; u < c->nlaws; ++u) {
+    float* t = h.data() + (size_t)u * (ncut + 1) * 2;
+    auto T = [&](double rho) { return short_law_factor(laws[u].kind, laws[u].a, laws[u].l, c->rs, rho); };
+    const double dr = c->dr_phys;
+    t[0] = (float)T(0.0);
+    t[1] = (float)(2.0 * (T(0.5 * dr) - T(0.0)));
+    for (int k = 1; k < ncut; ++k) {
+      const double lo = T((k - 0.5) * dr), hi = T((k + 0.5) * dr);
+      t[2 * k] = (float)(0.5 * (lo + hi));
+      t[2 * k + 1] = (float)(hi - lo);
+    }
+    t[2 * ncut] = 0.f;
+    t[2 * ncut + 1] = 0.f;
+  }
+  NG_TRY(ensure(c, c->d_tab, h.size() * sizeof(float)));
+  NG_CUDA(c, cudaMemcpy(c->d_tab.p, h.data(), h.size() * sizeof(float), cudaMemcpyHostToDevice));
+  return NG_OK;
+}
+
+// ---------------------------------------------------------------- KDK
+
+__global__ void k_kick(int64_t m, float* __restrict__ vel, const float* __restrict__ acc, float h) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
+       i += (int64_t)gridDim.x * blockDim.x)
+    vel[i] = fmaf(acc[i], h, vel[i]);
+}
+
+__global__ void k_drift(int64_t m, double* __restrict__ pos, const float* __restrict__ vel,
+                        double dt, double L) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double x = fma((double)vel[i], dt, pos[i]);
+    pos[i] = x - L * floor(x / L);
+  }
+}
+
+// ------------------------------------------------------------ pipeline
+
+static size_t node_bytes(int D) {
+  return 1 + 8 + 4 + 4 + 4 + 1 + 4 + (size_t)D * 32 + (size_t)D * 4 + 16 * 3 + (size_t)D * 16;
+}
+
+static int alloc_nodes(ng_ctx* c, int64_t cap) {
+  const int D = c->p.D;
+  NG_TRY(ensure(c, c->n_level, cap));
+  NG_TRY(ensure(c, c->n_prefix, cap * 8));
+  NG_TRY(ensure(c, c->n_first, cap * 4));
+  NG_TRY(ensure(c, c->n_count, cap * 4));
+  NG_TRY(ensure(c, c->n_child, cap * 4));
+  NG_TRY(ensure(c, c->n_nchild, cap));
+  NG_TRY(ensure(c, c->n_tmp, cap * 4));
+  NG_TRY(ensure(c, c->n_m64, cap * D * 32));
+  NG_TRY(ensure(c, c->n_cnt, cap * D * 4));
+  NG_TRY(ensure(c, c->n_geo, cap * 16));
+  NG_TRY(ensure(c, c->n_com, cap * 16));
+  NG_TRY(ensure(c, c->n_link, cap * 16));
+  NG_TRY(ensure(c, c->n_mono, cap * D * 16));
+  c->cap_nodes = cap;
+  (void)node_bytes;
+  return NG_OK;
+}
+
+static int alloc_bodies(ng_ctx* c, int64_t n) {
+  NG_TRY(ensure(c, c->body, n * 16));
+  NG_TRY(ensure(c, c->bleaf, n * 4));
+  NG_TRY(ensure(c, c->groups, n * 8));
+  NG_TRY(ensure(c, c->status, ST_COUNT * 4));
+  NG_TRY(ensure(c, c->counter, 8));
+  return NG_OK;
+}
+
+// Everything after the sort; no host synchronisation.
+static int tree_stages(ng_ctx* c) {
+  NG_TRY(build_octree(c));
+  NG_TRY(reduce_monopoles(c));
+  NG_TRY(build_groups(c));
+  NG_TRY(type_order(c));
+  return NG_OK;
+}
+
+static int read_status(ng_ctx* c, uint32_t* st) {
+  NG_CUDA(c, cudaMemcpyAsync(st, c->status.p, ST_COUNT * 4, cudaMemcpyDeviceToHost, c->stream));
+  NG_CUDA(c, cudaStreamSynchronize(c->stream));
+  return NG_OK;
+}
+
+static int check_flags(ng_ctx* c, uint32_t flags) {
+  if (flags & SF_NODE_OVERFLOW) return fail(c, NG_ENOMEM, "tree node capacity exceeded");
+  if (flags & SF_STACK_OVERFLOW) return fail(c, NG_ENOMEM, "walk stack capacity exceeded");
+  if (flags & SF_GROUP_OVERFLOW) return fail(c, NG_ENOMEM, "walk group capacity exceeded");
+  if (flags & SF_BAD_TYPE) return fail(c, NG_EINVAL, "a species value is >= D");
+  if (flags) return fail(c, NG_ECUDA, "device status flags 0x%x", flags);
+  return NG_OK;
+}
+
+// Sort + tree with capacity sizing (synchronises once per attempt).
+static int build_checked(ng_ctx* c, int64_t n, const double* pos, const uint8_t* type,
+                         const float* mass) {
+  c->n = n;
+  c->built = false;
+  NG_TRY(alloc_bodies(c, n));
+  NG_CUDA(c, cudaMemsetAsync(c->status.p, 0, ST_COUNT * 4, c->stream));
+  NG_TRY(sort_bodies(c, n, pos, type, mass));
+  if (c->cap_nodes == 0) {
+    const int leaf = std::max(1, c->p.leaf_size);
+    NG_TRY(alloc_nodes(c, std::max<int64_t>(4096, 3 * n / leaf + 1024)));
+  }
+  for (int attempt = 0; attempt < 8; ++attempt) {
+    NG_TRY(build_octree(c));
+    uint32_t st[ST_COUNT];
+    NG_TRY(read_status(c, st));
+    if (st[ST_FLAGS] & SF_BAD_TYPE) return check_flags(c, SF_BAD_TYPE);
+    if (st[ST_FLAGS] & SF_NODE_OVERFLOW) {
+      const int64_t need = (int64_t)st[ST_NODES_NEEDED];
+      NG_TRY(alloc_nodes(c, std::max<int64_t>(need + need / 2, 2 * c->cap_nodes)));
+      NG_CUDA(c, cudaMemsetAsync(c->status.p, 0, sizeof(uint32_t), c->stream));
+      continue;
+    }
+    c->nnodes = st[ST_LEVELS + kMaxLevel + 1];
+    NG_TRY(reduce_monopoles(c));
+    NG_TRY(build_groups(c));
+    NG_TRY(type_order(c));
+    NG_TRY(read_status(c, st));
+    NG_TRY(check_flags(c, st[ST_FLAGS]));
+    c->built = true;
+    return NG_OK;
+  }
+  return fail(c, NG_ENOMEM, "tree capacity could not be sized");
+}
+
+// Short + long acceleration into acc (no host synchronisation).
+static int force_stages(ng_ctx* c, float* acc) {
+  if (c->p.pm_mesh > 0) {
+    NG_TRY(pm_force(c, acc, false));
+    NG_TRY(launch_walk(c, acc, true, false));
+  } else {
+    NG_TRY(launch_walk(c, acc, false, false));
+  }
+  return NG_OK;
+}
+
+static bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+
+static int validate(ng_ctx* c, const ng_params* p) {
+  if (!p) return fail(c, NG_EINVAL, "params is NULL");
+  if (p->D < 1 || p->D > NG_MAX_SPECIES) return fail(c, NG_EINVAL, "D=%d outside 1..6", p->D);
+  if (!(p->box > 0) || !std::isfinite(p->box)) return fail(c, NG_EINVAL, "box must be > 0");
+  if (!(p->eps > 0) || !std::isfinite(p->eps)) return fail(c, NG_EINVAL, "eps must be > 0");
+  if (!(p->asmth > 0)) return fail(c, NG_EINVAL, "asmth must be > 0");
+  if (!(p->rcut_over_rs > 0)) return fail(c, NG_EINVAL, "rcut_over_rs must be > 0");
+  if (!(p->theta >= 0) || p->theta > 2.0) return fail(c, NG_EINVAL, "theta must be in [0, 2]");
+  if (p->pm_mesh != 0 && (!is_pow2(p->pm_mesh) || p->pm_mesh < 8 || p->pm_mesh > 1024))
+    return fail(c, NG_EINVAL, "pm_mesh must be 0 or a power of two in [8, 1024]");
+  if (p->leaf_size < 0 || p->leaf_size > 64) return fail(c, NG_EINVAL, "leaf_size must be 0..64");
+  if (p->group_size != 0 && p->group_size != 32)
+    return fail(c, NG_EINVAL, "group_size must be 0 or 32");
+  if (p->table_size < 0 || p->table_size > 8192) return fail(c, NG_EINVAL, "table_size 0..8192");
+  for (int i = 0; i < p->D; ++i)
+    for (int j = 0; j < p->D; ++j) {
+      if (!std::isfinite(p->G[i][j])) return fail(c, NG_EINVAL, "G[%d][%d] not finite", i, j);
+      if (p->law[i][j] != NG_NEWTON && p->law[i][j] != NG_YUKAWA)
+        return fail(c, NG_EINVAL, "law[%d][%d]=%d unknown", i, j, p->law[i][j]);
+      if (p->law[i][j] == NG_YUKAWA && (!(p->yuk_l[i][j] > 0) || !std::isfinite(p->yuk_a[i][j])))
+        return fail(c, NG_EINVAL, "Yukawa range yuk_l[%d][%d] must be > 0", i, j);
+    }
+  const double rs = p->pm_mesh > 0 ? p->asmth * p->box / p->pm_mesh : p->asmth * p->box;
+  if (!(p->rcut_over_rs * rs < 0.5 * p->box))
+    return fail(c, NG_EINVAL, "r_cut = %.4g must be below box/2", p->rcut_over_rs * rs);
+  return NG_OK;
+}
+
+}  // namespace ng
+
+using namespace ng;
+
+// Message of the last failed ng_create on this thread (read via ng_last_error(NULL)).
+static thread_local std::string g_create_err;
+
+extern "C" {
+
+int ng_create(ng_ctx** out, const ng_params* p, void* stream) {
+  if (!out) return NG_EINVAL;
+  *out = nullptr;
+  ng_ctx* c = new (std::nothrow) ng_ctx();
+  if (!c) return NG_ENOMEM;
+  int r = validate(c, p);
+  if (r != NG_OK) {
+    g_create_err = c->err;
+    delete c;
+    return r;
+  }
+  c->p = *p;
+  if (c->p.leaf_size == 0) c->p.leaf_size = 8;
+  if (c->p.group_size == 0) c->p.group_size = 32;
+  c->stream = (cudaStream_t)stream;
+  c->L = p->box;
+  c->rs = p->pm_mesh > 0 ? p->asmth * p->box / p->pm_mesh : p->asmth * p->box;
+  c->rcut = p->rcut_over_rs * c->rs;
+  cudaError_t e = cudaGetDevice(&c->device);
+  int v = 0;
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, c->device);
+  c->nsm = v;
+  if (e == cudaSuccess)
+    e = cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
+  c->smem_optin = (size_t)v;
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    delete c;
+    return NG_ECUDA;
+  }
+  r = build_tables(c);
+  if (r == NG_OK) r = ensure(c, c->status, ST_COUNT * 4);
+  if (r == NG_OK) r = ensure(c, c->counter, 8);
+  if (r != NG_OK) {
+    ng_destroy(c);
+    return r;
+  }
+  *out = c;
+  return NG_OK;
+}
+
+int ng_destroy(ng_ctx* c) {
+  if (!c) return NG_OK;
+  if (c->step_exec) cudaGraphExecDestroy(c->step_exec);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  if (c->plan_r2c) cufftDestroy(c->plan_r2c);
+  if (c->plan_c2r) cufftDestroy(c->plan_c2r);
+  DevBuf* bufs[] = {&c->d_tab, &c->keys_a, &c->keys_b, &c->vals_a, &c->vals_b, &c->blockhist,
+                    &c->skeys, &c->perm, &c->spos, &c->smass, &c->stype, &c->body, &c->bleaf,
+                    &c->tperm, &c->scan_part, &c->n_level, &c->n_prefix, &c->n_first,
+                    &c->n_count, &c->n_child, &c->n_nchild, &c->n_tmp, &c->n_off, &c->n_m64,
+                    &c->n_cnt, &c->n_geo, &c->n_com, &c->n_link, &c->n_mono, &c->groups,
+                    &c->status, &c->counter, &c->acc_tmp, &c->rho, &c->rhok, &c->phi};
+  for (DevBuf* b : bufs) release(*b);
+  delete c;
+  return NG_OK;
+}
+
+int ng_set_stream(ng_ctx* c, void* stream) {
+  if (!c) return NG_EINVAL;
+  c->stream = (cudaStream_t)stream;
+  if (c->step_exec) {
+    cudaGraphExecDestroy(c->step_exec);
+    c->step_exec = nullptr;
+  }
+  return NG_OK;
+}
+
+int ng_build_tree(ng_ctx* c, int64_t n, const double* pos, const uint8_t* type,
+                  const float* mass, uint64_t* keys_out, uint32_t* perm_out) {
+  if (!c) return NG_EINVAL;
+  if (n < 1 || n >= (int64_t)1 << 31) return fail(c, NG_EINVAL, "n=%lld outside [1, 2^31)", (long long)n);
+  if (!pos || !type || !mass) return fail(c, NG_EINVAL, "pos/type/mass must be device pointers");
+  NG_TRY(build_checked(c, n, pos, type, mass));
+  if (keys_out)
+    NG_CUDA(c, cudaMemcpyAsync(keys_out, c->keys_a.p, n * 8, cudaMemcpyDeviceToDevice, c->stream));
+  if (perm_out)
+    NG_CUDA(c, cudaMemcpyAsync(perm_out, c->vals_a.p, n * 4, cudaMemcpyDeviceToDevice, c->stream));
+  return NG_OK;
+}
+
+int ng_tree_force(ng_ctx* c, float* acc_out, uint64_t* interactions_out) {
+  if (!c) return NG_EINVAL;
+  if (!c->built) return fail(c, NG_ESTATE, "ng_tree_force before ng_build_tree");
+  if (!acc_out) return fail(c, NG_EINVAL, "acc_out is NULL");
+  if (interactions_out)
+    NG_CUDA(c, cudaMemsetAsync(c->counter.p, 0, 8, c->stream));
+  NG_TRY(launch_walk(c, acc_out, false, interactions_out != nullptr));
+  if (interactions_out) {
+    unsigned long long v = 0;
+    NG_CUDA(c, cudaMemcpyAsync(&v, c->counter.p, 8, cudaMemcpyDeviceToHost, c->stream));
+    uint32_t st[ST_COUNT];
+    NG_TRY(read_status(c, st));
+    NG_TRY(check_flags(c, st[ST_FLAGS]));
+    *interactions_out = v;
+  }
+  return NG_OK;
+}
+
+int ng_count_interactions(ng_ctx* c, int64_t* counts_out, uint64_t* total_out) {
+  if (!c) return NG_EINVAL;
+  if (!c->built) return fail(c, NG_ESTATE, "ng_count_interactions before ng_build_tree");
+  NG_TRY(launch_count(c, counts_out));
+  unsigned long long v = 0;
+  NG_CUDA(c, cudaMemcpyAsync(&v, c->counter.p, 8, cudaMemcpyDeviceToHost, c->stream));
+  uint32_t st[ST_COUNT];
+  NG_TRY(read_status(c, st));
+  NG_TRY(check_flags(c, st[ST_FLAGS]));
+  if (total_out) *total_out = v;
+  return NG_OK;
+}
+
+int ng_pm_force(ng_ctx* c, float* acc_out) {
+  if (!c) return NG_EINVAL;
+  if (!c->built) return fail(c, NG_ESTATE, "ng_pm_force before ng_build_tree");
+  if (!acc_out) return fail(c, NG_EINVAL, "acc_out is NULL");
+  return pm_force(c, acc_out, false);
+}
+
+static int step_once(ng_ctx* c, int64_t n, double* pos, float* vel, const uint8_t* type,
+                     const float* mass, float* acc, double dt) {
+  const int grid = device_grid(c, 8);
+  c->launches += 3;   // kick, drift, kick
+  k_kick<<<grid, 256, 0, c->stream>>>(3 * n, vel, acc, (float)(0.5 * dt));
+  k_drift<<<grid, 256, 0, c->stream>>>(3 * n, pos, vel, dt, c->L);
+  NG_CUDA(c, cudaGetLastError());
+  NG_TRY(sort_bodies(c, n, pos, type, mass));
+  NG_TRY(tree_stages(c));
+  NG_TRY(force_stages(c, acc));
+  k_kick<<<grid, 256, 0, c->stream>>>(3 * n, vel, acc, (float)(0.5 * dt));
+  NG_CUDA(c, cudaGetLastError());
+  return NG_OK;
+}
+
+int ng_step(ng_ctx* c, int64_t n, double* pos, float* vel, const uint8_t* type,
+            const float* mass, float* acc, int acc_valid, int nsteps, double dt) {
+  if (!c) return NG_EINVAL;
+  if (n < 1 || n >= (int64_t)1 << 31) return fail(c, NG_EINVAL, "n outside [1, 2^31)");
+  if (!pos || !vel || !type || !mass || !acc) return fail(c, NG_EINVAL, "NULL array");
+  if (nsteps < 0 || !std::isfinite(dt)) return fail(c, NG_EINVAL, "bad nsteps/dt");
+  if (!acc_valid) {
+    NG_TRY(build_checked(c, n, pos, type, mass));
+    NG_TRY(force_stages(c, acc));
+  }
+  if (nsteps == 0) {
+    NG_CUDA(c, cudaStreamSynchronize(c->stream));
+    return NG_OK;
+  }
+  const void* ptrs[5] = {pos, vel, type, mass, acc};
+  bool reuse = c->step_exec && c->graph_n == n && c->graph_dt == dt &&
+               c->graph_gen == c->alloc_gen && std::equal(ptrs, ptrs + 5, c->graph_ptrs);
+  int done = 0;
+  if (!reuse) {
+    // one eager step sizes every buffer, then the step is captured
+    const int grid = device_grid(c, 8);
+    k_kick<<<grid, 256, 0, c->stream>>>(3 * n, vel, acc, (float)(0.5 * dt));
+    k_drift<<<grid, 256, 0, c->stream>>>(3 * n, pos, vel, dt, c->L);
+    c->launches += 3;
+    NG_CUDA(c, cudaGetLastError());
+    NG_TRY(build_checked(c, n, pos, type, mass));
+    NG_TRY(force_stages(c, acc));
+    k_kick<<<grid, 256, 0, c->stream>>>(3 * n, vel, acc, (float)(0.5 * dt));
+    NG_CUDA(c, cudaGetLastError());
+    done = 1;
+    if (c->cap_nodes < c->nnodes + c->nnodes / 4 + 1024) {
+      NG_CUDA(c, cudaStreamSynchronize(c->stream));
+      NG_TRY(alloc_nodes(c, c->nnodes + c->nnodes / 4 + 1024));
+    }
+    NG_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (c->step_exec) {
+      cudaGraphExecDestroy(c->step_exec);
+      c->step_exec = nullptr;
+    }
+    if (done < nsteps) {
+      // capture needs a stream other than the legacy default one
+      if (!c->cap_stream)
+        NG_CUDA(c, cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+      cudaStream_t user = c->stream;
+      cudaGraph_t g = nullptr;
+      NG_CUDA(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeRelaxed));
+      c->stream = c->cap_stream;
+      const uint64_t before = c->launches;
+      const int r = step_once(c, n, pos, vel, type, mass, acc, dt);
+      c->graph_launches = c->launches - before;
+      c->launches = before;
+      c->stream = user;
+      const cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
+      cudaGetLastError();
+      if (r != NG_OK) {
+        if (g) cudaGraphDestroy(g);
+        return r;
+      }
+      if (e != cudaSuccess) return fail(c, NG_ECUDA, "step capture failed: %s", cudaGetErrorString(e));
+      const cudaError_t ei = cudaGraphInstantiate(&c->step_exec, g, 0);
+      cudaGraphDestroy(g);
+      if (ei != cudaSuccess)
+        return fail(c, NG_ECUDA, "graph instantiate failed: %s", cudaGetErrorString(ei));
+      c->graph_n = n;
+      c->graph_dt = dt;
+      c->graph_gen = c->alloc_gen;
+      std::copy(ptrs, ptrs + 5, c->graph_ptrs);
+    }
+  }
+  if (done < nsteps)
+    NG_CUDA(c, cudaMemsetAsync(c->status.p, 0, sizeof(uint32_t), c->stream));  // sticky flags
+  for (int s = done; s < nsteps; ++s) {
+    NG_CUDA(c, cudaGraphLaunch(c->step_exec, c->stream));
+    c->launches += c->graph_launches;
+  }
+  uint32_t st[ST_COUNT];
+  NG_TRY(read_status(c, st));
+  NG_TRY(check_flags(c, st[ST_FLAGS]));
+  c->built = true;
+  return NG_OK;
+}
+
+int ng_tree_export(ng_ctx* c, int64_t* nnodes, int32_t* level, uint64_t* prefix, int64_t* first,
+                   int64_t* count, int32_t* nchild, int64_t* child_first, uint32_t* cnt,
+                   double* mass, double* com) {
+  if (!c || !nnodes) return NG_EINVAL;
+  if (!c->built) return fail(c, NG_ESTATE, "no tree built");
+  NG_CUDA(c, cudaStreamSynchronize(c->stream));
+  const int64_t nn = c->nnodes;
+  const int D = c->p.D;
+  *nnodes = nn;
+  std::vector<uint8_t> u8(nn);
+  std::vector<uint32_t> u32(nn);
+  if (level) {
+    NG_CUDA(c, cudaMemcpy(u8.data(), c->n_level.p, nn, cudaMemcpyDeviceToHost));
+    for (int64_t k = 0; k < nn; ++k) level[k] = u8[k];
+  }
+  if (prefix) NG_CUDA(c, cudaMemcpy(prefix, c->n_prefix.p, nn * 8, cudaMemcpyDeviceToHost));
+  if (first) {
+    NG_CUDA(c, cudaMemcpy(u32.data(), c->n_first.p, nn * 4, cudaMemcpyDeviceToHost));
+    for (int64_t k = 0; k < nn; ++k) first[k] = u32[k];
+  }
+  if (count) {
+    NG_CUDA(c, cudaMemcpy(u32.data(), c->n_count.p, nn * 4, cudaMemcpyDeviceToHost));
+    for (int64_t k = 0; k < nn; ++k) count[k] = u32[k];
+  }
+  std::vector<uint8_t> nch(nn);
+  NG_CUDA(c, cudaMemcpy(nch.data(), c->n_nchild.p, nn, cudaMemcpyDeviceToHost));
+  if (nchild)
+    for (int64_t k = 0; k < nn; ++k) nchild[k] = nch[k];
+  if (child_first) {
+    NG_CUDA(c, cudaMemcpy(u32.data(), c->n_child.p, nn * 4, cudaMemcpyDeviceToHost));
+    for (int64_t k = 0; k < nn; ++k) child_first[k] = nch[k] ? (int64_t)u32[k] : -1;
+  }
+  if (cnt) NG_CUDA(c, cudaMemcpy(cnt, c->n_cnt.p, nn * D * 4, cudaMemcpyDeviceToHost));
+  if (mass || com) {
+    std::vector<double> m64((size_t)nn * D * 4);
+    NG_CUDA(c, cudaMemcpy(m64.data(), c->n_m64.p, m64.size() * 8, cudaMemcpyDeviceToHost));
+    for (int64_t k = 0; k < nn; ++k)
+      for (int t = 0; t < D; ++t) {
+        const double* s = &m64[((size_t)k * D + t) * 4];
+        if (mass) mass[k * D + t] = s[0];
+        if (com)
+          for (int d = 0; d < 3; ++d) com[(k * D + t) * 3 + d] = s[0] > 0 ? s[1 + d] / s[0] * c->L : 0.0;
+      }
+  }
+  return NG_OK;
+}
+
+int ng_type_order(ng_ctx* c, int64_t* type_offsets, uint32_t* order_out) {
+  if (!c) return NG_EINVAL;
+  if (!c->built) return fail(c, NG_ESTATE, "no tree built");
+  const int64_t n = c->n;
+  const int nblocks = (int)((n + 4095) / 4096);
+  if (type_offsets) {
+    NG_CUDA(c, cudaStreamSynchronize(c->stream));
+    for (int d = 0; d < c->p.D; ++d) {
+      uint32_t v = 0;
+      NG_CUDA(c, cudaMemcpy(&v, as<uint32_t>(c->blockhist) + (size_t)d * nblocks, 4,
+                            cudaMemcpyDeviceToHost));
+      type_offsets[d] = v;
+    }
+    type_offsets[c->p.D] = n;
+  }
+  if (order_out) {
+    // caller indices in type-major order: perm[tperm[j]]
+    std::vector<uint32_t> tp(n), pm(n);
+    NG_CUDA(c, cudaMemcpy(tp.data(), c->tperm.p, n * 4, cudaMemcpyDeviceToHost));
+    NG_CUDA(c, cudaMemcpy(pm.data(), c->vals_a.p, n * 4, cudaMemcpyDeviceToHost));
+    for (int64_t j = 0; j < n; ++j) tp[j] = pm[tp[j]];
+    NG_CUDA(c, cudaMemcpy(order_out, tp.data(), n * 4, cudaMemcpyHostToDevice));
+  }
+  return NG_OK;
+}
+
+int ng_launch_count(const ng_ctx* c, uint64_t* out) {
+  if (!c || !out) return NG_EINVAL;
+  *out = c->launches;
+  return NG_OK;
+}
+
+const char* ng_last_error(const ng_ctx* c) {
+  if (!c) return g_create_err.empty() ? "no context" : g_create_err.c_str();
+  return c->err.c_str();
+}
+
+const char* ng_version(void) { return "ngravs-gb300 0.1 (sm_103a)"; }
+
+}  // extern "C"

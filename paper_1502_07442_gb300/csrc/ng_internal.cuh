@@ -1,0 +1,188 @@
+// Internal declarations of the ngravs CUDA library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cufft.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/ngravs.h"
+
+namespace ng {
+
+// ----------------------------------------------------------------- limits
+constexpr int kMaxD = NG_MAX_SPECIES;
+constexpr int kMaxLevel = 20;           // 20 Morton bits per axis
+constexpr int kWarp = 32;
+
+// Status words in device memory (ctx->status).
+enum StatusSlot {
+  ST_FLAGS = 0,          // bit flags below
+  ST_NODES_NEEDED = 1,   // node count the last build asked for
+  ST_NGROUPS = 2,        // walk groups of the last build
+  ST_WORK = 3,           // walk work-queue counter
+  ST_LEVELS = 8,         // 22 level starts (levels 0..20, then end) + 21 level counts
+  ST_COUNT = 64
+};
+enum StatusFlag {
+  SF_NODE_OVERFLOW = 1,
+  SF_STACK_OVERFLOW = 2,
+  SF_GROUP_OVERFLOW = 4,
+  SF_BAD_TREE = 8,
+  SF_BAD_TYPE = 16
+};
+static_assert(ST_LEVELS + (kMaxLevel + 2) + (kMaxLevel + 1) <= ST_COUNT, "status block too small");
+
+// Growable device buffer.
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+// Walk tuning constants.
+constexpr int kListCap = 64;            // records per species list per warp
+constexpr int kStackCap = 512;          // node stack entries per warp
+constexpr int kWalkMaxWarps = 16;
+
+// Device view of the short-range walk inputs.
+struct WalkArgs {
+  // tree
+  const float4* geo;        // [node] centre (box units), half side
+  const float4* com;        // [node] all-species centre of mass - centre, total mass
+  const int4* link;         // [node] child_first, nchild, body_first, body_count
+  const float4* mono;       // [node][D] species com - centre, species mass
+  const float4* body;       // [sorted body] offset from its leaf centre, mass
+  const uint8_t* btype;     // [sorted body] species
+  const uint32_t* bleaf;    // [sorted body] leaf node holding the body
+  const double* spos;       // [3][n] sorted wrapped positions (box units * L)
+  const int2* groups;       // [group] first body, count
+  const uint32_t* perm;     // sorted -> caller index
+  uint32_t* status;         // device status words
+  // tables
+  const float2* tab;        // [law][ncut + 1] segment {c0, c1}
+  int tab_entries;          // ncut + 1
+  int ncut;
+  int8_t tabid[kMaxD][kMaxD];
+  float G[kMaxD][kMaxD];
+  // geometry
+  int64_t n;
+  double L, invL;           // box side and its inverse
+  double inv_dr;            // table units per box unit
+  float rcut_box;           // cut-off in box units
+  float theta2;
+  float eps2_tab;           // softening^2 in table units^2
+  float out_scale;          // converts accumulated table-unit sums to acceleration
+  // outputs
+  float* acc;               // [3][n] caller order
+  unsigned long long* counter;  // executed interaction counter (optional)
+  int accumulate;           // add into acc instead of overwriting
+};
+
+}  // namespace ng
+
+// Opaque context (defined here, declared in the public header).
+struct ng_ctx {
+  ng_params p{};
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int nsm = 0;
+  size_t smem_optin = 0;
+  std::string err;
+
+  // derived geometry
+  double L = 1.0, rs = 0, rcut = 0;
+
+  // short-range tables
+  int nlaws = 0, ncut = 0;
+  int8_t tabid[ng::kMaxD][ng::kMaxD]{};
+  double dr_phys = 0;                 // table spacing (physical length)
+  ng::DevBuf d_tab;
+
+  // particles of the last build
+  int64_t n = 0;
+  bool built = false;
+  ng::DevBuf keys_a, keys_b, vals_a, vals_b, blockhist;
+  ng::DevBuf skeys, perm, spos, smass, stype, body, bleaf, tperm, scan_part;
+  int64_t toffs[ng::kMaxD + 1]{};
+
+  // tree
+  int64_t cap_nodes = 0, nnodes = 0;
+  ng::DevBuf n_level, n_prefix, n_first, n_count, n_child, n_nchild, n_tmp, n_off;
+  ng::DevBuf n_m64, n_cnt, n_geo, n_com, n_link, n_mono;
+  ng::DevBuf groups;
+  ng::DevBuf status;     // uint32[ST_COUNT]
+  ng::DevBuf counter;    // unsigned long long
+  ng::DevBuf acc_tmp;    // float[3][n] scratch for summing short + long
+
+  // PM
+  int pm_ready = 0;
+  int pm_n = 0;
+  cufftHandle plan_r2c = 0, plan_c2r = 0;
+  ng::DevBuf rho, rhok, phi;
+
+  // kernels this library has launched (host-side count)
+  uint64_t launches = 0;
+  uint64_t graph_launches = 0;     // kernels in one captured step
+
+  // step graph (captured on a private stream, replayed on the caller's)
+  cudaStream_t cap_stream = nullptr;
+  uint64_t alloc_gen = 0;          // bumped whenever a device buffer is (re)allocated
+  uint64_t graph_gen = 0;
+  cudaGraphExec_t step_exec = nullptr;
+  int64_t graph_n = -1;
+  const void* graph_ptrs[5]{};
+  double graph_dt = 0;
+};
+
+namespace ng {
+
+// Error helpers: record a message on ctx and return a code.
+int fail(ng_ctx* c, int code, const char* fmt, ...);
+#define NG_CUDA(c, call)                                                             \
+  do {                                                                               \
+    cudaError_t e_ = (call);                                                         \
+    if (e_ != cudaSuccess) {                                                         \
+      cudaGetLastError(); /* leave no stale error for the next call */               \
+      return ::ng::fail((c), NG_ECUDA, "%s failed: %s (%s:%d)", #call,               \
+                        cudaGetErrorString(e_), __FILE__, __LINE__);                 \
+    }                                                                                \
+  } while (0)
+#define NG_TRY(expr)                 \
+  do {                               \
+    int r_ = (expr);                 \
+    if (r_ != NG_OK) return r_;      \
+  } while (0)
+
+// Ensure buf holds at least bytes (grows, contents not kept).
+int ensure(ng_ctx* c, DevBuf& buf, size_t bytes);
+void release(DevBuf& buf);
+
+template <class T>
+inline T* as(const DevBuf& b) { return static_cast<T*>(b.p); }
+
+// Device-wide exclusive scan of uint32 values; len read from *d_len when
+// d_len != nullptr (then len is an upper bound), total written to *d_total
+// when non-null. Needs ctx->scan_part scratch.
+int scan_u32(ng_ctx* c, const uint32_t* in, uint32_t* out, int64_t len,
+             const uint32_t* d_len, uint32_t* d_total);
+
+// Stages of the pipeline (each enqueues on c->stream, no host sync).
+int sort_bodies(ng_ctx* c, int64_t n, const double* pos, const uint8_t* type,
+                const float* mass);
+int build_octree(ng_ctx* c);                  // needs sorted bodies
+int reduce_monopoles(ng_ctx* c);              // needs octree
+int build_groups(ng_ctx* c);                  // needs octree
+int launch_walk(ng_ctx* c, float* acc, bool accumulate, bool count);
+int launch_count(ng_ctx* c, int64_t* counts);  // per-particle walk counts
+int pm_force(ng_ctx* c, float* acc, bool accumulate);
+int type_order(ng_ctx* c);
+
+// Host short-range law tables (double precision closed forms).
+int build_tables(ng_ctx* c);
+double short_law_factor(int law, double a, double l, double rs, double rho);
+
+int device_grid(ng_ctx* c, int per_sm);
+
+}  // namespace ng

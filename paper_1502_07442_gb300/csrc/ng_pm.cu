@@ -1,0 +1,226 @@
+// Long-range PM step (Sec. 2.4; Sec. 2.4.1 split; Sec. 3.2 Yukawa filter).
+//
+// Per active species j the CIC-deposited mass mesh rho_j is transformed
+// (cuFFT R2C, D transforms in one batched plan); every mode is then mapped
+// in place to phi_i(k) = sum_j K_ij(k) rho_j(k) for all passive species i at
+// once (the paper's D^2 passes, fused: each mode is read and written once);
+// D inverse transforms give phi_i, and each particle of passive species i
+// interpolates -grad phi_i (4-point differences at the 8 CIC corners).
+//
+// K_ij(k) = -4 pi G_ij [1/k^2 + a_ij e^{-mu^2 r_s^2}/(k^2 + mu^2)] e^{-k^2 r_s^2}
+//           / W(k)^2 / L^3,   W = prod_d sinc^2(pi n_d / N), K(0) = 0.
+// The 1/L^3 folds the cell volume of the density and the 1/N^3 of the
+// unnormalised inverse transform.
+#include <cmath>
+
+#include "ng_internal.cuh"
+
+namespace ng {
+
+struct PmLaw {
+  float G[kMaxD][kMaxD];
+  float yfac[kMaxD][kMaxD];   // a_ij exp(-mu^2 r_s^2), 0 for Newtonian pairs
+  float mu2[kMaxD][kMaxD];
+};
+
+__global__ void k_cic_deposit(int64_t n, const uint32_t* __restrict__ order,
+                              const double* __restrict__ spos, const float* __restrict__ smass,
+                              const uint8_t* __restrict__ stype, int N, double cells_per_len,
+                              float* __restrict__ rho) {
+  const size_t N3 = (size_t)N * N * N;
+  const int mask = N - 1;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t k = order[j];
+    const double ux = spos[k] * cells_per_len, uy = spos[n + k] * cells_per_len,
+                 uz = spos[2 * n + k] * cells_per_len;
+    const double fx0 = floor(ux), fy0 = floor(uy), fz0 = floor(uz);
+    const float fx = (float)(ux - fx0), fy = (float)(uy - fy0), fz = (float)(uz - fz0);
+    const int ix = (int)fx0 & mask, iy = (int)fy0 & mask, iz = (int)fz0 & mask;
+    const int jx = (ix + 1) & mask, jy = (iy + 1) & mask, jz = (iz + 1) & mask;
+    float* r = rho + (size_t)stype[k] * N3;
+    const float m = smass[k];
+    const float wx0 = 1.f - fx, wy0 = 1.f - fy, wz0 = 1.f - fz;
+    const size_t X0 = (size_t)ix * N * N, X1 = (size_t)jx * N * N;
+    const size_t Y0 = (size_t)iy * N, Y1 = (size_t)jy * N;
+    atomicAdd(r + X0 + Y0 + iz, m * wx0 * wy0 * wz0);
+    atomicAdd(r + X0 + Y0 + jz, m * wx0 * wy0 * fz);
+    atomicAdd(r + X0 + Y1 + iz, m * wx0 * fy * wz0);
+    atomicAdd(r + X0 + Y1 + jz, m * wx0 * fy * fz);
+    atomicAdd(r + X1 + Y0 + iz, m * fx * wy0 * wz0);
+    atomicAdd(r + X1 + Y0 + jz, m * fx * wy0 * fz);
+    atomicAdd(r + X1 + Y1 + iz, m * fx * fy * wz0);
+    atomicAdd(r + X1 + Y1 + jz, m * fx * fy * fz);
+  }
+}
+
+__device__ __forceinline__ float sinc_pi(int nd, int N) {
+  if (nd == 0) return 1.f;
+  const float x = 3.14159265358979f * (float)nd / (float)N;
+  return sinf(x) / x;
+}
+
+template <int D>
+__global__ void k_kspace(cufftComplex* __restrict__ mesh, int N, float kf, float rs2,
+                         float pref, PmLaw law) {
+  const int Nz = N / 2 + 1;
+  const size_t modes = (size_t)N * N * Nz;
+  for (size_t m = blockIdx.x * (size_t)blockDim.x + threadIdx.x; m < modes;
+       m += (size_t)gridDim.x * blockDim.x) {
+    const int z = (int)(m % Nz);
+    const int y = (int)((m / Nz) % N);
+    const int x = (int)(m / ((size_t)Nz * N));
+    const int nx = x <= N / 2 ? x : x - N;
+    const int ny = y <= N / 2 ? y : y - N;
+    const int nz = z;
+    cufftComplex in[D];
+#pragma unroll
+    for (int j = 0; j < D; ++j) in[j] = mesh[(size_t)j * modes + m];
+    const float k2 = kf * kf * (float)(nx * nx + ny * ny + nz * nz);
+    if (k2 == 0.f) {
+#pragma unroll
+      for (int i = 0; i < D; ++i) mesh[(size_t)i * modes + m] = make_cuComplex(0.f, 0.f);
+      continue;
+    }
+    const float sx = sinc_pi(nx, N), sy = sinc_pi(ny, N), sz = sinc_pi(nz, N);
+    const float w = sx * sx * sy * sy * sz * sz;
+    const float filt = expf(-k2 * rs2) / (w * w) * pref;
+    const float newton = 1.f / k2;
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+      float re = 0.f, im = 0.f;
+#pragma unroll
+      for (int j = 0; j < D; ++j) {
+        float K = newton;
+        if (law.yfac[i][j] != 0.f) K += law.yfac[i][j] / (k2 + law.mu2[i][j]);
+        K *= law.G[i][j] * filt;
+        re = fmaf(K, in[j].x, re);
+        im = fmaf(K, in[j].y, im);
+      }
+      mesh[(size_t)i * modes + m] = make_cuComplex(re, im);
+    }
+  }
+}
+
+// -grad phi_i by 4-point central differences at the 8 CIC corners of each
+// particle of passive species i, interpolated with the CIC weights.
+__global__ void k_pm_interp(int64_t n, const double* __restrict__ spos,
+                            const uint8_t* __restrict__ stype, const uint32_t* __restrict__ perm,
+                            const float* __restrict__ phi, int N, double cells_per_len,
+                            float inv_h, float* __restrict__ acc, int accumulate) {
+  const size_t N3 = (size_t)N * N * N;
+  const int mask = N - 1;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const double ux = spos[k] * cells_per_len, uy = spos[n + k] * cells_per_len,
+                 uz = spos[2 * n + k] * cells_per_len;
+    const double fx0 = floor(ux), fy0 = floor(uy), fz0 = floor(uz);
+    const float f[3] = {(float)(ux - fx0), (float)(uy - fy0), (float)(uz - fz0)};
+    const int i0[3] = {(int)fx0, (int)fy0, (int)fz0};
+    const float* P = phi + (size_t)stype[k] * N3;
+    auto at = [&](int x, int y, int z) {
+      return __ldg(P + ((size_t)(x & mask) * N + (y & mask)) * N + (z & mask));
+    };
+    float a[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const int dx = c >> 2, dy = (c >> 1) & 1, dz = c & 1;
+      const float w = (dx ? f[0] : 1.f - f[0]) * (dy ? f[1] : 1.f - f[1]) * (dz ? f[2] : 1.f - f[2]);
+      const int x = i0[0] + dx, y = i0[1] + dy, z = i0[2] + dz;
+      const float gx = (2.f / 3.f) * (at(x + 1, y, z) - at(x - 1, y, z)) -
+                       (1.f / 12.f) * (at(x + 2, y, z) - at(x - 2, y, z));
+      const float gy = (2.f / 3.f) * (at(x, y + 1, z) - at(x, y - 1, z)) -
+                       (1.f / 12.f) * (at(x, y + 2, z) - at(x, y - 2, z));
+      const float gz = (2.f / 3.f) * (at(x, y, z + 1) - at(x, y, z - 1)) -
+                       (1.f / 12.f) * (at(x, y, z + 2) - at(x, y, z - 2));
+      a[0] = fmaf(w, gx, a[0]);
+      a[1] = fmaf(w, gy, a[1]);
+      a[2] = fmaf(w, gz, a[2]);
+    }
+    const uint32_t i = perm[k];
+    const float s = -inv_h;
+    if (accumulate) {
+      acc[i] += s * a[0];
+      acc[n + i] += s * a[1];
+      acc[2 * n + i] += s * a[2];
+    } else {
+      acc[i] = s * a[0];
+      acc[n + i] = s * a[1];
+      acc[2 * n + i] = s * a[2];
+    }
+  }
+}
+
+static int pm_setup(ng_ctx* c) {
+  const int N = c->p.pm_mesh, D = c->p.D;
+  if (c->pm_ready && c->pm_n == N) return NG_OK;
+  const size_t N3 = (size_t)N * N * N;
+  const size_t modes = (size_t)N * N * (N / 2 + 1);
+  NG_TRY(ensure(c, c->rho, (size_t)D * N3 * sizeof(float)));
+  NG_TRY(ensure(c, c->rhok, (size_t)D * modes * sizeof(cufftComplex)));
+  NG_TRY(ensure(c, c->phi, (size_t)D * N3 * sizeof(float)));
+  int dims[3] = {N, N, N};
+  if (c->plan_r2c) cufftDestroy(c->plan_r2c);
+  if (c->plan_c2r) cufftDestroy(c->plan_c2r);
+  c->plan_r2c = c->plan_c2r = 0;
+  if (cufftPlanMany(&c->plan_r2c, 3, dims, nullptr, 1, (int)N3, nullptr, 1, (int)modes,
+                    CUFFT_R2C, D) != CUFFT_SUCCESS ||
+      cufftPlanMany(&c->plan_c2r, 3, dims, nullptr, 1, (int)modes, nullptr, 1, (int)N3,
+                    CUFFT_C2R, D) != CUFFT_SUCCESS)
+    return fail(c, NG_ECUDA, "cuFFT plan creation failed for a %d^3 mesh, batch %d", N, D);
+  c->pm_ready = 1;
+  c->pm_n = N;
+  return NG_OK;
+}
+
+int pm_force(ng_ctx* c, float* acc, bool accumulate) {
+  const int N = c->p.pm_mesh, D = c->p.D;
+  if (N <= 0) return fail(c, NG_ESTATE, "pm_mesh is 0: no long-range step configured");
+  NG_TRY(pm_setup(c));
+  const size_t N3 = (size_t)N * N * N;
+  const double L = c->L;
+  NG_CUDA(c, cudaMemsetAsync(c->rho.p, 0, (size_t)D * N3 * sizeof(float), c->stream));
+  const int grid = device_grid(c, 8);
+  c->launches += 3;   // deposit, k-space, interpolation (cuFFT kernels are the library's)
+  k_cic_deposit<<<grid, 256, 0, c->stream>>>(c->n, as<uint32_t>(c->tperm), as<double>(c->spos),
+                                            as<float>(c->smass), as<uint8_t>(c->stype), N,
+                                            (double)N / L, as<float>(c->rho));
+  NG_CUDA(c, cudaGetLastError());
+  if (cufftSetStream(c->plan_r2c, c->stream) != CUFFT_SUCCESS ||
+      cufftSetStream(c->plan_c2r, c->stream) != CUFFT_SUCCESS)
+    return fail(c, NG_ECUDA, "cufftSetStream failed");
+  if (cufftExecR2C(c->plan_r2c, as<cufftReal>(c->rho), as<cufftComplex>(c->rhok)) != CUFFT_SUCCESS)
+    return fail(c, NG_ECUDA, "cufftExecR2C failed");
+  PmLaw law{};
+  for (int i = 0; i < kMaxD; ++i)
+    for (int j = 0; j < kMaxD; ++j) {
+      law.G[i][j] = (float)c->p.G[i][j];
+      if (i < D && j < D && c->p.law[i][j] == NG_YUKAWA) {
+        const double mu = 1.0 / c->p.yuk_l[i][j];
+        law.mu2[i][j] = (float)(mu * mu);
+        law.yfac[i][j] = (float)(c->p.yuk_a[i][j] * std::exp(-mu * mu * c->rs * c->rs));
+      }
+    }
+  const float kf = (float)(2.0 * M_PI / L);
+  const float pref = (float)(-4.0 * M_PI / (L * L * L));
+  const float rs2 = (float)(c->rs * c->rs);
+  cufftComplex* mk = as<cufftComplex>(c->rhok);
+  switch (D) {
+    case 1: k_kspace<1><<<grid, 256, 0, c->stream>>>(mk, N, kf, rs2, pref, law); break;
+    case 2: k_kspace<2><<<grid, 256, 0, c->stream>>>(mk, N, kf, rs2, pref, law); break;
+    case 3: k_kspace<3><<<grid, 256, 0, c->stream>>>(mk, N, kf, rs2, pref, law); break;
+    case 4: k_kspace<4><<<grid, 256, 0, c->stream>>>(mk, N, kf, rs2, pref, law); break;
+    case 5: k_kspace<5><<<grid, 256, 0, c->stream>>>(mk, N, kf, rs2, pref, law); break;
+    default: k_kspace<6><<<grid, 256, 0, c->stream>>>(mk, N, kf, rs2, pref, law); break;
+  }
+  NG_CUDA(c, cudaGetLastError());
+  if (cufftExecC2R(c->plan_c2r, mk, as<cufftReal>(c->phi)) != CUFFT_SUCCESS)
+    return fail(c, NG_ECUDA, "cufftExecC2R failed");
+  k_pm_interp<<<grid, 256, 0, c->stream>>>(c->n, as<double>(c->spos), as<uint8_t>(c->stype),
+                                          as<uint32_t>(c->vals_a), as<float>(c->phi), N,
+                                          (double)N / L, (float)(N / L), acc, accumulate ? 1 : 0);
+  NG_CUDA(c, cudaGetLastError());
+  return NG_OK;
+}
+
+}  // namespace ng

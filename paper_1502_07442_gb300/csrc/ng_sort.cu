@@ -1,0 +1,311 @@
+// Sort stage (Sec. 2.4): periodic wrap, 63-bit Morton+type keys, stable LSD
+// radix sort, one gather of the particle data into sorted order, and the
+// type-major order (bodies grouped by type, each type in key order).
+#include <cstdarg>
+#include <cstdio>
+
+#include "ng_internal.cuh"
+
+namespace ng {
+
+// ------------------------------------------------------------ block scan
+
+template <int THREADS>
+__device__ __forceinline__ uint32_t block_inclusive_scan(uint32_t v, uint32_t* warp_tot,
+                                                         uint32_t* total) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t t = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += t;
+  }
+  if (lane == 31) warp_tot[wid] = v;
+  __syncthreads();
+  if (wid == 0) {
+    uint32_t w = lane < THREADS / 32 ? warp_tot[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t t = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += t;
+    }
+    if (lane < THREADS / 32) warp_tot[lane] = w;
+    if (lane == THREADS / 32 - 1) *total = w;
+  }
+  __syncthreads();
+  if (wid > 0) v += warp_tot[wid - 1];
+  return v;
+}
+
+constexpr int kScanThreads = 1024;
+constexpr int kScanBlocks = 256;
+
+__device__ __forceinline__ int64_t scan_len(int64_t bound, const uint32_t* d_len) {
+  if (!d_len) return bound;
+  const int64_t l = (int64_t)*d_len;
+  return l < bound ? l : bound;
+}
+
+__global__ void __launch_bounds__(kScanThreads)
+k_scan_partial(const uint32_t* __restrict__ in, int64_t bound, const uint32_t* d_len,
+               uint32_t* part) {
+  const int64_t len = scan_len(bound, d_len);
+  const int64_t chunk = (len + gridDim.x - 1) / gridDim.x;
+  const int64_t b0 = (int64_t)blockIdx.x * chunk;
+  const int64_t b1 = b0 + chunk < len ? b0 + chunk : len;
+  uint32_t s = 0;
+  for (int64_t i = b0 + threadIdx.x; i < b1; i += blockDim.x) s += in[i];
+#pragma unroll
+  for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  __shared__ uint32_t ws[32];
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    s = threadIdx.x < blockDim.x / 32 ? ws[threadIdx.x] : 0;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+  }
+}
+
+__global__ void __launch_bounds__(kScanThreads)
+k_scan_final(const uint32_t* in, uint32_t* out, int64_t bound, const uint32_t* d_len,
+             const uint32_t* __restrict__ part, uint32_t* d_total) {
+  __shared__ uint32_t warp_tot[32];
+  __shared__ uint32_t tile_total;
+  __shared__ uint32_t off;
+  const int64_t len = scan_len(bound, d_len);
+  const int64_t chunk = (len + gridDim.x - 1) / gridDim.x;
+  const int64_t b0 = (int64_t)blockIdx.x * chunk;
+  const int64_t b1 = b0 + chunk < len ? b0 + chunk : len;
+  if (threadIdx.x < 32) {
+    uint32_t s = 0;
+    for (int j = threadIdx.x; j < (int)blockIdx.x; j += 32) s += part[j];
+#pragma unroll
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) off = s;
+  }
+  __syncthreads();
+  uint32_t carry = off;
+  for (int64_t base = b0; base < b1; base += kScanThreads) {
+    const int64_t i = base + threadIdx.x;
+    const uint32_t v = i < b1 ? in[i] : 0u;
+    const uint32_t inc = block_inclusive_scan<kScanThreads>(v, warp_tot, &tile_total);
+    if (i < b1) out[i] = carry + inc - v;
+    __syncthreads();
+    carry += tile_total;
+    __syncthreads();
+  }
+  if (d_total && blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) *d_total = carry;
+}
+
+int scan_u32(ng_ctx* c, const uint32_t* in, uint32_t* out, int64_t len, const uint32_t* d_len,
+             uint32_t* d_total) {
+  NG_TRY(ensure(c, c->scan_part, kScanBlocks * sizeof(uint32_t)));
+  uint32_t* part = as<uint32_t>(c->scan_part);
+  k_scan_partial<<<kScanBlocks, kScanThreads, 0, c->stream>>>(in, len, d_len, part);
+  k_scan_final<<<kScanBlocks, kScanThreads, 0, c->stream>>>(in, out, len, d_len, part, d_total);
+  c->launches += 2;
+  NG_CUDA(c, cudaGetLastError());
+  return NG_OK;
+}
+
+// --------------------------------------------------------------- keys
+
+// Periodic wrap x - L floor(x / L) with each operation rounded separately
+// (no fused multiply-add), so that the host reference rounds identically.
+__device__ __forceinline__ double wrap_box(double x, double L) {
+  const double f = floor(__ddiv_rn(x, L));
+  return __dsub_rn(x, __dmul_rn(L, f));
+}
+
+__device__ __forceinline__ uint64_t quantise20(double w, double L) {
+  double q = floor(__dmul_rn(__ddiv_rn(w, L), 1048576.0));
+  q = q < 0.0 ? 0.0 : q;
+  q = q > 1048575.0 ? 1048575.0 : q;
+  return (uint64_t)q;
+}
+
+// Spread the low 21 bits of v to every third bit.
+__device__ __forceinline__ uint64_t spread3(uint64_t v) {
+  v &= 0x1fffffull;
+  v = (v | (v << 32)) & 0x1f00000000ffffull;
+  v = (v | (v << 16)) & 0x1f0000ff0000ffull;
+  v = (v | (v << 8)) & 0x100f00f00f00f00full;
+  v = (v | (v << 4)) & 0x10c30c30c30c30c3ull;
+  v = (v | (v << 2)) & 0x1249249249249249ull;
+  return v;
+}
+
+__global__ void k_keys(int64_t n, const double* __restrict__ pos, const uint8_t* __restrict__ type,
+                       double L, uint64_t* __restrict__ keys, uint32_t* __restrict__ idx) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t qx = quantise20(wrap_box(pos[i], L), L);
+    const uint64_t qy = quantise20(wrap_box(pos[n + i], L), L);
+    const uint64_t qz = quantise20(wrap_box(pos[2 * n + i], L), L);
+    const uint64_t m = (spread3(qx) << 2) | (spread3(qy) << 1) | spread3(qz);
+    keys[i] = (m << 3) | (uint64_t)(type[i] & 7);
+    idx[i] = (uint32_t)i;
+  }
+}
+
+// ---------------------------------------------------------- radix sort
+
+constexpr int kRsThreads = 256;
+constexpr int kRsItems = 16;                       // keys per lane
+constexpr int kRsWarps = kRsThreads / 32;
+constexpr int kRsTile = kRsThreads * kRsItems;     // 4096 keys per block
+
+__global__ void __launch_bounds__(kRsThreads)
+k_rs_hist(const uint64_t* __restrict__ keys, int64_t n, int shift, uint32_t mask,
+          uint32_t* __restrict__ hist, int nblocks) {
+  __shared__ uint32_t cnt[256];
+  cnt[threadIdx.x] = 0;
+  __syncthreads();
+  const int64_t t0 = (int64_t)blockIdx.x * kRsTile;
+  for (int j = threadIdx.x; j < kRsTile; j += kRsThreads) {
+    const int64_t i = t0 + j;
+    if (i < n) atomicAdd(&cnt[(uint32_t)(keys[i] >> shift) & mask], 1u);
+  }
+  __syncthreads();
+  hist[(int64_t)threadIdx.x * nblocks + blockIdx.x] = cnt[threadIdx.x];
+}
+
+// Stable scatter of one digit: each warp ranks its contiguous sub-tile in
+// order (match_any groups equal digits), warps are then ordered per digit.
+__global__ void __launch_bounds__(kRsThreads)
+k_rs_scatter(const uint64_t* __restrict__ kin, const uint32_t* __restrict__ vin,
+             uint64_t* __restrict__ kout, uint32_t* __restrict__ vout, int64_t n, int shift,
+             uint32_t mask, const uint32_t* __restrict__ offs, int nblocks) {
+  __shared__ uint32_t wcnt[kRsWarps][256];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int j = threadIdx.x; j < kRsWarps * 256; j += kRsThreads) (&wcnt[0][0])[j] = 0;
+  __syncthreads();
+  const int64_t sub0 = (int64_t)blockIdx.x * kRsTile + (int64_t)w * (kRsTile / kRsWarps);
+  const uint32_t lt = (1u << lane) - 1u;
+  uint64_t k[kRsItems];
+  uint32_t v[kRsItems], rank[kRsItems];
+#pragma unroll
+  for (int it = 0; it < kRsItems; ++it) {
+    const int64_t i = sub0 + it * 32 + lane;
+    const bool valid = i < n;
+    k[it] = valid ? kin[i] : 0ull;
+    v[it] = valid ? vin[i] : 0u;
+    const uint32_t d = (uint32_t)(k[it] >> shift) & mask;
+    const uint32_t peers = __match_any_sync(0xffffffffu, valid ? d : 0xffffffffu);
+    uint32_t prior = 0;
+    if (valid) prior = wcnt[w][d];
+    __syncwarp();
+    rank[it] = prior + __popc(peers & lt);
+    if (valid && (peers & lt) == 0) wcnt[w][d] = prior + __popc(peers);
+    __syncwarp();
+  }
+  __syncthreads();
+  {
+    uint32_t run = offs[(int64_t)threadIdx.x * nblocks + blockIdx.x];
+#pragma unroll
+    for (int ww = 0; ww < kRsWarps; ++ww) {
+      const uint32_t t = wcnt[ww][threadIdx.x];
+      wcnt[ww][threadIdx.x] = run;
+      run += t;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int it = 0; it < kRsItems; ++it) {
+    const int64_t i = sub0 + it * 32 + lane;
+    if (i < n) {
+      const uint32_t d = (uint32_t)(k[it] >> shift) & mask;
+      const uint32_t dst = wcnt[w][d] + rank[it];
+      kout[dst] = k[it];
+      vout[dst] = v[it];
+    }
+  }
+}
+
+static int radix_pass(ng_ctx* c, const uint64_t* kin, const uint32_t* vin, uint64_t* kout,
+                      uint32_t* vout, int64_t n, int shift, uint32_t mask) {
+  const int nblocks = (int)((n + kRsTile - 1) / kRsTile);
+  uint32_t* hist = as<uint32_t>(c->blockhist);
+  k_rs_hist<<<nblocks, kRsThreads, 0, c->stream>>>(kin, n, shift, mask, hist, nblocks);
+  NG_TRY(scan_u32(c, hist, hist, (int64_t)256 * nblocks, nullptr, nullptr));
+  k_rs_scatter<<<nblocks, kRsThreads, 0, c->stream>>>(kin, vin, kout, vout, n, shift, mask, hist,
+                                                     nblocks);
+  c->launches += 2;
+  NG_CUDA(c, cudaGetLastError());
+  return NG_OK;
+}
+
+// -------------------------------------------------------------- gather
+
+__global__ void k_gather(int64_t n, const uint32_t* __restrict__ perm,
+                         const double* __restrict__ pos, const uint8_t* __restrict__ type,
+                         const float* __restrict__ mass, double L, int D,
+                         double* __restrict__ spos, float* __restrict__ smass,
+                         uint8_t* __restrict__ stype, uint32_t* status) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t i = perm[k];
+    spos[k] = wrap_box(pos[i], L);
+    spos[n + k] = wrap_box(pos[n + i], L);
+    spos[2 * n + k] = wrap_box(pos[2 * n + i], L);
+    smass[k] = mass[i];
+    const uint8_t ti = type[i];
+    if (ti >= D) atomicOr(&status[ST_FLAGS], (uint32_t)SF_BAD_TYPE);
+    stype[k] = ti < D ? ti : 0;    // out-of-range species: flagged, never used as an index
+  }
+}
+
+__global__ void k_iota(int64_t n, uint32_t* out) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x)
+    out[k] = (uint32_t)k;
+}
+
+int device_grid(ng_ctx* c, int per_sm) { return c->nsm * per_sm; }
+
+int sort_bodies(ng_ctx* c, int64_t n, const double* pos, const uint8_t* type, const float* mass) {
+  const int nblocks = (int)((n + kRsTile - 1) / kRsTile);
+  NG_TRY(ensure(c, c->keys_a, n * 8));
+  NG_TRY(ensure(c, c->keys_b, n * 8));
+  NG_TRY(ensure(c, c->vals_a, n * 4));
+  NG_TRY(ensure(c, c->vals_b, n * 4));
+  NG_TRY(ensure(c, c->blockhist, (size_t)256 * nblocks * 4));
+  NG_TRY(ensure(c, c->spos, n * 24));
+  NG_TRY(ensure(c, c->smass, n * 4));
+  NG_TRY(ensure(c, c->stype, n));
+  NG_TRY(ensure(c, c->tperm, n * 4));
+  uint64_t *ka = as<uint64_t>(c->keys_a), *kb = as<uint64_t>(c->keys_b);
+  uint32_t *va = as<uint32_t>(c->vals_a), *vb = as<uint32_t>(c->vals_b);
+  const int grid = device_grid(c, 8);
+  k_keys<<<grid, 256, 0, c->stream>>>(n, pos, type, c->L, ka, va);
+  c->launches += 2;   // keys + gather
+  NG_CUDA(c, cudaGetLastError());
+  // 8 passes of 8 bits: the result returns to (ka, va)
+  for (int pass = 0; pass < 8; ++pass) {
+    const bool even = (pass & 1) == 0;
+    NG_TRY(radix_pass(c, even ? ka : kb, even ? va : vb, even ? kb : ka, even ? vb : va, n,
+                      8 * pass, 0xffu));
+  }
+  k_gather<<<grid, 256, 0, c->stream>>>(n, va, pos, type, mass, c->L, c->p.D,
+                                        as<double>(c->spos), as<float>(c->smass),
+                                        as<uint8_t>(c->stype), as<uint32_t>(c->status));
+  NG_CUDA(c, cudaGetLastError());
+  return NG_OK;
+}
+
+// Type-major order: one stable radix pass on the species bits of the sorted
+// keys. tperm[j] = sorted index of the j-th body in type-major order.
+int type_order(ng_ctx* c) {
+  const int64_t n = c->n;
+  const int grid = device_grid(c, 8);
+  uint64_t *ka = as<uint64_t>(c->keys_a), *kb = as<uint64_t>(c->keys_b);
+  uint32_t* vb = as<uint32_t>(c->vals_b);
+  k_iota<<<grid, 256, 0, c->stream>>>(n, vb);
+  c->launches += 1;
+  NG_CUDA(c, cudaGetLastError());
+  NG_TRY(radix_pass(c, ka, vb, kb, as<uint32_t>(c->tperm), n, 0, 7u));
+  return NG_OK;
+}
+
+}  // namespace ng

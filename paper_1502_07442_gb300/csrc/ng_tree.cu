@@ -1,0 +1,405 @@
+// Tree stage (Sec. 2.2): canonical Morton-prefix octree built breadth-first
+// one level per launch (node ranges stay on the device, no host round trip),
+// per-node per-species monopoles reduced bottom-up in double precision with
+// warp shuffles, and the walk groups.
+//
+// Canonical tree: nodes are the non-empty Morton cells reachable from the
+// root; a cell is a leaf iff it holds <= leaf_size bodies or is at level 20;
+// children are the non-empty octants in octant order; nodes are numbered
+// level by level, and within a level in key order.
+#include "ng_internal.cuh"
+
+namespace ng {
+
+struct Levels {
+  uint32_t* start;   // [kMaxLevel + 2]: first node of each level, then end
+  uint32_t* count;   // [kMaxLevel + 1]: nodes per level
+};
+
+__device__ __forceinline__ Levels levels_of(uint32_t* status) {
+  return Levels{status + ST_LEVELS, status + ST_LEVELS + kMaxLevel + 2};
+}
+
+__global__ void k_tree_init(uint32_t* status, int64_t n, uint8_t* level, uint64_t* prefix,
+                            uint32_t* first, uint32_t* count) {
+  if (threadIdx.x == 0) {
+    Levels lv = levels_of(status);
+    for (int l = 0; l <= kMaxLevel + 1; ++l) lv.start[l] = 1;
+    for (int l = 0; l <= kMaxLevel; ++l) lv.count[l] = 0;
+    lv.start[0] = 0;
+    lv.start[1] = 1;
+    lv.count[0] = 1;
+    status[ST_NODES_NEEDED] = 1;
+    status[ST_NGROUPS] = 0;
+    level[0] = 0;
+    prefix[0] = 0;
+    first[0] = 0;
+    count[0] = (uint32_t)n;
+  }
+}
+
+// First index in [lo, hi) whose child octant at shift is >= oct.
+__device__ __forceinline__ uint32_t octant_bound(const uint64_t* __restrict__ keys, uint32_t lo,
+                                                 uint32_t hi, int shift, uint32_t oct) {
+  while (lo < hi) {
+    const uint32_t mid = lo + ((hi - lo) >> 1);
+    const uint32_t o = (uint32_t)((keys[mid] >> (3 + shift)) & 7ull);
+    if (o < oct) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+__global__ void k_tree_count(int lvl, uint32_t* status, int64_t cap, int leaf_size,
+                             const uint64_t* __restrict__ keys, const uint32_t* __restrict__ first,
+                             const uint32_t* __restrict__ count, uint8_t* nchild,
+                             uint32_t* tmp) {
+  Levels lv = levels_of(status);
+  const uint32_t s = lv.start[lvl];
+  uint32_t e = lv.start[lvl + 1];
+  if (e > cap) e = (uint32_t)cap;
+  const int shift = 3 * (kMaxLevel - (lvl + 1));
+  for (uint32_t k = s + blockIdx.x * blockDim.x + threadIdx.x; k < e;
+       k += gridDim.x * blockDim.x) {
+    const uint32_t f = first[k], c = count[k];
+    uint32_t nch = 0;
+    if ((int)c > leaf_size && lvl < kMaxLevel) {
+      uint32_t prev = f;
+      for (uint32_t o = 1; o <= 8; ++o) {
+        const uint32_t b = o < 8 ? octant_bound(keys, prev, f + c, shift, o) : f + c;
+        nch += b > prev;
+        prev = b;
+      }
+    }
+    nchild[k] = (uint8_t)nch;
+    tmp[k - s] = nch;
+  }
+}
+
+__global__ void k_tree_emit(int lvl, uint32_t* status, int64_t cap,
+                            const uint64_t* __restrict__ keys, uint8_t* level, uint64_t* prefix,
+                            uint32_t* first, uint32_t* count, const uint8_t* __restrict__ nchild,
+                            uint32_t* child, const uint32_t* __restrict__ off) {
+  Levels lv = levels_of(status);
+  const uint32_t s = lv.start[lvl];
+  uint32_t e = lv.start[lvl + 1];
+  if (e > cap) e = (uint32_t)cap;
+  const uint32_t next0 = lv.start[lvl + 1];
+  const uint32_t total = lv.count[lvl + 1];
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    const uint64_t end = (uint64_t)next0 + total;
+    lv.start[lvl + 2] = (uint32_t)(end < 0xffffffffull ? end : 0xffffffffull);
+    // only levels up to the first overflow are counted correctly: the node
+    // estimate is taken there and never from the truncated levels below it
+    if (!(status[ST_FLAGS] & SF_NODE_OVERFLOW)) {
+      status[ST_NODES_NEEDED] = (uint32_t)(end < 0xffffffffull ? end : 0xffffffffull);
+      if (end > (uint64_t)cap) status[ST_FLAGS] |= (uint32_t)SF_NODE_OVERFLOW;
+    }
+  }
+  const int shift = 3 * (kMaxLevel - (lvl + 1));
+  for (uint32_t k = s + blockIdx.x * blockDim.x + threadIdx.x; k < e;
+       k += gridDim.x * blockDim.x) {
+    const uint32_t nch = nchild[k];
+    if (nch == 0) {
+      child[k] = 0xffffffffu;
+      continue;
+    }
+    const uint32_t c0 = next0 + off[k - s];
+    child[k] = c0;
+    const uint32_t f = first[k], c = count[k];
+    const uint64_t pre = prefix[k];
+    uint32_t prev = f, j = 0;
+    for (uint32_t o = 1; o <= 8; ++o) {
+      const uint32_t b = o < 8 ? octant_bound(keys, prev, f + c, shift, o) : f + c;
+      if (b > prev) {
+        const uint64_t id = (uint64_t)c0 + j;
+        if (id < (uint64_t)cap) {
+          level[id] = (uint8_t)(lvl + 1);
+          prefix[id] = (pre << 3) | (uint64_t)(o - 1);
+          first[id] = prev;
+          count[id] = b - prev;
+        }
+        ++j;
+      }
+      prev = b;
+    }
+  }
+}
+
+int build_octree(ng_ctx* c) {
+  const int64_t n = c->n;
+  const int64_t cap = c->cap_nodes;
+  uint32_t* st = as<uint32_t>(c->status);
+  uint8_t* level = as<uint8_t>(c->n_level);
+  uint64_t* prefix = as<uint64_t>(c->n_prefix);
+  uint32_t* first = as<uint32_t>(c->n_first);
+  uint32_t* count = as<uint32_t>(c->n_count);
+  uint8_t* nchild = as<uint8_t>(c->n_nchild);
+  uint32_t* child = as<uint32_t>(c->n_child);
+  uint32_t* tmp = as<uint32_t>(c->n_tmp);
+  const uint64_t* keys = as<uint64_t>(c->keys_a);
+  const int leaf = c->p.leaf_size;
+  k_tree_init<<<1, 32, 0, c->stream>>>(st, n, level, prefix, first, count);
+  c->launches += 1 + (kMaxLevel + 1) + kMaxLevel;   // init, counts, emits (scans count themselves)
+  const int grid = device_grid(c, 4);
+  for (int l = 0; l <= kMaxLevel; ++l) {
+    k_tree_count<<<grid, 256, 0, c->stream>>>(l, st, cap, leaf, keys, first, count, nchild, tmp);
+    if (l == kMaxLevel) break;
+    // children per level: exclusive scan of the per-node child counts
+    uint32_t* lvcount = st + ST_LEVELS + kMaxLevel + 2;
+    NG_TRY(scan_u32(c, tmp, tmp, cap, lvcount + l, lvcount + l + 1));
+    k_tree_emit<<<grid, 256, 0, c->stream>>>(l, st, cap, keys, level, prefix, first, count,
+                                             nchild, child, tmp);
+  }
+  NG_CUDA(c, cudaGetLastError());
+  return NG_OK;
+}
+
+// --------------------------------------------------------- monopoles
+
+__device__ __forceinline__ uint32_t compact3(uint64_t v) {
+  v &= 0x1249249249249249ull;
+  v = (v ^ (v >> 2)) & 0x10c30c30c30c30c3ull;
+  v = (v ^ (v >> 4)) & 0x100f00f00f00f00full;
+  v = (v ^ (v >> 8)) & 0x1f0000ff0000ffull;
+  v = (v ^ (v >> 16)) & 0x1f00000000ffffull;
+  v = (v ^ (v >> 32)) & 0x1fffffull;
+  return (uint32_t)v;
+}
+
+// Centre (box units) of a node from its level and Morton prefix.
+__device__ __forceinline__ void node_centre(int lvl, uint64_t pre, double c[3], double* side) {
+  const double s = 1.0 / (double)(1u << lvl);
+  c[0] = ((double)compact3(pre >> 2) + 0.5) * s;
+  c[1] = ((double)compact3(pre >> 1) + 0.5) * s;
+  c[2] = ((double)compact3(pre) + 0.5) * s;
+  *side = s;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ uint32_t warp_sum_u(uint32_t v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+struct MonoArgs {
+  const uint8_t* level;
+  const uint64_t* prefix;
+  const uint32_t* first;
+  const uint32_t* count;
+  const uint8_t* nchild;
+  const uint32_t* child;
+  const double* spos;      // [3][n] physical
+  const float* smass;
+  const uint8_t* stype;
+  double* m64;             // [node][D][4]: mass, sum m x, sum m y, sum m z (box units)
+  uint32_t* cnt;           // [node][D]
+  float4* geo;
+  float4* com;
+  int4* link;
+  float4* mono;            // [node][D]
+  float4* body;            // [sorted body]
+  uint32_t* bleaf;         // [sorted body] leaf index
+  uint32_t* status;
+  int64_t n, cap;
+  double invL;
+};
+
+// One warp per node of level lvl: leaves reduce their bodies (and write the
+// body records), internal nodes reduce their children.
+template <int D>
+__global__ void __launch_bounds__(256) k_monopoles(int lvl, MonoArgs a) {
+  if (a.status[ST_FLAGS] & SF_NODE_OVERFLOW) return;   // truncated tree: do not read it
+  Levels lv = levels_of(a.status);
+  const uint32_t s = lv.start[lvl];
+  uint32_t e = lv.start[lvl + 1];
+  if (e > a.cap) e = (uint32_t)a.cap;
+  const int lane = threadIdx.x & 31;
+  const uint32_t wglobal = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t wcount = (gridDim.x * blockDim.x) >> 5;
+  for (uint32_t k = s + wglobal; k < e; k += wcount) {
+    double cen[3], side;
+    node_centre(lvl, a.prefix[k], cen, &side);
+    double sm[D], sx[D], sy[D], sz[D];
+    uint32_t sc[D];
+#pragma unroll
+    for (int t = 0; t < D; ++t) { sm[t] = sx[t] = sy[t] = sz[t] = 0.0; sc[t] = 0; }
+    const uint32_t nch = a.nchild[k];
+    const uint32_t f = a.first[k], c = a.count[k];
+    if (nch == 0) {
+      for (uint32_t b = f + lane; b < f + c; b += 32) {
+        const double x = a.spos[b] * a.invL, y = a.spos[a.n + b] * a.invL,
+                     z = a.spos[2 * a.n + b] * a.invL;
+        const float m = a.smass[b];
+        const int t = a.stype[b];
+        a.body[b] = make_float4((float)(x - cen[0]), (float)(y - cen[1]), (float)(z - cen[2]), m);
+        a.bleaf[b] = k;
+        const double md = (double)m;
+#pragma unroll
+        for (int q = 0; q < D; ++q) {
+          const bool on = (t == q);
+          sm[q] += on ? md : 0.0;
+          sx[q] += on ? md * x : 0.0;
+          sy[q] += on ? md * y : 0.0;
+          sz[q] += on ? md * z : 0.0;
+          sc[q] += on ? 1u : 0u;
+        }
+      }
+    } else if ((uint32_t)lane < nch) {
+      const uint32_t ch = a.child[k] + lane;
+#pragma unroll
+      for (int q = 0; q < D; ++q) {
+        const double* src = a.m64 + ((size_t)ch * D + q) * 4;
+        sm[q] = src[0];
+        sx[q] = src[1];
+        sy[q] = src[2];
+        sz[q] = src[3];
+        sc[q] = a.cnt[(size_t)ch * D + q];
+      }
+    }
+    double mt = 0, xt = 0, yt = 0, zt = 0;
+#pragma unroll
+    for (int q = 0; q < D; ++q) {
+      sm[q] = warp_sum(sm[q]);
+      sx[q] = warp_sum(sx[q]);
+      sy[q] = warp_sum(sy[q]);
+      sz[q] = warp_sum(sz[q]);
+      sc[q] = warp_sum_u(sc[q]);
+      mt += sm[q];
+      xt += sx[q];
+      yt += sy[q];
+      zt += sz[q];
+    }
+    if (lane < D) {
+      // lane q writes species q (registers indexed by the unrolled loop)
+#pragma unroll
+      for (int q = 0; q < D; ++q) {
+        if (lane == q) {
+          double* dst = a.m64 + ((size_t)k * D + q) * 4;
+          dst[0] = sm[q];
+          dst[1] = sx[q];
+          dst[2] = sy[q];
+          dst[3] = sz[q];
+          a.cnt[(size_t)k * D + q] = sc[q];
+          float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (sm[q] > 0.0)
+            r = make_float4((float)(sx[q] / sm[q] - cen[0]), (float)(sy[q] / sm[q] - cen[1]),
+                            (float)(sz[q] / sm[q] - cen[2]), (float)sm[q]);
+          a.mono[(size_t)k * D + q] = r;
+        }
+      }
+    }
+    if (lane == 31) {
+      a.geo[k] = make_float4((float)cen[0], (float)cen[1], (float)cen[2], (float)(0.5 * side));
+      float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (mt > 0.0)
+        r = make_float4((float)(xt / mt - cen[0]), (float)(yt / mt - cen[1]),
+                        (float)(zt / mt - cen[2]), (float)mt);
+      a.com[k] = r;
+      a.link[k] = make_int4(nch ? (int)a.child[k] : -1, (int)nch, (int)f, (int)c);
+    }
+  }
+}
+
+int reduce_monopoles(ng_ctx* c) {
+  MonoArgs a;
+  a.level = as<uint8_t>(c->n_level);
+  a.prefix = as<uint64_t>(c->n_prefix);
+  a.first = as<uint32_t>(c->n_first);
+  a.count = as<uint32_t>(c->n_count);
+  a.nchild = as<uint8_t>(c->n_nchild);
+  a.child = as<uint32_t>(c->n_child);
+  a.spos = as<double>(c->spos);
+  a.smass = as<float>(c->smass);
+  a.stype = as<uint8_t>(c->stype);
+  a.m64 = as<double>(c->n_m64);
+  a.cnt = as<uint32_t>(c->n_cnt);
+  a.geo = as<float4>(c->n_geo);
+  a.com = as<float4>(c->n_com);
+  a.link = as<int4>(c->n_link);
+  a.mono = as<float4>(c->n_mono);
+  a.body = as<float4>(c->body);
+  a.bleaf = as<uint32_t>(c->bleaf);
+  a.status = as<uint32_t>(c->status);
+  a.n = c->n;
+  a.cap = c->cap_nodes;
+  a.invL = 1.0 / c->L;
+  const int grid = device_grid(c, 8);
+  c->launches += kMaxLevel + 1;
+  for (int l = kMaxLevel; l >= 0; --l) {
+    switch (c->p.D) {
+      case 1: k_monopoles<1><<<grid, 256, 0, c->stream>>>(l, a); break;
+      case 2: k_monopoles<2><<<grid, 256, 0, c->stream>>>(l, a); break;
+      case 3: k_monopoles<3><<<grid, 256, 0, c->stream>>>(l, a); break;
+      case 4: k_monopoles<4><<<grid, 256, 0, c->stream>>>(l, a); break;
+      case 5: k_monopoles<5><<<grid, 256, 0, c->stream>>>(l, a); break;
+      default: k_monopoles<6><<<grid, 256, 0, c->stream>>>(l, a); break;
+    }
+  }
+  NG_CUDA(c, cudaGetLastError());
+  return NG_OK;
+}
+
+// ------------------------------------------------------------- groups
+
+// Walk groups: runs of consecutive sibling cells holding <= G bodies each
+// (and <= G together) whose parent holds more than G; leaves with more than
+// G bodies are cut into chunks of G. Every body lands in exactly one group.
+__global__ void k_groups(uint32_t* status, int64_t cap, int G, const uint32_t* __restrict__ first,
+                         const uint32_t* __restrict__ count, const uint8_t* __restrict__ nchild,
+                         const uint32_t* __restrict__ child, int2* groups, int64_t gcap) {
+  if (status[ST_FLAGS] & SF_NODE_OVERFLOW) return;
+  Levels lv = levels_of(status);
+  uint32_t total = lv.start[kMaxLevel + 1];
+  if (total > cap) total = (uint32_t)cap;
+  auto emit = [&](uint32_t f, uint32_t c) {
+    const uint32_t g = atomicAdd(&status[ST_NGROUPS], 1u);
+    if (g < gcap) groups[g] = make_int2((int)f, (int)c);
+    else atomicOr(&status[ST_FLAGS], (uint32_t)SF_GROUP_OVERFLOW);
+  };
+  auto emit_chunks = [&](uint32_t f, uint32_t c) {
+    for (uint32_t o = 0; o < c; o += G) emit(f + o, c - o < (uint32_t)G ? c - o : G);
+  };
+  for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < total;
+       k += gridDim.x * blockDim.x) {
+    const uint32_t c = count[k];
+    if (k == 0 && c <= (uint32_t)G) { emit(first[0], c); continue; }
+    if (c <= (uint32_t)G) continue;
+    const uint32_t nch = nchild[k];
+    if (nch == 0) {
+      if (k == 0) emit_chunks(first[0], c);
+      continue;
+    }
+    uint32_t bf = 0, bc = 0;
+    for (uint32_t j = 0; j < nch; ++j) {
+      const uint32_t ch = child[k] + j;
+      const uint32_t cc = count[ch];
+      if (cc > (uint32_t)G) {
+        if (bc) { emit(bf, bc); bc = 0; }
+        if (nchild[ch] == 0) emit_chunks(first[ch], cc);
+        continue;
+      }
+      if (bc + cc > (uint32_t)G) { emit(bf, bc); bc = 0; }
+      if (bc == 0) bf = first[ch];
+      bc += cc;
+    }
+    if (bc) emit(bf, bc);
+  }
+}
+
+int build_groups(ng_ctx* c) {
+  NG_TRY(ensure(c, c->groups, (size_t)c->n * sizeof(int2)));
+  c->launches += 1;
+  k_groups<<<device_grid(c, 4), 256, 0, c->stream>>>(
+      as<uint32_t>(c->status), c->cap_nodes, c->p.group_size, as<uint32_t>(c->n_first),
+      as<uint32_t>(c->n_count), as<uint8_t>(c->n_nchild), as<uint32_t>(c->n_child),
+      as<int2>(c->groups), c->n);
+  NG_CUDA(c, cudaGetLastError());
+  return NG_OK;
+}
+
+}  // namespace ng

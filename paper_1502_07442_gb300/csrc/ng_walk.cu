@@ -1,0 +1,517 @@
+// Short-range tree walk (Sec. 2.2) with the TreePM short-range laws of
+// Sec. 2.4.1, evaluated in FP32 on group-relative offsets.
+//
+// One warp walks the tree for one group of up to 32 spatially compact bodies
+// (one body per lane). Nodes are popped 32 at a time from a warp stack in
+// shared memory and classified against the group's bounding box:
+//   skip    the node cube lies >= r_cut from the box;
+//   accept  l < theta * d, d = distance from the box to the node's
+//           all-species centre of mass (and the box is outside the cube):
+//           its D species monopoles go to D per-species record lists;
+//   leaf    a rejected leaf: its bodies go to the list of their species;
+//   open    a rejected internal node: its children are pushed.
+// When a list may overflow, all lists are evaluated: every lane interacts its
+// body with every record. Records and bodies are float4 {x, y, z, m} in
+// table units relative to a dyadic group origin, so node-centre offsets are
+// exact in FP32 and no FP64 enters the inner loop.
+//
+// Inner loop per (body, record): q = |d|^2 + eps^2, inv = rsqrt(q); the
+// table index is rint(q * inv) read from the float bits of q*inv + 2^23; the
+// table holds one linear segment {c0, c1} per index, zero past the cut-off;
+// the force is m * (c0 + t c1) * inv^3 * d, accumulated per active species
+// (the coupling G[s][t] is applied once per body at the end).
+#include "ng_internal.cuh"
+
+namespace ng {
+
+template <int D>
+struct __align__(16) WarpSmem {
+  float4 list[D][kListCap];
+  float4 leafc[32];
+  int leafq[32];
+  int stack[kStackCap];
+};
+
+constexpr float kMagic = 8388608.0f;   // 2^23
+constexpr int kMagicBits = 0x4B000000;
+
+__device__ __forceinline__ float wrap_unit(float d) { return d - rintf(d); }
+
+template <int D>
+__device__ __forceinline__ void evaluate(WarpSmem<D>* ws, int (&lc)[D], const float2* const (&tb)[D],
+                                         float xr, float yr, float zr, float eps2, int clampbits,
+                                         float (&ax)[D], float (&ay)[D], float (&az)[D],
+                                         unsigned long long& nint, int nactive) {
+  __syncwarp();
+#pragma unroll
+  for (int t = 0; t < D; ++t) {
+    const int cnt = lc[t];
+    const float2* __restrict__ T = tb[t];
+    float sx = 0.f, sy = 0.f, sz = 0.f;
+#pragma unroll 4
+    for (int j = 0; j < cnt; ++j) {
+      const float4 r = ws->list[t][j];
+      const float dx = r.x - xr, dy = r.y - yr, dz = r.z - zr;
+      const float q = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
+      const float inv = rsqrtf(q);
+      const float fi = fmaf(q, inv, kMagic);
+      const int bits = min(__float_as_int(fi), clampbits);
+      const float r0 = __int_as_float(bits) - kMagic;
+      const float tt = fmaf(q, inv, -r0);
+      const float2 e = T[bits - kMagicBits];
+      const float g = fmaf(tt, e.y, e.x);
+      const float inv2 = inv * inv;
+      const float f = (r.w * g) * (inv2 * inv);
+      sx = fmaf(f, dx, sx);
+      sy = fmaf(f, dy, sy);
+      sz = fmaf(f, dz, sz);
+    }
+    ax[t] += sx;
+    ay[t] += sy;
+    az[t] += sz;
+    nint += (unsigned long long)cnt * (unsigned long long)nactive;
+    lc[t] = 0;
+  }
+  __syncwarp();
+}
+
+template <int D>
+__global__ void __launch_bounds__(kWalkMaxWarps * 32, 1) k_walk(WalkArgs a, int nlaws) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* tab = reinterpret_cast<float2*>(smem_raw);
+  const int ntab = nlaws * a.tab_entries;
+  for (int i = threadIdx.x; i < ntab; i += blockDim.x) tab[i] = a.tab[i];
+  const size_t tab_bytes = ((size_t)ntab * sizeof(float2) + 15) & ~(size_t)15;
+  WarpSmem<D>* ws = reinterpret_cast<WarpSmem<D>*>(smem_raw + tab_bytes) + (threadIdx.x >> 5);
+  __syncthreads();
+
+  const int lane = threadIdx.x & 31;
+  const uint32_t lt = (1u << lane) - 1u;
+  if (a.status[ST_FLAGS] & SF_NODE_OVERFLOW) return;   // truncated tree: do not walk it
+  const uint32_t nnodes = a.status[ST_LEVELS + kMaxLevel + 1];
+  uint32_t ngroups = a.status[ST_NGROUPS];
+  if (ngroups > (uint32_t)a.n) ngroups = (uint32_t)a.n;
+  const float rc2 = a.rcut_box * a.rcut_box;
+  const float s_tab = (float)a.inv_dr;
+  const int clampbits = kMagicBits + a.ncut;
+  unsigned long long nint = 0;
+
+  while (true) {
+    uint32_t g = 0;
+    if (lane == 0) g = atomicAdd(&a.status[ST_WORK], 1u);
+    g = __shfl_sync(0xffffffffu, g, 0);
+    if (g >= ngroups) break;
+    const int2 gr = a.groups[g];
+    const int nact = gr.y;
+    const bool active = lane < nact;
+    const int64_t p = gr.x + (active ? lane : 0);
+    const double x = a.spos[p] * a.invL, y = a.spos[a.n + p] * a.invL,
+                 z = a.spos[2 * a.n + p] * a.invL;
+    const int s = active ? a.btype[p] : 0;
+    // bounding box relative to the group's first body (FP32 is ample here)
+    const double x0 = __shfl_sync(0xffffffffu, x, 0), y0 = __shfl_sync(0xffffffffu, y, 0),
+                 z0 = __shfl_sync(0xffffffffu, z, 0);
+    float lo[3] = {(float)(x - x0), (float)(y - y0), (float)(z - z0)};
+    float hi[3] = {lo[0], lo[1], lo[2]};
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        lo[d] = fminf(lo[d], __shfl_xor_sync(0xffffffffu, lo[d], o));
+        hi[d] = fmaxf(hi[d], __shfl_xor_sync(0xffffffffu, hi[d], o));
+      }
+    }
+    // dyadic origin (multiple of 2^-21, exact in FP32) at the box centre
+    const double scale21 = 2097152.0;
+    const double oxd = rint((x0 + 0.5 * ((double)lo[0] + (double)hi[0])) * scale21) / scale21;
+    const double oyd = rint((y0 + 0.5 * ((double)lo[1] + (double)hi[1])) * scale21) / scale21;
+    const double ozd = rint((z0 + 0.5 * ((double)lo[2] + (double)hi[2])) * scale21) / scale21;
+    const float ox = (float)oxd, oy = (float)oyd, oz = (float)ozd;
+    const float pad = 1.0f / 1048576.0f;
+    const float gx = 0.5f * (hi[0] - lo[0]) + pad, gy = 0.5f * (hi[1] - lo[1]) + pad,
+                gz = 0.5f * (hi[2] - lo[2]) + pad;
+    // the body's own position is formed exactly as its record in the lists
+    // (leaf centre offset + body offset, then scaled), so the self term has
+    // d = 0 exactly and contributes nothing
+    float xr, yr, zr;
+    {
+      const float4 lg = a.geo[a.bleaf[p]];
+      const float4 bd = a.body[p];
+      xr = (wrap_unit(lg.x - ox) + bd.x) * s_tab;
+      yr = (wrap_unit(lg.y - oy) + bd.y) * s_tab;
+      zr = (wrap_unit(lg.z - oz) + bd.z) * s_tab;
+    }
+
+    const float2* tb[D];
+#pragma unroll
+    for (int t = 0; t < D; ++t) tb[t] = tab + (int)a.tabid[s][t] * a.tab_entries;
+    float ax[D], ay[D], az[D];
+    int lc[D];
+#pragma unroll
+    for (int t = 0; t < D; ++t) { ax[t] = ay[t] = az[t] = 0.f; lc[t] = 0; }
+
+    if (lane == 0) ws->stack[0] = 0;
+    int size = 1;
+    bool overflow = false;
+    uint32_t visits = 0;            // a tree has nnodes nodes: more visits means corruption
+    __syncwarp();
+    while (size > 0) {
+      int room = (kStackCap - size) / 7;
+      if (room < 1 || visits > nnodes) { overflow = true; break; }
+      const int k = min(min(32, size), room);
+      visits += k;
+      const int node = lane < k ? ws->stack[size - k + lane] : -1;
+      size -= k;
+      __syncwarp();
+      // classify
+      int cls = 0;   // 0 skip, 1 accept, 2 leaf, 3 open
+      float dcx = 0.f, dcy = 0.f, dcz = 0.f;
+      int4 lk = make_int4(0, 0, 0, 0);
+      if (node >= 0) {
+        const float4 ge = a.geo[node];
+        lk = a.link[node];
+        dcx = wrap_unit(ge.x - ox);
+        dcy = wrap_unit(ge.y - oy);
+        dcz = wrap_unit(ge.z - oz);
+        const float hx = fmaxf(0.f, fabsf(dcx) - ge.w - gx);
+        const float hy = fmaxf(0.f, fabsf(dcy) - ge.w - gy);
+        const float hz = fmaxf(0.f, fabsf(dcz) - ge.w - gz);
+        const float d2min = hx * hx + hy * hy + hz * hz;
+        if (d2min < rc2) {
+          const float4 cm = a.com[node];
+          const float ex = fmaxf(0.f, fabsf(dcx + cm.x) - gx);
+          const float ey = fmaxf(0.f, fabsf(dcy + cm.y) - gy);
+          const float ez = fmaxf(0.f, fabsf(dcz + cm.z) - gz);
+          const float dd2 = ex * ex + ey * ey + ez * ez;
+          const float side = 2.f * ge.w;
+          if (d2min > 0.f && side * side < a.theta2 * dd2) cls = 1;
+          else cls = lk.y == 0 ? 2 : 3;
+        }
+      }
+      // make room in the lists for up to 32 more records per species
+      {
+        bool full = false;
+#pragma unroll
+        for (int t = 0; t < D; ++t) full |= lc[t] > kListCap - 32;
+        if (full) evaluate<D>(ws, lc, tb, xr, yr, zr, a.eps2_tab, clampbits, ax, ay, az, nint, nact);
+      }
+      // accepted nodes: one record per species with mass
+      {
+        const uint32_t acc_mask = __ballot_sync(0xffffffffu, cls == 1);
+        if (acc_mask) {
+#pragma unroll
+          for (int t = 0; t < D; ++t) {
+            float4 mo = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (cls == 1) mo = a.mono[(size_t)node * D + t];
+            const bool has = cls == 1 && mo.w > 0.f;
+            const uint32_t b = __ballot_sync(0xffffffffu, has);
+            if (has)
+              ws->list[t][lc[t] + __popc(b & lt)] =
+                  make_float4((dcx + mo.x) * s_tab, (dcy + mo.y) * s_tab, (dcz + mo.z) * s_tab, mo.w);
+            lc[t] += __popc(b);
+          }
+        }
+      }
+      // rejected internal nodes: push children
+      {
+        const int nch = cls == 3 ? lk.y : 0;
+        int incl = nch;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int t = __shfl_up_sync(0xffffffffu, incl, o);
+          if (lane >= o) incl += t;
+        }
+        const int total = __shfl_sync(0xffffffffu, incl, 31);
+        const int base = size + incl - nch;
+        for (int cc = 0; cc < nch; ++cc) ws->stack[base + cc] = lk.x + cc;
+        size += total;
+      }
+      // rejected leaves: bodies into the lists of their species
+      {
+        const uint32_t lm = __ballot_sync(0xffffffffu, cls == 2);
+        if (lm) {
+          if (cls == 2) {
+            const int pos = __popc(lm & lt);
+            ws->leafq[pos] = node;
+            ws->leafc[pos] = make_float4(dcx, dcy, dcz, 0.f);
+          }
+          __syncwarp();
+          const int nl = __popc(lm);
+          for (int j = 0; j < nl; ++j) {
+            const int ln = ws->leafq[j];
+            const float4 lc4 = ws->leafc[j];
+            const int4 ll = a.link[ln];
+            for (int b0 = 0; b0 < ll.w; b0 += 32) {
+              bool full = false;
+#pragma unroll
+              for (int t = 0; t < D; ++t) full |= lc[t] > kListCap - 32;
+              if (full)
+                evaluate<D>(ws, lc, tb, xr, yr, zr, a.eps2_tab, clampbits, ax, ay, az, nint, nact);
+              const bool has = b0 + lane < ll.w;
+              float4 bd = make_float4(0.f, 0.f, 0.f, 0.f);
+              int bt = -1;
+              if (has) {
+                bd = a.body[ll.z + b0 + lane];
+                bt = a.btype[ll.z + b0 + lane];
+              }
+#pragma unroll
+              for (int t = 0; t < D; ++t) {
+                const uint32_t bb = __ballot_sync(0xffffffffu, bt == t);
+                if (bt == t)
+                  ws->list[t][lc[t] + __popc(bb & lt)] =
+                      make_float4((lc4.x + bd.x) * s_tab, (lc4.y + bd.y) * s_tab,
+                                  (lc4.z + bd.z) * s_tab, bd.w);
+                lc[t] += __popc(bb);
+              }
+            }
+          }
+          __syncwarp();
+        }
+      }
+      __syncwarp();
+    }
+    evaluate<D>(ws, lc, tb, xr, yr, zr, a.eps2_tab, clampbits, ax, ay, az, nint, nact);
+    if (overflow) {
+      if (lane == 0) atomicOr(&a.status[ST_FLAGS], (uint32_t)SF_STACK_OVERFLOW);
+      continue;
+    }
+    if (active) {
+      float fx = 0.f, fy = 0.f, fz = 0.f;
+#pragma unroll
+      for (int t = 0; t < D; ++t) {
+        const float G = a.G[s][t];
+        fx = fmaf(G, ax[t], fx);
+        fy = fmaf(G, ay[t], fy);
+        fz = fmaf(G, az[t], fz);
+      }
+      const uint32_t i = a.perm[p];
+      fx *= a.out_scale;
+      fy *= a.out_scale;
+      fz *= a.out_scale;
+      if (a.accumulate) {
+        a.acc[i] += fx;
+        a.acc[a.n + i] += fy;
+        a.acc[2 * a.n + i] += fz;
+      } else {
+        a.acc[i] = fx;
+        a.acc[a.n + i] = fy;
+        a.acc[2 * a.n + i] = fz;
+      }
+    }
+  }
+  if (a.counter && lane == 0 && nint) atomicAdd(a.counter, nint);
+}
+
+template <int D>
+static size_t walk_smem(int nlaws, int entries, int nwarps) {
+  const size_t tab_bytes = ((size_t)nlaws * entries * sizeof(float2) + 15) & ~(size_t)15;
+  return tab_bytes + (size_t)nwarps * sizeof(WarpSmem<D>);
+}
+
+template <int D>
+static int launch_walk_d(ng_ctx* c, WalkArgs& a) {
+  int nwarps = kWalkMaxWarps;
+  while (nwarps > 1 && walk_smem<D>(c->nlaws, a.tab_entries, nwarps) > c->smem_optin) --nwarps;
+  const size_t smem = walk_smem<D>(c->nlaws, a.tab_entries, nwarps);
+  if (smem > c->smem_optin)
+    return fail(c, NG_ENOMEM, "walk needs %zu B shared memory (max %zu)", smem, c->smem_optin);
+  NG_CUDA(c, cudaFuncSetAttribute(k_walk<D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem));
+  int per_sm = 0;
+  NG_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walk<D>, nwarps * 32, smem));
+  if (per_sm < 1) per_sm = 1;
+  k_walk<D><<<c->nsm * per_sm, nwarps * 32, smem, c->stream>>>(a, c->nlaws);
+  c->launches += 1;
+  NG_CUDA(c, cudaGetLastError());
+  return NG_OK;
+}
+
+int launch_walk(ng_ctx* c, float* acc, bool accumulate, bool count) {
+  WalkArgs a{};
+  a.geo = as<float4>(c->n_geo);
+  a.com = as<float4>(c->n_com);
+  a.link = as<int4>(c->n_link);
+  a.mono = as<float4>(c->n_mono);
+  a.body = as<float4>(c->body);
+  a.btype = as<uint8_t>(c->stype);
+  a.bleaf = as<uint32_t>(c->bleaf);
+  a.spos = as<double>(c->spos);
+  a.groups = as<int2>(c->groups);
+  a.perm = as<uint32_t>(c->vals_a);
+  a.status = as<uint32_t>(c->status);
+  a.tab = as<float2>(c->d_tab);
+  a.tab_entries = c->ncut + 1;
+  a.ncut = c->ncut;
+  for (int i = 0; i < kMaxD; ++i)
+    for (int j = 0; j < kMaxD; ++j) {
+      a.tabid[i][j] = c->tabid[i][j];
+      a.G[i][j] = (float)c->p.G[i][j];
+    }
+  a.n = c->n;
+  a.L = c->L;
+  a.invL = 1.0 / c->L;
+  a.inv_dr = c->L / c->dr_phys;
+  a.rcut_box = (float)(c->rcut / c->L);
+  a.theta2 = (float)(c->p.theta * c->p.theta);
+  const double eps_tab = c->p.eps / c->dr_phys;
+  a.eps2_tab = (float)(eps_tab * eps_tab);
+  a.out_scale = (float)(1.0 / (c->dr_phys * c->dr_phys));
+  a.acc = acc;
+  a.counter = count ? as<unsigned long long>(c->counter) : nullptr;
+  a.accumulate = accumulate ? 1 : 0;
+  NG_CUDA(c, cudaMemsetAsync(as<uint32_t>(c->status) + ST_WORK, 0, sizeof(uint32_t), c->stream));
+  switch (c->p.D) {
+    case 1: return launch_walk_d<1>(c, a);
+    case 2: return launch_walk_d<2>(c, a);
+    case 3: return launch_walk_d<3>(c, a);
+    case 4: return launch_walk_d<4>(c, a);
+    case 5: return launch_walk_d<5>(c, a);
+    default: return launch_walk_d<6>(c, a);
+  }
+}
+
+// ------------------------------------------------ per-particle count walk
+
+// The algorithm's own unit of work: the per-particle walk with the geometric
+// criterion evaluated in double precision (each operation rounded on its
+// own, in the order of the definition). One thread per sorted body.
+struct CountArgs {
+  const uint8_t* level;
+  const uint64_t* prefix;
+  const uint32_t* first;
+  const uint32_t* count;
+  const uint8_t* nchild;
+  const uint32_t* child;
+  const double* m64;       // [node][D][4]
+  const double* spos;
+  const uint32_t* perm;
+  int64_t n;
+  int D;
+  double invL, rcut2, theta;
+  int64_t* out;            // [caller index] or nullptr
+  unsigned long long* total;
+  uint32_t* status;
+};
+
+__device__ __forceinline__ uint32_t compact3c(uint64_t v) {
+  v &= 0x1249249249249249ull;
+  v = (v ^ (v >> 2)) & 0x10c30c30c30c30c3ull;
+  v = (v ^ (v >> 4)) & 0x100f00f00f00f00full;
+  v = (v ^ (v >> 8)) & 0x1f0000ff0000ffull;
+  v = (v ^ (v >> 16)) & 0x1f00000000ffffull;
+  v = (v ^ (v >> 32)) & 0x1fffffull;
+  return (uint32_t)v;
+}
+
+__device__ __forceinline__ double min_image_d(double d) { return __dsub_rn(d, rint(d)); }
+
+constexpr int kCountStack = 192;
+
+__global__ void __launch_bounds__(128) k_count(CountArgs a) {
+  if (a.status[ST_FLAGS] & SF_NODE_OVERFLOW) return;
+  unsigned long long mine = 0;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < a.n;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const double x[3] = {a.spos[k] * a.invL, a.spos[a.n + k] * a.invL, a.spos[2 * a.n + k] * a.invL};
+    uint32_t stack[kCountStack];
+    int sp = 0;
+    stack[sp++] = 0;
+    long long cnt = 0;
+    uint32_t visits = 0;
+    const uint32_t nnodes = a.status[ST_LEVELS + kMaxLevel + 1];
+    while (sp > 0) {
+      if (++visits > nnodes) {
+        atomicOr(&a.status[ST_FLAGS], (uint32_t)SF_BAD_TREE);
+        break;
+      }
+      const uint32_t nd = stack[--sp];
+      const int lvl = a.level[nd];
+      const uint64_t pre = a.prefix[nd];
+      const double side = 1.0 / (double)(1u << lvl);
+      const double c[3] = {((double)compact3c(pre >> 2) + 0.5) * side,
+                           ((double)compact3c(pre >> 1) + 0.5) * side,
+                           ((double)compact3c(pre) + 0.5) * side};
+      const double half = __dmul_rn(0.5, side);
+      double g2 = 0.0;
+      bool inside = true;
+#pragma unroll
+      for (int e = 0; e < 3; ++e) {
+        const double dc = min_image_d(__dsub_rn(c[e], x[e]));
+        double gap = __dsub_rn(fabs(dc), half);
+        gap = gap > 0.0 ? gap : 0.0;
+        g2 = __dadd_rn(g2, __dmul_rn(gap, gap));
+        if (fabs(dc) > half) inside = false;
+      }
+      if (g2 >= a.rcut2) continue;
+      const uint32_t nch = a.nchild[nd];
+      if (!inside) {
+        double mt = 0.0, sx = 0.0, sy = 0.0, sz = 0.0;
+        int nspec = 0;
+        for (int t = 0; t < a.D; ++t) {
+          const double* m = a.m64 + ((size_t)nd * a.D + t) * 4;
+          mt += m[0];
+          sx += m[1];
+          sy += m[2];
+          sz += m[3];
+          nspec += m[0] > 0.0;
+        }
+        const double com[3] = {sx / mt, sy / mt, sz / mt};
+        double dd2 = 0.0;
+#pragma unroll
+        for (int e = 0; e < 3; ++e) {
+          const double v = min_image_d(__dsub_rn(com[e], x[e]));
+          dd2 = __dadd_rn(dd2, __dmul_rn(v, v));
+        }
+        if (side < __dmul_rn(a.theta, sqrt(dd2))) {
+          cnt += nspec;
+          continue;
+        }
+      }
+      if (nch == 0) {
+        const uint32_t f = a.first[nd], c2 = a.count[nd];
+        cnt += c2;
+        if ((uint64_t)k >= f && (uint64_t)k < (uint64_t)f + c2) cnt -= 1;
+      } else {
+        if (sp + (int)nch > kCountStack) {
+          atomicOr(&a.status[ST_FLAGS], (uint32_t)SF_STACK_OVERFLOW);
+          break;
+        }
+        for (int ch = (int)nch - 1; ch >= 0; --ch) stack[sp++] = a.child[nd] + ch;
+      }
+    }
+    if (a.out) a.out[a.perm[k]] = cnt;
+    mine += (unsigned long long)cnt;
+  }
+  for (int o = 16; o; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);
+  if ((threadIdx.x & 31) == 0 && mine) atomicAdd(a.total, mine);
+}
+
+int launch_count(ng_ctx* c, int64_t* counts) {
+  CountArgs a;
+  a.level = as<uint8_t>(c->n_level);
+  a.prefix = as<uint64_t>(c->n_prefix);
+  a.first = as<uint32_t>(c->n_first);
+  a.count = as<uint32_t>(c->n_count);
+  a.nchild = as<uint8_t>(c->n_nchild);
+  a.child = as<uint32_t>(c->n_child);
+  a.m64 = as<double>(c->n_m64);
+  a.spos = as<double>(c->spos);
+  a.perm = as<uint32_t>(c->vals_a);
+  a.n = c->n;
+  a.D = c->p.D;
+  a.invL = 1.0 / c->L;
+  const double rc = c->rcut / c->L;
+  a.rcut2 = rc * rc;
+  a.theta = c->p.theta;
+  a.out = counts;
+  a.total = as<unsigned long long>(c->counter);
+  a.status = as<uint32_t>(c->status);
+  NG_CUDA(c, cudaMemsetAsync(a.total, 0, sizeof(unsigned long long), c->stream));
+  const int blocks = (int)std::min<int64_t>((c->n + 127) / 128, (int64_t)c->nsm * 16);
+  k_count<<<blocks, 128, 0, c->stream>>>(a);
+  c->launches += 1;
+  NG_CUDA(c, cudaGetLastError());
+  return NG_OK;
+}
+
+}  // namespace ng

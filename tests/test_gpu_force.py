@@ -1,0 +1,155 @@
+"""GPU parity of the forces through the C ABI against the FP64 oracle.
+
+Tolerances (FP32 on the GPU):
+* direct short-range sum (theta = 0): per-particle relative error <= 2e-5
+  (particles whose reference force is below 1e-6 of the rms are excluded,
+  Sec. 3.1 metric with a floor);
+* tree mode (theta = 0.5): 99th percentile of the relative error against the
+  FP64 direct sum <= 1.1x that of the oracle's per-particle tree walk;
+* PM long-range part: max error <= 2e-4 of the rms long-range acceleration
+  (FP32 CIC atomics and FP32 FFTs of N^3 meshes; the oracle is FP64);
+* KDK steps: velocities within 1e-4 of their rms, positions within 1e-9.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from common import device_arrays, ng_params, oracle_params, small_clustered
+from metrics import rel_err
+from paper_1502_07442_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ng():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1502_07442_gb300 import binding, build
+    build.build()
+    return binding
+
+
+def _short_force(ng, prm, w, count=False):
+    import torch
+    pos, typ, mass = device_arrays(w)
+    sim = ng.Simulation(ng_params(prm))
+    ng.ng_build_tree(sim.ctx, pos, typ, mass)
+    acc = torch.empty((3, typ.numel()), dtype=torch.float32, device=pos.device)
+    nint = ng.ng_tree_force(sim.ctx, acc, count=count)
+    torch.cuda.synchronize()
+    out = acc.cpu().numpy().astype(np.float64)
+    sim.close()
+    return (out, nint) if count else out
+
+
+DIRECT_CASES = [
+    ("cfg0", lambda: inputs.workload("uniform4k_d2_newton")),
+    ("clustered_d3_yukawa", lambda: small_clustered(20000, 3, 51, yukawa=True)),
+    ("clustered_d6", lambda: small_clustered(12000, 6, 52)),
+    ("uniform_d1_ragged", lambda: small_clustered(1000 + 17, 1, 53)),
+]
+
+
+@pytest.mark.parametrize("name,make", DIRECT_CASES, ids=[c[0] for c in DIRECT_CASES])
+def test_direct_mode_matches_oracle(ng, name, make):
+    w = make()
+    prm = dict(w["params"], theta=0.0)
+    got = _short_force(ng, prm, w)
+    ref = oracle.direct(oracle_params(prm), w["pos"], w["type"], w["mass"])
+    err, nfloor = rel_err(got, ref)
+    assert nfloor <= 0.001 * w["type"].size + 2
+    assert err.max() <= 2e-5, f"max {err.max():.3g} p99 {np.percentile(err, 99):.3g}"
+
+
+TREE_CASES = [
+    ("cfg0", lambda: inputs.workload("uniform4k_d2_newton")),
+    ("clustered_d4_yukawa", lambda: small_clustered(30000, 4, 54, yukawa=True)),
+    ("clustered_d2", lambda: small_clustered(30000, 2, 55)),
+]
+
+
+@pytest.mark.parametrize("name,make", TREE_CASES, ids=[c[0] for c in TREE_CASES])
+def test_tree_mode_error_within_oracle_bound(ng, name, make):
+    w = make()
+    prm = w["params"]
+    got, nint = _short_force(ng, prm, w, count=True)
+    op = oracle_params(prm)
+    ref = oracle.direct(op, w["pos"], w["type"], w["mass"])
+    tree, cnt = oracle.tree_walk(op, w["pos"], w["type"], w["mass"])
+    e_gpu, _ = rel_err(got, ref)
+    e_cpu, _ = rel_err(tree, ref)
+    assert np.percentile(e_gpu, 99) <= 1.1 * np.percentile(e_cpu, 99)
+    # the group walk opens at least as much as the per-particle walk
+    assert nint >= cnt.sum()
+
+
+def test_single_and_two_bodies(ng):
+    prm = dict(small_clustered(8, 1, 56)["params"], theta=0.5)
+    w1 = dict(pos=np.array([[0.3], [0.4], [0.5]]), type=np.zeros(1, np.uint8),
+              mass=np.ones(1, np.float32))
+    assert np.all(_short_force(ng, prm, w1) == 0.0)
+    w2 = dict(pos=np.array([[0.30, 0.31], [0.4, 0.4], [0.5, 0.5]]), type=np.zeros(2, np.uint8),
+              mass=np.ones(2, np.float32))
+    got = _short_force(ng, prm, w2)
+    ref = oracle.direct(oracle_params(prm), w2["pos"], w2["type"], w2["mass"])
+    np.testing.assert_allclose(got, ref, rtol=2e-5, atol=1e-30)
+
+
+PM_CASES = [
+    ("cfg0", lambda: inputs.workload("uniform4k_d2_newton")),
+    ("clustered_d4_yukawa_m64", lambda: small_clustered(30000, 4, 57, yukawa=True, mesh=64)),
+    ("clustered_d5_m32", lambda: small_clustered(9000, 5, 58, mesh=32)),
+]
+
+
+@pytest.mark.parametrize("name,make", PM_CASES, ids=[c[0] for c in PM_CASES])
+def test_pm_matches_oracle(ng, name, make):
+    import torch
+    w = make()
+    prm = w["params"]
+    pos, typ, mass = device_arrays(w)
+    sim = ng.Simulation(ng_params(prm))
+    ng.ng_build_tree(sim.ctx, pos, typ, mass)
+    acc = torch.empty((3, typ.numel()), dtype=torch.float32, device=pos.device)
+    ng.ng_pm_force(sim.ctx, acc)
+    torch.cuda.synchronize()
+    got = acc.cpu().numpy().astype(np.float64)
+    sim.close()
+    ref = oracle.pm(oracle_params(prm), w["pos"], w["type"], w["mass"])
+    rms = np.sqrt(np.mean(np.sum(ref ** 2, axis=0)))
+    err = np.linalg.norm(got - ref, axis=0) / rms
+    assert err.max() <= 2e-4, f"max {err.max():.3g}, mean {err.mean():.3g}"
+
+
+def test_kdk_steps_match_oracle(ng):
+    import torch
+    w = small_clustered(4096, 2, 59, mesh=32)
+    prm = dict(w["params"], theta=0.0)
+    rng = inputs.rng_for(60)
+    vel0 = (0.01 * rng.standard_normal((3, 4096))).astype(np.float32)
+    pos, typ, mass = device_arrays(w)
+    vel = torch.from_numpy(vel0.copy()).to(pos.device)
+    acc = torch.empty((3, 4096), dtype=torch.float32, device=pos.device)
+    sim = ng.Simulation(ng_params(prm))
+    ng.ng_step(sim.ctx, pos, vel, typ, mass, acc, False, 4, 1e-3)
+    torch.cuda.synchronize()
+    x_ref, v_ref, a_ref = oracle.kdk(oracle_params(prm), w["pos"], vel0.astype(np.float64),
+                                     w["type"], w["mass"], 4, 1e-3)
+    d = pos.cpu().numpy() - x_ref
+    d -= np.rint(d)
+    assert np.abs(d).max() <= 1e-9
+    v = vel.cpu().numpy()
+    rms = np.sqrt(np.mean(v_ref ** 2))
+    assert np.abs(v - v_ref).max() <= 1e-4 * rms
+    err, _ = rel_err(acc.cpu().numpy(), a_ref)
+    assert np.percentile(err, 99) <= 1e-4
+    # a second call reuses the captured step graph
+    ng.ng_step(sim.ctx, pos, vel, typ, mass, acc, True, 2, 1e-3)
+    torch.cuda.synchronize()
+    x2, v2, _ = oracle.kdk(oracle_params(prm), x_ref, v_ref, w["type"], w["mass"], 2, 1e-3)
+    d = pos.cpu().numpy() - x2
+    d -= np.rint(d)
+    assert np.abs(d).max() <= 1e-9
+    sim.close()

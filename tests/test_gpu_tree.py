@@ -1,0 +1,102 @@
+"""GPU parity of the integer outputs (bit-exact) and the FP64 monopoles:
+keys, permutation, canonical octree, N_perp counts, type-major order and
+the per-particle interaction counts, through the C ABI against the oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from common import device_arrays, ng_params, oracle_params, small_clustered
+from paper_1502_07442_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ng():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1502_07442_gb300 import binding, build
+    build.build()
+    return binding
+
+
+def _cases():
+    yield "cfg0", inputs.workload("uniform4k_d2_newton")
+    yield "clustered_d4", small_clustered(40000, 4, 41, yukawa=True)
+    yield "tiny1", small_clustered(1, 1, 42)
+    yield "tiny33", small_clustered(33, 3, 43)
+    w = small_clustered(5000, 2, 44, leaf=1)
+    w["pos"][:, 100:400] = w["pos"][:, 99:100]             # 300 duplicates: level-20 leaf
+    yield "dups_leaf1", w
+
+
+CASES = list(_cases())
+
+
+@pytest.mark.parametrize("name,w", CASES, ids=[c[0] for c in CASES])
+def test_keys_perm_tree_bit_exact(ng, name, w):
+    import torch
+    prm = w["params"]
+    pos, typ, mass = device_arrays(w)
+    n = typ.numel()
+    sim = ng.Simulation(ng_params(prm))
+    keys = torch.empty(n, dtype=torch.int64, device=pos.device)
+    perm = torch.empty(n, dtype=torch.int32, device=pos.device)
+    ng.ng_build_tree(sim.ctx, pos, typ, mass, keys, perm)
+    torch.cuda.synchronize()
+    k_ref = oracle.keys(w["pos"], w["type"])
+    p_ref = oracle.sort_perm(k_ref)
+    assert np.array_equal(perm.cpu().numpy().view(np.uint32), p_ref)
+    assert np.array_equal(keys.cpu().numpy().view(np.uint64), k_ref[p_ref])
+    T = ng.ng_tree_export(sim.ctx, prm["D"])
+    R = oracle.tree(oracle_params(prm), w["pos"], w["type"], w["mass"])
+    for f in ("level", "prefix", "first", "count", "nchild", "child_first", "cnt"):
+        assert np.array_equal(T[f], R[f].astype(T[f].dtype)), f
+    np.testing.assert_allclose(T["mass"], R["mass"], rtol=1e-12, atol=0)
+    # centres of mass: the same FP64 sums of m x in another order (tree levels);
+    # both round within (terms + 2) units of 2^-53 of the box size per coordinate
+    dcom = np.abs(T["com"] - R["com"]).max(axis=2)
+    bound = 2.0 ** -53 * 4 * (R["cnt"].astype(np.float64) + 2)
+    assert np.all(dcom <= bound)
+    sim.close()
+
+
+@pytest.mark.parametrize("name,w", CASES[:2], ids=[c[0] for c in CASES[:2]])
+def test_type_major_order(ng, name, w):
+    import torch
+    prm = w["params"]
+    pos, typ, mass = device_arrays(w)
+    n = typ.numel()
+    sim = ng.Simulation(ng_params(prm))
+    ng.ng_build_tree(sim.ctx, pos, typ, mass)
+    order = torch.empty(n, dtype=torch.int32, device=pos.device)
+    offs = ng.ng_type_order(sim.ctx, prm["D"], order)
+    p_ref = oracle.sort_perm(oracle.keys(w["pos"], w["type"]))
+    t_sorted = w["type"][p_ref]
+    want = p_ref[np.argsort(t_sorted, kind="stable")]
+    assert np.array_equal(order.cpu().numpy().view(np.uint32), want)
+    counts = np.bincount(w["type"], minlength=prm["D"])
+    assert np.array_equal(offs, np.concatenate([[0], np.cumsum(counts)]))
+    sim.close()
+
+
+@pytest.mark.parametrize("name,w,theta", [(CASES[0][0], CASES[0][1], 0.5),
+                                          (CASES[1][0], CASES[1][1], 0.5),
+                                          (CASES[1][0], CASES[1][1], 0.0),
+                                          (CASES[4][0], CASES[4][1], 0.7)],
+                         ids=["cfg0", "clustered_d4", "clustered_d4_direct", "dups_leaf1"])
+def test_interaction_counts_bit_exact(ng, name, w, theta):
+    import torch
+    prm = dict(w["params"], theta=theta)
+    pos, typ, mass = device_arrays(w)
+    n = typ.numel()
+    sim = ng.Simulation(ng_params(prm))
+    ng.ng_build_tree(sim.ctx, pos, typ, mass)
+    counts = torch.empty(n, dtype=torch.int64, device=pos.device)
+    total = ng.ng_count_interactions(sim.ctx, counts)
+    _, c_ref = oracle.tree_walk(oracle_params(prm), w["pos"], w["type"], w["mass"])
+    got = counts.cpu().numpy()
+    assert np.array_equal(got, c_ref)
+    assert total == int(c_ref.sum())
+    sim.close()
