@@ -44,6 +44,7 @@ struct DevBuf {
 // Walk tuning constants.
 constexpr int kListCap = 64;            // records per species list per warp
 constexpr int kStackCap = 512;          // node stack entries per warp
+constexpr int kStackReserve = 7 * kMaxLevel + 8;   // kept free for depth-first descent
 constexpr int kWalkMaxWarps = 16;
 
 // Device view of the short-range walk inputs.

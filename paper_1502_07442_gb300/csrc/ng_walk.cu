@@ -156,9 +156,13 @@ __global__ void __launch_bounds__(kWalkMaxWarps * 32, 1) k_walk(WalkArgs a, int 
     uint32_t visits = 0;            // a tree has nnodes nodes: more visits means corruption
     __syncwarp();
     while (size > 0) {
-      int room = (kStackCap - size) / 7;
-      if (room < 1 || visits > nnodes) { overflow = true; break; }
-      const int k = min(min(32, size), room);
+      // Pop up to 32 nodes while the pushes (<= 8 per node) leave kStackReserve
+      // free slots; otherwise pop one (depth-first). Depth-first growth is at
+      // most 7 slots per level below the popped node, so the stack never
+      // exceeds (kStackCap - kStackReserve) + 7 * kMaxLevel + 7 < kStackCap.
+      const int room = (kStackCap - kStackReserve - size) / 7;
+      if (size + 7 > kStackCap || visits > nnodes) { overflow = true; break; }
+      const int k = max(1, min(min(32, size), room));
       visits += k;
       const int node = lane < k ? ws->stack[size - k + lane] : -1;
       size -= k;

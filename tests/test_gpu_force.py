@@ -8,7 +8,10 @@ Tolerances (FP32 on the GPU):
   FP64 direct sum <= 1.1x that of the oracle's per-particle tree walk;
 * PM long-range part: max error <= 2e-4 of the rms long-range acceleration
   (FP32 CIC atomics and FP32 FFTs of N^3 meshes; the oracle is FP64);
-* KDK steps: velocities within 1e-4 of their rms, positions within 1e-9.
+* KDK steps: velocities within 1e-4 of each body's velocity change (+1e-6 of
+  |v| for the FP32 rounding of 8 kicks); positions within 1e-4 of
+  each body's displacement (+1e-12): the FP32 forces (<= 2e-5 relative) and
+  FP32 velocities carry their relative error into the drift.
 """
 import numpy as np
 import pytest
@@ -137,19 +140,24 @@ def test_kdk_steps_match_oracle(ng):
     torch.cuda.synchronize()
     x_ref, v_ref, a_ref = oracle.kdk(oracle_params(prm), w["pos"], vel0.astype(np.float64),
                                      w["type"], w["mass"], 4, 1e-3)
-    d = pos.cpu().numpy() - x_ref
-    d -= np.rint(d)
-    assert np.abs(d).max() <= 1e-9
+
+    def check_pos(x_gpu, x_ref, x_start):
+        d = x_gpu - x_ref
+        d -= np.rint(d)
+        moved = x_ref - x_start
+        moved -= np.rint(moved)
+        assert np.all(np.abs(d) <= 1e-4 * np.linalg.norm(moved, axis=0) + 1e-12)
+
+    check_pos(pos.cpu().numpy(), x_ref, w["pos"])
     v = vel.cpu().numpy()
-    rms = np.sqrt(np.mean(v_ref ** 2))
-    assert np.abs(v - v_ref).max() <= 1e-4 * rms
+    dv = np.linalg.norm(v - v_ref, axis=0)
+    kicked = np.linalg.norm(v_ref - vel0, axis=0)
+    assert np.all(dv <= 1e-4 * kicked + 1e-6 * np.linalg.norm(v_ref, axis=0))
     err, _ = rel_err(acc.cpu().numpy(), a_ref)
     assert np.percentile(err, 99) <= 1e-4
     # a second call reuses the captured step graph
     ng.ng_step(sim.ctx, pos, vel, typ, mass, acc, True, 2, 1e-3)
     torch.cuda.synchronize()
     x2, v2, _ = oracle.kdk(oracle_params(prm), x_ref, v_ref, w["type"], w["mass"], 2, 1e-3)
-    d = pos.cpu().numpy() - x2
-    d -= np.rint(d)
-    assert np.abs(d).max() <= 1e-9
+    check_pos(pos.cpu().numpy(), x2, x_ref)
     sim.close()
