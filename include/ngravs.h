@@ -57,19 +57,22 @@ enum { NG_NEWTON = 0, NG_YUKAWA = 1 };
  *  law[i][j]      NG_NEWTON, or NG_YUKAWA for Eq. (yukawa) with C = 1:
  *                 phi_ij(r) = -G_ij M (1 + yuk_a[i][j] exp(-r / yuk_l[i][j])) / r.
  *  eps            Plummer softening length (> 0): the radial law is
- *                 evaluated at sqrt(r^2 + eps^2).
+ *                 evaluated at rho = sqrt(r^2 + eps^2).
  *  box            periodic box side L.
  *  pm_mesh        PM mesh points per side N_m (power of two, 0 = no PM).
  *  asmth          split scale in mesh cells: r_s = asmth * L / N_m; when
  *                 pm_mesh == 0, r_s = asmth * L (short-range law still split).
  *  rcut_over_rs   short-range cut-off r_cut = rcut_over_rs * r_s (< L/2);
- *                 a term contributes iff the unsoftened r < r_cut.
+ *                 a term contributes iff rho < r_cut.
  *  theta          opening angle: a node of side l is used as D monopoles when
  *                 l < theta * d (d from the target group to the node's centre
  *                 of mass); theta = 0 opens every node (direct summation).
  *  leaf_size      maximum bodies per tree leaf (1..64, 0 = 8).
  *  group_size     particles per walk group (32 or 64, 0 = 32).
  *  table_size     short-range table entries per law (0 = automatic).
+ *  group_cell     walk groups: runs of sibling cells of at most this many
+ *                 bodies are cut into balanced chunks of <= group_size
+ *                 (>= group_size, <= 4096; 0 = 32).
  */
 typedef struct {
   int32_t D;
@@ -77,7 +80,7 @@ typedef struct {
   int32_t leaf_size;
   int32_t group_size;
   int32_t table_size;
-  int32_t reserved0;
+  int32_t group_cell;
   double G[NG_MAX_SPECIES][NG_MAX_SPECIES];
   int32_t law[NG_MAX_SPECIES][NG_MAX_SPECIES];
   double yuk_a[NG_MAX_SPECIES][NG_MAX_SPECIES];

@@ -80,6 +80,7 @@ def lib():
         L.or_tree.restype = i64
         for f in ("or_direct", "or_direct_cells"):
             getattr(L, f).argtypes = [P, i64, vp, vp, vp, i64, vp, vp]
+        L.or_direct_mag.argtypes = [P, i64, vp, vp, vp, i64, vp, vp, vp]
         L.or_tree_walk.argtypes = [P, i64, vp, vp, vp, i64, vp, vp, vp]
         L.or_tree_walk_timed.argtypes = [P, i64, vp, vp, vp, i64, vp, vp, vp, vp]
         L.or_fft1d.argtypes = [i64, vp, vp, ctypes.c_int]
@@ -190,6 +191,20 @@ def direct(p: OrParams, pos, typ, mass, tgt=None, cells=True):
     f = lib().or_direct_cells if cells else lib().or_direct
     f(ctypes.byref(p), n, _p(pos), _p(typ), _p(mass), t.size, _p(t), _p(acc))
     return acc
+
+
+def direct_mag(p: OrParams, pos, typ, mass, tgt=None):
+    """Brute-force direct sum and, per target, the sum of the term magnitudes."""
+    pos = _soa(pos)
+    typ = np.ascontiguousarray(typ, np.uint8)
+    mass = np.ascontiguousarray(mass, np.float32)
+    n = pos.shape[1]
+    t = _targets(n, tgt)
+    acc = np.zeros((3, t.size))
+    mag = np.zeros(t.size)
+    lib().or_direct_mag(ctypes.byref(p), n, _p(pos), _p(typ), _p(mass), t.size, _p(t), _p(acc),
+                        _p(mag))
+    return acc, mag
 
 
 def tree_walk(p: OrParams, pos, typ, mass, tgt=None):

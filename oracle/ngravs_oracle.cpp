@@ -25,8 +25,9 @@
  *    is the closed form coded in short_factor() below.
  *  - Sec. 2 (D^2 softenings, kind unspecified): one Plummer length eps; the
  *    radial law F(r)/r is evaluated at rho = sqrt(r^2 + eps^2) and the
- *    vector is F(rho)/rho * r_vec. The cut-off uses the unsoftened r:
- *    a term contributes iff r < r_cut (strict).
+ *    vector is F(rho)/rho * r_vec. The cut-off (not given by the paper) is
+ *    applied to the same argument: a term contributes iff rho < r_cut,
+ *    i.e. r^2 + eps^2 < r_cut^2 (strict).
  *  - Sec. 2.2 tree: canonical Morton-prefix octree; a cell is a leaf iff it
  *    holds <= leaf_size bodies or sits at level 20. Per node and species:
  *    mass, centre of mass and body count (N_perp).
@@ -148,17 +149,20 @@ static double min_image(double d, double L) {
 }
 
 /* Acceleration on a passive particle of species s from a point of active
- * mass M and species t at min-image separation d (source - target). */
+ * mass M and species t at min-image separation d (source - target); mag
+ * (optional) accumulates the magnitude of the term. */
 static void pair_accel(const or_params* p, int s, int t, double M,
-                       const double d[3], double acc[3]) {
+                       const double d[3], double acc[3], double* mag = nullptr) {
   const double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-  if (!(r2 < p->rcut * p->rcut)) return;
-  const double rho = std::sqrt(r2 + p->eps * p->eps);
+  const double q = r2 + p->eps * p->eps;
+  if (!(q < p->rcut * p->rcut)) return;
+  const double rho = std::sqrt(q);
   const double T = or_short_factor(p->law[s][t], p->ya[s][t], p->yl[s][t], p->rs, rho);
   const double f = p->G[s][t] * M * T / (rho * rho * rho);
   acc[0] += f * d[0];
   acc[1] += f * d[1];
   acc[2] += f * d[2];
+  if (mag) *mag += std::fabs(f) * std::sqrt(r2);
 }
 
 /* --------------------------------------------------------- Morton keys */
@@ -352,23 +356,36 @@ int64_t or_tree(const or_params* p, int64_t n, const double* pos,
 
 /* ---------------------------------------------------- short-range forces */
 
+void or_direct_mag(const or_params* p, int64_t n, const double* pos,
+                   const uint8_t* type, const float* mass, int64_t ntgt,
+                   const int64_t* tgt, double* acc, double* mag);
+
 /* Brute-force direct short-range sum (Eq. (map) with N_perp = 1) for the
  * targets listed in tgt (original indices); acc is [3][ntgt]. */
 void or_direct(const or_params* p, int64_t n, const double* pos,
                const uint8_t* type, const float* mass, int64_t ntgt,
                const int64_t* tgt, double* acc) {
+  or_direct_mag(p, n, pos, type, mass, ntgt, tgt, acc, nullptr);
+}
+
+/* The same sum; mag (optional, [ntgt]) receives sum_k |a_k|, the scale of
+ * the rounding error any finite-precision evaluation of the sum carries. */
+void or_direct_mag(const or_params* p, int64_t n, const double* pos,
+                   const uint8_t* type, const float* mass, int64_t ntgt,
+                   const int64_t* tgt, double* acc, double* mag) {
   const double L = p->box;
 #pragma omp parallel for schedule(dynamic, 16)
   for (int64_t q = 0; q < ntgt; ++q) {
     const int64_t i = tgt[q];
-    double a[3] = {0, 0, 0};
+    double a[3] = {0, 0, 0}, m = 0.0;
     for (int64_t k = 0; k < n; ++k) {
       if (k == i) continue;
       double d[3];
       for (int c = 0; c < 3; ++c) d[c] = min_image(pos[c * n + k] - pos[c * n + i], L);
-      pair_accel(p, type[i], type[k], mass[k], d, a);
+      pair_accel(p, type[i], type[k], mass[k], d, a, &m);
     }
     for (int c = 0; c < 3; ++c) acc[c * ntgt + q] = a[c];
+    if (mag) mag[q] = m;
   }
 }
 

@@ -33,7 +33,7 @@ class NgParams(ctypes.Structure):
     _fields_ = [
         ("D", ctypes.c_int32), ("pm_mesh", ctypes.c_int32), ("leaf_size", ctypes.c_int32),
         ("group_size", ctypes.c_int32), ("table_size", ctypes.c_int32),
-        ("reserved0", ctypes.c_int32),
+        ("group_cell", ctypes.c_int32),
         ("G", _M6d), ("law", _M6i), ("yuk_a", _M6d), ("yuk_l", _M6d),
         ("eps", ctypes.c_double), ("box", ctypes.c_double), ("asmth", ctypes.c_double),
         ("rcut_over_rs", ctypes.c_double), ("theta", ctypes.c_double),
@@ -94,12 +94,14 @@ def _check(ctx, code):
 
 
 def make_params(D, G, *, eps, box=1.0, pm_mesh=0, asmth=1.25, rcut_over_rs=4.5, theta=0.5,
-                leaf_size=8, group_size=32, table_size=0, law=None, yuk_a=None, yuk_l=None):
+                leaf_size=8, group_size=32, table_size=0, law=None, yuk_a=None, yuk_l=None,
+                group_cell=0):
     p = NgParams()
     p.D, p.pm_mesh, p.leaf_size, p.group_size, p.table_size = (int(D), int(pm_mesh), int(leaf_size),
                                                                int(group_size), int(table_size))
     p.eps, p.box, p.asmth, p.rcut_over_rs, p.theta = (float(eps), float(box), float(asmth),
                                                       float(rcut_over_rs), float(theta))
+    p.group_cell = int(group_cell)
     G = np.asarray(G, np.float64)
     law = np.zeros((D, D), np.int32) if law is None else np.asarray(law, np.int32)
     ya = np.zeros((D, D)) if yuk_a is None else np.asarray(yuk_a, np.float64)
@@ -124,7 +126,7 @@ def params_from_workload(w: dict, **over) -> NgParams:
     return make_params(q["D"], q["G"], eps=q["eps"], box=box, pm_mesh=mesh, asmth=asmth,
                        rcut_over_rs=float(q["rcut"]) / rs, theta=q["theta"],
                        leaf_size=q.get("leaf_size", 8), law=q["law"], yuk_a=q["ya"], yuk_l=q["yl"],
-                       table_size=q.get("table_size", 0))
+                       table_size=q.get("table_size", 0), group_cell=q.get("group_cell", 0))
 
 
 def _ptr(t):

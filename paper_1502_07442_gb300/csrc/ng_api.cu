@@ -75,7 +75,8 @@ double short_law_factor(int law, double a, double l, double rs, double rho) {
 // One table per distinct law; segment k (k < ncut) is the chord of T over
 // [(k - 1/2) dr, (k + 1/2) dr] (segment 0 over [0, dr/2]); the walk reads
 // c0 + t c1 with t = rho/dr - k; entry ncut is zero (beyond the cut-off,
-// which sits at rho = (ncut - 1/2) dr = sqrt(r_cut^2 + eps^2)).
+// which sits at rho = (ncut - 1/2) dr = r_cut). The table depends on the
+// law, r_s and r_cut only, not on the softening.
 int build_tables(ng_ctx* c) {
   const ng_params& p = c->p;
   const int D = p.D;
@@ -97,13 +98,12 @@ int build_tables(ng_ctx* c) {
   c->nlaws = (int)laws.size();
   int ncut = p.table_size;
   if (ncut <= 0) {
-    const size_t budget = 96 * 1024;
+    const size_t budget = 64 * 1024;
     ncut = (int)std::min<size_t>(4096, budget / (sizeof(float) * 2 * laws.size()) - 1);
   }
   if (ncut < 16) return fail(c, NG_EINVAL, "table_size %d too small", ncut);
   c->ncut = ncut;
-  const double rho_cut = std::sqrt(c->rcut * c->rcut + p.eps * p.eps);
-  c->dr_phys = rho_cut / (ncut - 0.5);
+  c->dr_phys = c->rcut / (ncut - 0.5);
   // separations in table units must stay below 2^22 for the float-bit index
   if (std::sqrt(3.0) * c->L / c->dr_phys > 4.0e6)
     return fail(c, NG_EINVAL, "box too large relative to the table spacing (box/dr = %.3g)",
@@ -137,11 +137,11 @@ __global__ void k_kick(int64_t m, float* __restrict__ vel, const float* __restri
 }
 
 __global__ void k_drift(int64_t m, double* __restrict__ pos, const float* __restrict__ vel,
-                        double dt, double L) {
+                        double dt, double L, double invL, bool pow2) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
        i += (int64_t)gridDim.x * blockDim.x) {
     const double x = fma((double)vel[i], dt, pos[i]);
-    pos[i] = x - L * floor(x / L);
+    pos[i] = x - L * floor(pow2 ? x * invL : x / L);
   }
 }
 
@@ -266,6 +266,8 @@ static int validate(ng_ctx* c, const ng_params* p) {
   if (p->group_size != 0 && p->group_size != 32)
     return fail(c, NG_EINVAL, "group_size must be 0 or 32");
   if (p->table_size < 0 || p->table_size > 8192) return fail(c, NG_EINVAL, "table_size 0..8192");
+  if (p->group_cell != 0 && (p->group_cell < 32 || p->group_cell > 4096))
+    return fail(c, NG_EINVAL, "group_cell must be 0 or in [32, 4096]");
   for (int i = 0; i < p->D; ++i)
     for (int j = 0; j < p->D; ++j) {
       if (!std::isfinite(p->G[i][j])) return fail(c, NG_EINVAL, "G[%d][%d] not finite", i, j);
@@ -303,6 +305,7 @@ int ng_create(ng_ctx** out, const ng_params* p, void* stream) {
   c->p = *p;
   if (c->p.leaf_size == 0) c->p.leaf_size = 8;
   if (c->p.group_size == 0) c->p.group_size = 32;
+  if (c->p.group_cell == 0) c->p.group_cell = c->p.group_size;
   c->stream = (cudaStream_t)stream;
   c->L = p->box;
   c->rs = p->pm_mesh > 0 ? p->asmth * p->box / p->pm_mesh : p->asmth * p->box;
@@ -413,7 +416,7 @@ static int step_once(ng_ctx* c, int64_t n, double* pos, float* vel, const uint8_
   const int grid = device_grid(c, 8);
   c->launches += 3;   // kick, drift, kick
   k_kick<<<grid, 256, 0, c->stream>>>(3 * n, vel, acc, (float)(0.5 * dt));
-  k_drift<<<grid, 256, 0, c->stream>>>(3 * n, pos, vel, dt, c->L);
+  k_drift<<<grid, 256, 0, c->stream>>>(3 * n, pos, vel, dt, c->L, 1.0 / c->L, box_is_pow2(c->L));
   NG_CUDA(c, cudaGetLastError());
   NG_TRY(sort_bodies(c, n, pos, type, mass));
   NG_TRY(tree_stages(c));
@@ -445,7 +448,7 @@ int ng_step(ng_ctx* c, int64_t n, double* pos, float* vel, const uint8_t* type,
     // one eager step sizes every buffer, then the step is captured
     const int grid = device_grid(c, 8);
     k_kick<<<grid, 256, 0, c->stream>>>(3 * n, vel, acc, (float)(0.5 * dt));
-    k_drift<<<grid, 256, 0, c->stream>>>(3 * n, pos, vel, dt, c->L);
+    k_drift<<<grid, 256, 0, c->stream>>>(3 * n, pos, vel, dt, c->L, 1.0 / c->L, box_is_pow2(c->L));
     c->launches += 3;
     NG_CUDA(c, cudaGetLastError());
     NG_TRY(build_checked(c, n, pos, type, mass));

@@ -43,9 +43,13 @@ struct DevBuf {
 
 // Walk tuning constants.
 constexpr int kListCap = 64;            // records per species list per warp
-constexpr int kStackCap = 512;          // node stack entries per warp
+constexpr int kStackCap = 384;          // node stack entries per warp
 constexpr int kStackReserve = 7 * kMaxLevel + 8;   // kept free for depth-first descent
-constexpr int kWalkMaxWarps = 16;
+constexpr int kWalkMaxWarps = 32;
+// Warps per walk block by species count: as many as the per-warp lists and a
+// 64 KB law table leave room for in 227 KB of shared memory; the register
+// budget follows (65536 / threads).
+__host__ __device__ constexpr int walk_warps(int D) { return D <= 3 ? 32 : D == 4 ? 24 : D == 5 ? 20 : 16; }
 
 // Device view of the short-range walk inputs.
 struct WalkArgs {
@@ -185,5 +189,6 @@ int build_tables(ng_ctx* c);
 double short_law_factor(int law, double a, double l, double rs, double rho);
 
 int device_grid(ng_ctx* c, int per_sm);
+bool box_is_pow2(double L);   // L = 2^k: x / L == x * (1 / L) exactly
 
 }  // namespace ng

@@ -1,6 +1,7 @@
 // Sort stage (Sec. 2.4): periodic wrap, 63-bit Morton+type keys, stable LSD
 // radix sort, one gather of the particle data into sorted order, and the
 // type-major order (bodies grouped by type, each type in key order).
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 
@@ -111,15 +112,21 @@ int scan_u32(ng_ctx* c, const uint32_t* in, uint32_t* out, int64_t len, const ui
 
 // --------------------------------------------------------------- keys
 
+// x / L rounded once. For a power-of-two L the product with 1/L is the same
+// number (both exact), and FP64 division costs ~10 FP64 operations here.
+__device__ __forceinline__ double div_box(double x, double L, double invL, bool pow2) {
+  return pow2 ? __dmul_rn(x, invL) : __ddiv_rn(x, L);
+}
+
 // Periodic wrap x - L floor(x / L) with each operation rounded separately
 // (no fused multiply-add), so that the host reference rounds identically.
-__device__ __forceinline__ double wrap_box(double x, double L) {
-  const double f = floor(__ddiv_rn(x, L));
+__device__ __forceinline__ double wrap_box(double x, double L, double invL, bool pow2) {
+  const double f = floor(div_box(x, L, invL, pow2));
   return __dsub_rn(x, __dmul_rn(L, f));
 }
 
-__device__ __forceinline__ uint64_t quantise20(double w, double L) {
-  double q = floor(__dmul_rn(__ddiv_rn(w, L), 1048576.0));
+__device__ __forceinline__ uint64_t quantise20(double w, double L, double invL, bool pow2) {
+  double q = floor(__dmul_rn(div_box(w, L, invL, pow2), 1048576.0));
   q = q < 0.0 ? 0.0 : q;
   q = q > 1048575.0 ? 1048575.0 : q;
   return (uint64_t)q;
@@ -137,12 +144,13 @@ __device__ __forceinline__ uint64_t spread3(uint64_t v) {
 }
 
 __global__ void k_keys(int64_t n, const double* __restrict__ pos, const uint8_t* __restrict__ type,
-                       double L, uint64_t* __restrict__ keys, uint32_t* __restrict__ idx) {
+                       double L, double invL, bool pow2, uint64_t* __restrict__ keys,
+                       uint32_t* __restrict__ idx) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const uint64_t qx = quantise20(wrap_box(pos[i], L), L);
-    const uint64_t qy = quantise20(wrap_box(pos[n + i], L), L);
-    const uint64_t qz = quantise20(wrap_box(pos[2 * n + i], L), L);
+    const uint64_t qx = quantise20(wrap_box(pos[i], L, invL, pow2), L, invL, pow2);
+    const uint64_t qy = quantise20(wrap_box(pos[n + i], L, invL, pow2), L, invL, pow2);
+    const uint64_t qz = quantise20(wrap_box(pos[2 * n + i], L, invL, pow2), L, invL, pow2);
     const uint64_t m = (spread3(qx) << 2) | (spread3(qy) << 1) | spread3(qz);
     keys[i] = (m << 3) | (uint64_t)(type[i] & 7);
     idx[i] = (uint32_t)i;
@@ -240,15 +248,15 @@ static int radix_pass(ng_ctx* c, const uint64_t* kin, const uint32_t* vin, uint6
 
 __global__ void k_gather(int64_t n, const uint32_t* __restrict__ perm,
                          const double* __restrict__ pos, const uint8_t* __restrict__ type,
-                         const float* __restrict__ mass, double L, int D,
-                         double* __restrict__ spos, float* __restrict__ smass,
+                         const float* __restrict__ mass, double L, double invL, bool pow2,
+                         int D, double* __restrict__ spos, float* __restrict__ smass,
                          uint8_t* __restrict__ stype, uint32_t* status) {
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
        k += (int64_t)gridDim.x * blockDim.x) {
     const uint32_t i = perm[k];
-    spos[k] = wrap_box(pos[i], L);
-    spos[n + k] = wrap_box(pos[n + i], L);
-    spos[2 * n + k] = wrap_box(pos[2 * n + i], L);
+    spos[k] = wrap_box(pos[i], L, invL, pow2);
+    spos[n + k] = wrap_box(pos[n + i], L, invL, pow2);
+    spos[2 * n + k] = wrap_box(pos[2 * n + i], L, invL, pow2);
     smass[k] = mass[i];
     const uint8_t ti = type[i];
     if (ti >= D) atomicOr(&status[ST_FLAGS], (uint32_t)SF_BAD_TYPE);
@@ -264,6 +272,11 @@ __global__ void k_iota(int64_t n, uint32_t* out) {
 
 int device_grid(ng_ctx* c, int per_sm) { return c->nsm * per_sm; }
 
+bool box_is_pow2(double L) {
+  int e = 0;
+  return std::frexp(L, &e) == 0.5;
+}
+
 int sort_bodies(ng_ctx* c, int64_t n, const double* pos, const uint8_t* type, const float* mass) {
   const int nblocks = (int)((n + kRsTile - 1) / kRsTile);
   NG_TRY(ensure(c, c->keys_a, n * 8));
@@ -278,7 +291,8 @@ int sort_bodies(ng_ctx* c, int64_t n, const double* pos, const uint8_t* type, co
   uint64_t *ka = as<uint64_t>(c->keys_a), *kb = as<uint64_t>(c->keys_b);
   uint32_t *va = as<uint32_t>(c->vals_a), *vb = as<uint32_t>(c->vals_b);
   const int grid = device_grid(c, 8);
-  k_keys<<<grid, 256, 0, c->stream>>>(n, pos, type, c->L, ka, va);
+  const bool pow2 = box_is_pow2(c->L);
+  k_keys<<<grid, 256, 0, c->stream>>>(n, pos, type, c->L, 1.0 / c->L, pow2, ka, va);
   c->launches += 2;   // keys + gather
   NG_CUDA(c, cudaGetLastError());
   // 8 passes of 8 bits: the result returns to (ka, va)
@@ -287,7 +301,7 @@ int sort_bodies(ng_ctx* c, int64_t n, const double* pos, const uint8_t* type, co
     NG_TRY(radix_pass(c, even ? ka : kb, even ? va : vb, even ? kb : ka, even ? vb : va, n,
                       8 * pass, 0xffu));
   }
-  k_gather<<<grid, 256, 0, c->stream>>>(n, va, pos, type, mass, c->L, c->p.D,
+  k_gather<<<grid, 256, 0, c->stream>>>(n, va, pos, type, mass, c->L, 1.0 / c->L, pow2, c->p.D,
                                         as<double>(c->spos), as<float>(c->smass),
                                         as<uint8_t>(c->stype), as<uint32_t>(c->status));
   NG_CUDA(c, cudaGetLastError());

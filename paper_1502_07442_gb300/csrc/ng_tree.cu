@@ -175,17 +175,6 @@ __device__ __forceinline__ void node_centre(int lvl, uint64_t pre, double c[3], 
   *side = s;
 }
 
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-__device__ __forceinline__ uint32_t warp_sum_u(uint32_t v) {
-#pragma unroll
-  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
 struct MonoArgs {
   const uint8_t* level;
   const uint64_t* prefix;
@@ -209,8 +198,12 @@ struct MonoArgs {
   double invL;
 };
 
-// One warp per node of level lvl: leaves reduce their bodies (and write the
-// body records), internal nodes reduce their children.
+// One thread per node of level lvl (FP64 is ~1/64 of the FP32 rate here, so
+// every FP64 operation counts): a leaf adds each body to its own species
+// (4 FP64 operations per body) and writes the body records; an internal node
+// adds its <= 8 children. The FP32 walk records need no FP64 division: the
+// mass-weighted offset sum(m x) - M c is formed with one FP64 FMA and divided
+// by M in FP32.
 template <int D>
 __global__ void __launch_bounds__(256) k_monopoles(int lvl, MonoArgs a) {
   if (a.status[ST_FLAGS] & SF_NODE_OVERFLOW) return;   // truncated tree: do not read it
@@ -218,10 +211,8 @@ __global__ void __launch_bounds__(256) k_monopoles(int lvl, MonoArgs a) {
   const uint32_t s = lv.start[lvl];
   uint32_t e = lv.start[lvl + 1];
   if (e > a.cap) e = (uint32_t)a.cap;
-  const int lane = threadIdx.x & 31;
-  const uint32_t wglobal = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const uint32_t wcount = (gridDim.x * blockDim.x) >> 5;
-  for (uint32_t k = s + wglobal; k < e; k += wcount) {
+  for (uint32_t k = s + blockIdx.x * blockDim.x + threadIdx.x; k < e;
+       k += gridDim.x * blockDim.x) {
     double cen[3], side;
     node_centre(lvl, a.prefix[k], cen, &side);
     double sm[D], sx[D], sy[D], sz[D];
@@ -231,7 +222,7 @@ __global__ void __launch_bounds__(256) k_monopoles(int lvl, MonoArgs a) {
     const uint32_t nch = a.nchild[k];
     const uint32_t f = a.first[k], c = a.count[k];
     if (nch == 0) {
-      for (uint32_t b = f + lane; b < f + c; b += 32) {
+      for (uint32_t b = f; b < f + c; ++b) {
         const double x = a.spos[b] * a.invL, y = a.spos[a.n + b] * a.invL,
                      z = a.spos[2 * a.n + b] * a.invL;
         const float m = a.smass[b];
@@ -239,69 +230,59 @@ __global__ void __launch_bounds__(256) k_monopoles(int lvl, MonoArgs a) {
         a.body[b] = make_float4((float)(x - cen[0]), (float)(y - cen[1]), (float)(z - cen[2]), m);
         a.bleaf[b] = k;
         const double md = (double)m;
+        // species slot chosen by an unrolled compare (no dynamic register index)
 #pragma unroll
         for (int q = 0; q < D; ++q) {
-          const bool on = (t == q);
-          sm[q] += on ? md : 0.0;
-          sx[q] += on ? md * x : 0.0;
-          sy[q] += on ? md * y : 0.0;
-          sz[q] += on ? md * z : 0.0;
-          sc[q] += on ? 1u : 0u;
+          if (t == q) {
+            sm[q] += md;
+            sx[q] = fma(md, x, sx[q]);
+            sy[q] = fma(md, y, sy[q]);
+            sz[q] = fma(md, z, sz[q]);
+            sc[q] += 1u;
+          }
         }
       }
-    } else if ((uint32_t)lane < nch) {
-      const uint32_t ch = a.child[k] + lane;
+    } else {
+      const uint32_t c0 = a.child[k];
+      for (uint32_t j = 0; j < nch; ++j) {
+        const uint32_t ch = c0 + j;
 #pragma unroll
-      for (int q = 0; q < D; ++q) {
-        const double* src = a.m64 + ((size_t)ch * D + q) * 4;
-        sm[q] = src[0];
-        sx[q] = src[1];
-        sy[q] = src[2];
-        sz[q] = src[3];
-        sc[q] = a.cnt[(size_t)ch * D + q];
+        for (int q = 0; q < D; ++q) {
+          const double4 v = *reinterpret_cast<const double4*>(a.m64 + ((size_t)ch * D + q) * 4);
+          sm[q] += v.x;
+          sx[q] += v.y;
+          sy[q] += v.z;
+          sz[q] += v.w;
+          sc[q] += a.cnt[(size_t)ch * D + q];
+        }
       }
     }
     double mt = 0, xt = 0, yt = 0, zt = 0;
 #pragma unroll
     for (int q = 0; q < D; ++q) {
-      sm[q] = warp_sum(sm[q]);
-      sx[q] = warp_sum(sx[q]);
-      sy[q] = warp_sum(sy[q]);
-      sz[q] = warp_sum(sz[q]);
-      sc[q] = warp_sum_u(sc[q]);
+      *reinterpret_cast<double4*>(a.m64 + ((size_t)k * D + q) * 4) = make_double4(sm[q], sx[q], sy[q], sz[q]);
+      a.cnt[(size_t)k * D + q] = sc[q];
+      float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (sm[q] > 0.0) {
+        const float im = 1.0f / (float)sm[q];
+        r = make_float4((float)fma(-sm[q], cen[0], sx[q]) * im, (float)fma(-sm[q], cen[1], sy[q]) * im,
+                        (float)fma(-sm[q], cen[2], sz[q]) * im, (float)sm[q]);
+      }
+      a.mono[(size_t)k * D + q] = r;
       mt += sm[q];
       xt += sx[q];
       yt += sy[q];
       zt += sz[q];
     }
-    if (lane < D) {
-      // lane q writes species q (registers indexed by the unrolled loop)
-#pragma unroll
-      for (int q = 0; q < D; ++q) {
-        if (lane == q) {
-          double* dst = a.m64 + ((size_t)k * D + q) * 4;
-          dst[0] = sm[q];
-          dst[1] = sx[q];
-          dst[2] = sy[q];
-          dst[3] = sz[q];
-          a.cnt[(size_t)k * D + q] = sc[q];
-          float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
-          if (sm[q] > 0.0)
-            r = make_float4((float)(sx[q] / sm[q] - cen[0]), (float)(sy[q] / sm[q] - cen[1]),
-                            (float)(sz[q] / sm[q] - cen[2]), (float)sm[q]);
-          a.mono[(size_t)k * D + q] = r;
-        }
-      }
+    a.geo[k] = make_float4((float)cen[0], (float)cen[1], (float)cen[2], (float)(0.5 * side));
+    float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (mt > 0.0) {
+      const float im = 1.0f / (float)mt;
+      r = make_float4((float)fma(-mt, cen[0], xt) * im, (float)fma(-mt, cen[1], yt) * im,
+                      (float)fma(-mt, cen[2], zt) * im, (float)mt);
     }
-    if (lane == 31) {
-      a.geo[k] = make_float4((float)cen[0], (float)cen[1], (float)cen[2], (float)(0.5 * side));
-      float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (mt > 0.0)
-        r = make_float4((float)(xt / mt - cen[0]), (float)(yt / mt - cen[1]),
-                        (float)(zt / mt - cen[2]), (float)mt);
-      a.com[k] = r;
-      a.link[k] = make_int4(nch ? (int)a.child[k] : -1, (int)nch, (int)f, (int)c);
-    }
+    a.com[k] = r;
+    a.link[k] = make_int4(nch ? (int)a.child[k] : -1, (int)nch, (int)f, (int)c);
   }
 }
 
@@ -346,10 +327,12 @@ int reduce_monopoles(ng_ctx* c) {
 
 // ------------------------------------------------------------- groups
 
-// Walk groups: runs of consecutive sibling cells holding <= G bodies each
-// (and <= G together) whose parent holds more than G; leaves with more than
-// G bodies are cut into chunks of G. Every body lands in exactly one group.
-__global__ void k_groups(uint32_t* status, int64_t cap, int G, const uint32_t* __restrict__ first,
+// Walk groups: runs of consecutive sibling cells holding <= S bodies each
+// (and <= S together) whose parent holds more than S, each run cut into
+// ceil(c / G) contiguous chunks of balanced size; leaves with more than S
+// bodies are cut the same way. Every body lands in exactly one group.
+__global__ void k_groups(uint32_t* status, int64_t cap, int G, int S,
+                         const uint32_t* __restrict__ first,
                          const uint32_t* __restrict__ count, const uint8_t* __restrict__ nchild,
                          const uint32_t* __restrict__ child, int2* groups, int64_t gcap) {
   if (status[ST_FLAGS] & SF_NODE_OVERFLOW) return;
@@ -362,13 +345,19 @@ __global__ void k_groups(uint32_t* status, int64_t cap, int G, const uint32_t* _
     else atomicOr(&status[ST_FLAGS], (uint32_t)SF_GROUP_OVERFLOW);
   };
   auto emit_chunks = [&](uint32_t f, uint32_t c) {
-    for (uint32_t o = 0; o < c; o += G) emit(f + o, c - o < (uint32_t)G ? c - o : G);
+    const uint32_t k = (c + G - 1) / G, base = c / k, rem = c % k;
+    for (uint32_t j = 0, o = 0; j < k; ++j) {
+      const uint32_t len = base + (j < rem ? 1u : 0u);
+      emit(f + o, len);
+      o += len;
+    }
   };
+  const uint32_t SS = (uint32_t)S;
   for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < total;
        k += gridDim.x * blockDim.x) {
     const uint32_t c = count[k];
-    if (k == 0 && c <= (uint32_t)G) { emit(first[0], c); continue; }
-    if (c <= (uint32_t)G) continue;
+    if (k == 0 && c <= SS) { emit_chunks(first[0], c); continue; }
+    if (c <= SS) continue;
     const uint32_t nch = nchild[k];
     if (nch == 0) {
       if (k == 0) emit_chunks(first[0], c);
@@ -378,16 +367,16 @@ __global__ void k_groups(uint32_t* status, int64_t cap, int G, const uint32_t* _
     for (uint32_t j = 0; j < nch; ++j) {
       const uint32_t ch = child[k] + j;
       const uint32_t cc = count[ch];
-      if (cc > (uint32_t)G) {
-        if (bc) { emit(bf, bc); bc = 0; }
+      if (cc > SS) {
+        if (bc) { emit_chunks(bf, bc); bc = 0; }
         if (nchild[ch] == 0) emit_chunks(first[ch], cc);
         continue;
       }
-      if (bc + cc > (uint32_t)G) { emit(bf, bc); bc = 0; }
+      if (bc + cc > SS) { emit_chunks(bf, bc); bc = 0; }
       if (bc == 0) bf = first[ch];
       bc += cc;
     }
-    if (bc) emit(bf, bc);
+    if (bc) emit_chunks(bf, bc);
   }
 }
 
@@ -395,7 +384,8 @@ int build_groups(ng_ctx* c) {
   NG_TRY(ensure(c, c->groups, (size_t)c->n * sizeof(int2)));
   c->launches += 1;
   k_groups<<<device_grid(c, 4), 256, 0, c->stream>>>(
-      as<uint32_t>(c->status), c->cap_nodes, c->p.group_size, as<uint32_t>(c->n_first),
+      as<uint32_t>(c->status), c->cap_nodes, c->p.group_size, c->p.group_cell,
+      as<uint32_t>(c->n_first),
       as<uint32_t>(c->n_count), as<uint8_t>(c->n_nchild), as<uint32_t>(c->n_child),
       as<int2>(c->groups), c->n);
   NG_CUDA(c, cudaGetLastError());

@@ -26,9 +26,10 @@ namespace ng {
 
 template <int D>
 struct __align__(16) WarpSmem {
-  float4 list[D][kListCap];
-  float4 leafc[32];
-  int leafq[32];
+  float4 list[D][kListCap];   // records per active species, table units
+  float4 leafc[32];           // opened leaves: centre offset from the origin (box units)
+  int2 leafb[32];             // opened leaves: first body, body count
+  int leafo[32];              // opened leaves: exclusive prefix of body counts
   int stack[kStackCap];
 };
 
@@ -38,45 +39,7 @@ constexpr int kMagicBits = 0x4B000000;
 __device__ __forceinline__ float wrap_unit(float d) { return d - rintf(d); }
 
 template <int D>
-__device__ __forceinline__ void evaluate(WarpSmem<D>* ws, int (&lc)[D], const float2* const (&tb)[D],
-                                         float xr, float yr, float zr, float eps2, int clampbits,
-                                         float (&ax)[D], float (&ay)[D], float (&az)[D],
-                                         unsigned long long& nint, int nactive) {
-  __syncwarp();
-#pragma unroll
-  for (int t = 0; t < D; ++t) {
-    const int cnt = lc[t];
-    const float2* __restrict__ T = tb[t];
-    float sx = 0.f, sy = 0.f, sz = 0.f;
-#pragma unroll 4
-    for (int j = 0; j < cnt; ++j) {
-      const float4 r = ws->list[t][j];
-      const float dx = r.x - xr, dy = r.y - yr, dz = r.z - zr;
-      const float q = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
-      const float inv = rsqrtf(q);
-      const float fi = fmaf(q, inv, kMagic);
-      const int bits = min(__float_as_int(fi), clampbits);
-      const float r0 = __int_as_float(bits) - kMagic;
-      const float tt = fmaf(q, inv, -r0);
-      const float2 e = T[bits - kMagicBits];
-      const float g = fmaf(tt, e.y, e.x);
-      const float inv2 = inv * inv;
-      const float f = (r.w * g) * (inv2 * inv);
-      sx = fmaf(f, dx, sx);
-      sy = fmaf(f, dy, sy);
-      sz = fmaf(f, dz, sz);
-    }
-    ax[t] += sx;
-    ay[t] += sy;
-    az[t] += sz;
-    nint += (unsigned long long)cnt * (unsigned long long)nactive;
-    lc[t] = 0;
-  }
-  __syncwarp();
-}
-
-template <int D>
-__global__ void __launch_bounds__(kWalkMaxWarps * 32, 1) k_walk(WalkArgs a, int nlaws) {
+__global__ void __launch_bounds__(walk_warps(D) * 32, 1) k_walk(WalkArgs a, int nlaws) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2* tab = reinterpret_cast<float2*>(smem_raw);
   const int ntab = nlaws * a.tab_entries;
@@ -94,6 +57,7 @@ __global__ void __launch_bounds__(kWalkMaxWarps * 32, 1) k_walk(WalkArgs a, int 
   const float rc2 = a.rcut_box * a.rcut_box;
   const float s_tab = (float)a.inv_dr;
   const int clampbits = kMagicBits + a.ncut;
+  const float eps2 = a.eps2_tab;
   unsigned long long nint = 0;
 
   while (true) {
@@ -105,61 +69,135 @@ __global__ void __launch_bounds__(kWalkMaxWarps * 32, 1) k_walk(WalkArgs a, int 
     const int nact = gr.y;
     const bool active = lane < nact;
     const int64_t p = gr.x + (active ? lane : 0);
-    const double x = a.spos[p] * a.invL, y = a.spos[a.n + p] * a.invL,
-                 z = a.spos[2 * a.n + p] * a.invL;
-    const int s = active ? a.btype[p] : 0;
-    // bounding box relative to the group's first body (FP32 is ample here)
-    const double x0 = __shfl_sync(0xffffffffu, x, 0), y0 = __shfl_sync(0xffffffffu, y, 0),
-                 z0 = __shfl_sync(0xffffffffu, z, 0);
-    float lo[3] = {(float)(x - x0), (float)(y - y0), (float)(z - z0)};
-    float hi[3] = {lo[0], lo[1], lo[2]};
+    const int s = a.btype[p];
+    float ox, oy, oz, gx, gy, gz;
+    const float4 lg = a.geo[a.bleaf[p]];
+    const float4 bd = a.body[p];
+    {
+      // bounding box (box units, FP32; no FP64 in the walk) relative to the
+      // leaf centre of the group's first body; group bodies lie in one cell
+      // far smaller than the box, so no wrap is needed inside the group
+      const float rx = __shfl_sync(0xffffffffu, lg.x, 0), ry = __shfl_sync(0xffffffffu, lg.y, 0),
+                  rz = __shfl_sync(0xffffffffu, lg.z, 0);
+      float lo[3] = {(lg.x - rx) + bd.x, (lg.y - ry) + bd.y, (lg.z - rz) + bd.z};
+      float hi[3] = {lo[0], lo[1], lo[2]};
 #pragma unroll
-    for (int o = 16; o; o >>= 1) {
+      for (int o = 16; o; o >>= 1) {
 #pragma unroll
-      for (int d = 0; d < 3; ++d) {
-        lo[d] = fminf(lo[d], __shfl_xor_sync(0xffffffffu, lo[d], o));
-        hi[d] = fmaxf(hi[d], __shfl_xor_sync(0xffffffffu, hi[d], o));
+        for (int d = 0; d < 3; ++d) {
+          lo[d] = fminf(lo[d], __shfl_xor_sync(0xffffffffu, lo[d], o));
+          hi[d] = fmaxf(hi[d], __shfl_xor_sync(0xffffffffu, hi[d], o));
+        }
       }
+      // dyadic origin (a multiple of 2^-21, exact in FP32) at the box centre
+      const float s21 = 2097152.0f, i21 = 1.0f / 2097152.0f;
+      ox = rintf((rx + 0.5f * (lo[0] + hi[0])) * s21) * i21;
+      oy = rintf((ry + 0.5f * (lo[1] + hi[1])) * s21) * i21;
+      oz = rintf((rz + 0.5f * (lo[2] + hi[2])) * s21) * i21;
+      const float pad = 1.0f / 1048576.0f;
+      gx = 0.5f * (hi[0] - lo[0]) + pad;
+      gy = 0.5f * (hi[1] - lo[1]) + pad;
+      gz = 0.5f * (hi[2] - lo[2]) + pad;
     }
-    // dyadic origin (multiple of 2^-21, exact in FP32) at the box centre
-    const double scale21 = 2097152.0;
-    const double oxd = rint((x0 + 0.5 * ((double)lo[0] + (double)hi[0])) * scale21) / scale21;
-    const double oyd = rint((y0 + 0.5 * ((double)lo[1] + (double)hi[1])) * scale21) / scale21;
-    const double ozd = rint((z0 + 0.5 * ((double)lo[2] + (double)hi[2])) * scale21) / scale21;
-    const float ox = (float)oxd, oy = (float)oyd, oz = (float)ozd;
-    const float pad = 1.0f / 1048576.0f;
-    const float gx = 0.5f * (hi[0] - lo[0]) + pad, gy = 0.5f * (hi[1] - lo[1]) + pad,
-                gz = 0.5f * (hi[2] - lo[2]) + pad;
     // the body's own position is formed exactly as its record in the lists
     // (leaf centre offset + body offset, then scaled), so the self term has
     // d = 0 exactly and contributes nothing
-    float xr, yr, zr;
-    {
-      const float4 lg = a.geo[a.bleaf[p]];
-      const float4 bd = a.body[p];
-      xr = (wrap_unit(lg.x - ox) + bd.x) * s_tab;
-      yr = (wrap_unit(lg.y - oy) + bd.y) * s_tab;
-      zr = (wrap_unit(lg.z - oz) + bd.z) * s_tab;
-    }
+    const float xr = (wrap_unit(lg.x - ox) + bd.x) * s_tab;
+    const float yr = (wrap_unit(lg.y - oy) + bd.y) * s_tab;
+    const float zr = (wrap_unit(lg.z - oz) + bd.z) * s_tab;
 
-    const float2* tb[D];
-#pragma unroll
-    for (int t = 0; t < D; ++t) tb[t] = tab + (int)a.tabid[s][t] * a.tab_entries;
     float ax[D], ay[D], az[D];
-    int lc[D];
+    int lc[D];                      // records per species list (same in every lane)
 #pragma unroll
     for (int t = 0; t < D; ++t) { ax[t] = ay[t] = az[t] = 0.f; lc[t] = 0; }
 
     if (lane == 0) ws->stack[0] = 0;
     int size = 1;
+    int qtotal = 0, qdone = 0, nl = 0;   // queued bodies of opened leaves
     bool overflow = false;
     uint32_t visits = 0;            // a tree has nnodes nodes: more visits means corruption
     __syncwarp();
-    while (size > 0) {
-      // Pop up to 32 nodes while the pushes (<= 8 per node) leave kStackReserve
-      // free slots; otherwise pop one (depth-first). Depth-first growth is at
-      // most 7 slots per level below the popped node, so the stack never
-      // exceeds (kStackCap - kStackReserve) + 7 * kMaxLevel + 7 < kStackCap.
+    while (true) {
+      // ---- the single evaluation site: lists that could overflow on the
+      // next round of (<= 32 per species) appends, or everything at the end
+      const bool drain = size == 0 && qdone >= qtotal;
+#pragma unroll 1
+      for (int t = 0; t < D; ++t) {
+        int cnt = 0;
+#pragma unroll
+        for (int q = 0; q < D; ++q) cnt = (q == t) ? lc[q] : cnt;
+        if (cnt > kListCap - 32 || (drain && cnt > 0)) {
+          const float2* __restrict__ T = tab + (int)a.tabid[s][t] * a.tab_entries;
+          const float4* __restrict__ list = ws->list[t];
+          float sx = 0.f, sy = 0.f, sz = 0.f;
+          __syncwarp();
+#pragma unroll 4
+          for (int j = 0; j < cnt; ++j) {
+            const float4 r = list[j];
+            const float dx = r.x - xr, dy = r.y - yr, dz = r.z - zr;
+            const float qq = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
+            const float inv = rsqrtf(qq);
+            const float fi = fmaf(qq, inv, kMagic);
+            const int bits = min(__float_as_int(fi), clampbits);
+            const float r0 = __int_as_float(bits) - kMagic;
+            const float tt = fmaf(qq, inv, -r0);
+            const float2 e = T[bits - kMagicBits];
+            const float gg = fmaf(tt, e.y, e.x);
+            const float inv2 = inv * inv;
+            const float f = (r.w * gg) * (inv2 * inv);
+            sx = fmaf(f, dx, sx);
+            sy = fmaf(f, dy, sy);
+            sz = fmaf(f, dz, sz);
+          }
+          __syncwarp();
+#pragma unroll
+          for (int q = 0; q < D; ++q) {
+            if (q == t) {
+              ax[q] += sx;
+              ay[q] += sy;
+              az[q] += sz;
+              lc[q] = 0;
+            }
+          }
+          nint += (unsigned long long)cnt * (unsigned long long)nact;
+        }
+      }
+      if (drain) break;
+
+      if (qdone < qtotal) {
+        // ---- one chunk of up to 32 queued leaf bodies into the lists of their species
+        const int f = qdone + lane;
+        const bool has = f < qtotal;
+        float4 rec = make_float4(0.f, 0.f, 0.f, 0.f);
+        int bt = -1;
+        if (has) {
+          // leaf holding queued body f: last leaf whose prefix is <= f
+          int lo = 0, hi = nl - 1;
+          while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (ws->leafo[mid] <= f) lo = mid; else hi = mid - 1;
+          }
+          const int b = ws->leafb[lo].x + (f - ws->leafo[lo]);
+          const float4 lc4 = ws->leafc[lo];
+          const float4 bb = a.body[b];
+          bt = a.btype[b];
+          rec = make_float4((lc4.x + bb.x) * s_tab, (lc4.y + bb.y) * s_tab, (lc4.z + bb.z) * s_tab, bb.w);
+        }
+#pragma unroll
+        for (int t = 0; t < D; ++t) {
+          const uint32_t m = __ballot_sync(0xffffffffu, bt == t);
+          if (bt == t) ws->list[t][lc[t] + __popc(m & lt)] = rec;
+          lc[t] += __popc(m);
+        }
+        qdone += 32;
+        __syncwarp();
+        continue;
+      }
+
+      // ---- pop up to 32 nodes while the pushes (<= 8 per node) leave
+      // kStackReserve free slots; otherwise pop one (depth-first). Depth-first
+      // growth is at most 7 slots per level below the popped node, so the
+      // stack never exceeds (kStackCap - kStackReserve) + 7 * kMaxLevel + 7.
       const int room = (kStackCap - kStackReserve - size) / 7;
       if (size + 7 > kStackCap || visits > nnodes) { overflow = true; break; }
       const int k = max(1, min(min(32, size), room));
@@ -167,12 +205,13 @@ __global__ void __launch_bounds__(kWalkMaxWarps * 32, 1) k_walk(WalkArgs a, int 
       const int node = lane < k ? ws->stack[size - k + lane] : -1;
       size -= k;
       __syncwarp();
-      // classify
+      // classify: the three node records are fetched together
       int cls = 0;   // 0 skip, 1 accept, 2 leaf, 3 open
       float dcx = 0.f, dcy = 0.f, dcz = 0.f;
       int4 lk = make_int4(0, 0, 0, 0);
       if (node >= 0) {
         const float4 ge = a.geo[node];
+        const float4 cm = a.com[node];
         lk = a.link[node];
         dcx = wrap_unit(ge.x - ox);
         dcy = wrap_unit(ge.y - oy);
@@ -182,7 +221,6 @@ __global__ void __launch_bounds__(kWalkMaxWarps * 32, 1) k_walk(WalkArgs a, int 
         const float hz = fmaxf(0.f, fabsf(dcz) - ge.w - gz);
         const float d2min = hx * hx + hy * hy + hz * hz;
         if (d2min < rc2) {
-          const float4 cm = a.com[node];
           const float ex = fmaxf(0.f, fabsf(dcx + cm.x) - gx);
           const float ey = fmaxf(0.f, fabsf(dcy + cm.y) - gy);
           const float ez = fmaxf(0.f, fabsf(dcz + cm.z) - gz);
@@ -192,28 +230,18 @@ __global__ void __launch_bounds__(kWalkMaxWarps * 32, 1) k_walk(WalkArgs a, int 
           else cls = lk.y == 0 ? 2 : 3;
         }
       }
-      // make room in the lists for up to 32 more records per species
-      {
-        bool full = false;
-#pragma unroll
-        for (int t = 0; t < D; ++t) full |= lc[t] > kListCap - 32;
-        if (full) evaluate<D>(ws, lc, tb, xr, yr, zr, a.eps2_tab, clampbits, ax, ay, az, nint, nact);
-      }
       // accepted nodes: one record per species with mass
-      {
-        const uint32_t acc_mask = __ballot_sync(0xffffffffu, cls == 1);
-        if (acc_mask) {
+      if (__any_sync(0xffffffffu, cls == 1)) {
 #pragma unroll
-          for (int t = 0; t < D; ++t) {
-            float4 mo = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (cls == 1) mo = a.mono[(size_t)node * D + t];
-            const bool has = cls == 1 && mo.w > 0.f;
-            const uint32_t b = __ballot_sync(0xffffffffu, has);
-            if (has)
-              ws->list[t][lc[t] + __popc(b & lt)] =
-                  make_float4((dcx + mo.x) * s_tab, (dcy + mo.y) * s_tab, (dcz + mo.z) * s_tab, mo.w);
-            lc[t] += __popc(b);
-          }
+        for (int t = 0; t < D; ++t) {
+          float4 mo = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (cls == 1) mo = a.mono[(size_t)node * D + t];
+          const bool has = mo.w > 0.f;
+          const uint32_t b = __ballot_sync(0xffffffffu, has);
+          if (has)
+            ws->list[t][lc[t] + __popc(b & lt)] =
+                make_float4((dcx + mo.x) * s_tab, (dcy + mo.y) * s_tab, (dcz + mo.z) * s_tab, mo.w);
+          lc[t] += __popc(b);
         }
       }
       // rejected internal nodes: push children
@@ -230,51 +258,31 @@ __global__ void __launch_bounds__(kWalkMaxWarps * 32, 1) k_walk(WalkArgs a, int 
         for (int cc = 0; cc < nch; ++cc) ws->stack[base + cc] = lk.x + cc;
         size += total;
       }
-      // rejected leaves: bodies into the lists of their species
+      // rejected leaves: queue their bodies (drained 32 per iteration above)
       {
         const uint32_t lm = __ballot_sync(0xffffffffu, cls == 2);
         if (lm) {
+          const int nb = cls == 2 ? lk.w : 0;
+          int incl = nb;
+#pragma unroll
+          for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+          }
+          qtotal = __shfl_sync(0xffffffffu, incl, 31);
+          qdone = 0;
+          nl = __popc(lm);
           if (cls == 2) {
             const int pos = __popc(lm & lt);
-            ws->leafq[pos] = node;
             ws->leafc[pos] = make_float4(dcx, dcy, dcz, 0.f);
+            ws->leafb[pos] = make_int2(lk.z, lk.w);
+            ws->leafo[pos] = incl - nb;
           }
-          __syncwarp();
-          const int nl = __popc(lm);
-          for (int j = 0; j < nl; ++j) {
-            const int ln = ws->leafq[j];
-            const float4 lc4 = ws->leafc[j];
-            const int4 ll = a.link[ln];
-            for (int b0 = 0; b0 < ll.w; b0 += 32) {
-              bool full = false;
-#pragma unroll
-              for (int t = 0; t < D; ++t) full |= lc[t] > kListCap - 32;
-              if (full)
-                evaluate<D>(ws, lc, tb, xr, yr, zr, a.eps2_tab, clampbits, ax, ay, az, nint, nact);
-              const bool has = b0 + lane < ll.w;
-              float4 bd = make_float4(0.f, 0.f, 0.f, 0.f);
-              int bt = -1;
-              if (has) {
-                bd = a.body[ll.z + b0 + lane];
-                bt = a.btype[ll.z + b0 + lane];
-              }
-#pragma unroll
-              for (int t = 0; t < D; ++t) {
-                const uint32_t bb = __ballot_sync(0xffffffffu, bt == t);
-                if (bt == t)
-                  ws->list[t][lc[t] + __popc(bb & lt)] =
-                      make_float4((lc4.x + bd.x) * s_tab, (lc4.y + bd.y) * s_tab,
-                                  (lc4.z + bd.z) * s_tab, bd.w);
-                lc[t] += __popc(bb);
-              }
-            }
-          }
-          __syncwarp();
         }
       }
       __syncwarp();
     }
-    evaluate<D>(ws, lc, tb, xr, yr, zr, a.eps2_tab, clampbits, ax, ay, az, nint, nact);
+    __syncwarp();
     if (overflow) {
       if (lane == 0) atomicOr(&a.status[ST_FLAGS], (uint32_t)SF_STACK_OVERFLOW);
       continue;
@@ -314,7 +322,7 @@ static size_t walk_smem(int nlaws, int entries, int nwarps) {
 
 template <int D>
 static int launch_walk_d(ng_ctx* c, WalkArgs& a) {
-  int nwarps = kWalkMaxWarps;
+  int nwarps = walk_warps(D);
   while (nwarps > 1 && walk_smem<D>(c->nlaws, a.tab_entries, nwarps) > c->smem_optin) --nwarps;
   const size_t smem = walk_smem<D>(c->nlaws, a.tab_entries, nwarps);
   if (smem > c->smem_optin)

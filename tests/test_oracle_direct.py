@@ -34,14 +34,33 @@ def test_passive_active_convention_two_bodies():
     assert np.all(a[1:] == 0.0)
 
 
-def test_cutoff_is_strict_on_unsoftened_r():
+def test_cutoff_is_strict_on_softened_separation():
+    # a term contributes iff sqrt(r^2 + eps^2) < r_cut
     p = _params(1, rcut=0.1, eps=0.01)
     typ = np.zeros(2, np.uint8)
     mass = np.ones(2, np.float32)
-    inside = np.array([[0.5, 0.5 + 0.0999999], [0.5, 0.5], [0.5, 0.5]])
-    outside = np.array([[0.5, 0.6000001], [0.5, 0.5], [0.5, 0.5]])
+    r_in = np.sqrt(0.1 ** 2 - 0.01 ** 2) * (1 - 1e-9)
+    r_out = np.sqrt(0.1 ** 2 - 0.01 ** 2) * (1 + 1e-9)
+    inside = np.array([[0.5, 0.5 + r_in], [0.5, 0.5], [0.5, 0.5]])
+    outside = np.array([[0.5, 0.5 + r_out], [0.5, 0.5], [0.5, 0.5]])
     assert oracle.direct(p, inside, typ, mass, cells=False)[0, 0] > 0
     assert np.all(oracle.direct(p, outside, typ, mass, cells=False) == 0.0)
+
+
+def test_magnitude_sum_bounds_the_force():
+    rng = inputs.rng_for(18)
+    n = 300
+    pos = inputs.clustered(n, rng, nspheres=3, a=0.01)
+    typ = inputs.species_uniform(n, 2, rng)
+    mass = rng.uniform(0.5, 1.5, n).astype(np.float32)
+    p = _params(2, rs=0.03)
+    a, mag = oracle.direct_mag(p, pos, typ, mass)
+    np.testing.assert_allclose(a, oracle.direct(p, pos, typ, mass), rtol=1e-13, atol=0)
+    assert np.all(np.linalg.norm(a, axis=0) <= mag * (1 + 1e-12))
+    # one pair: the sum of magnitudes is the magnitude
+    two = np.array([[0.5, 0.52], [0.5, 0.5], [0.5, 0.5]])
+    a2, m2 = oracle.direct_mag(p, two, np.zeros(2, np.uint8), np.ones(2, np.float32))
+    np.testing.assert_allclose(np.linalg.norm(a2, axis=0), m2, rtol=1e-14)
 
 
 def test_periodic_minimum_image():
