@@ -186,6 +186,111 @@ int ng_tree_export(ng_ctx* ctx, int64_t* nnodes, int32_t* level, uint64_t* prefi
  */
 int ng_type_order(ng_ctx* ctx, int64_t* type_offsets, uint32_t* order_out);
 
+/* ------------------------------------------------------------ batches
+ *
+ * Many independent simulations (uneven n, D, couplings) advanced together
+ * on one GPU. The paper has no counterpart (it runs one simulation over MPI
+ * ranks); each simulation still follows ng_step exactly. Within one batch
+ * step every simulation's sort, tree and PM stages run on one of several
+ * worker streams, and the short-range walk of all simulations that share the
+ * species count and the law table is one persistent kernel launch whose
+ * warps take (simulation, group) items from one work queue. The step is
+ * captured once as a CUDA graph and replayed.
+ */
+typedef struct ng_batch ng_batch;
+
+/* nsim >= 1 parameter blocks (validated as in ng_create); stream as in
+ * ng_create. *out is released with ng_batch_destroy. */
+int ng_batch_create(ng_batch** out, int nsim, const ng_params* params, void* stream);
+int ng_batch_destroy(ng_batch* b);
+
+/*
+ * nsteps kick-drift-kick steps of every simulation. Each argument is a HOST
+ * array of nsim entries; the pointers in it are DEVICE arrays laid out as for
+ * ng_step (n[i] bodies of simulation i). acc_valid as for ng_step. The first
+ * call (and any call whose pointers, sizes or dt differ from the captured
+ * ones) runs one step eagerly to size every buffer and captures the next.
+ * Synchronises the stream at the end and reports device errors.
+ */
+int ng_batch_step(ng_batch* b, const int64_t* n, double* const* pos, float* const* vel,
+                  const uint8_t* const* type, const float* const* mass, float* const* acc,
+                  int acc_valid, int nsteps, double dt);
+
+/* Number of simulations; number of walk launches per step (one per class of
+ * simulations sharing D and the law table). */
+int ng_batch_size(const ng_batch* b);
+int ng_batch_walk_launches(const ng_batch* b);
+/* Kernels launched by all member contexts so far (see ng_launch_count). */
+int ng_batch_launch_count(const ng_batch* b, uint64_t* out);
+const char* ng_batch_last_error(const ng_batch* b);
+
+/* ------------------------------------------------------------ serving
+ *
+ * A stream of independent requests (force evaluations and short
+ * integrations, each a full solve as above; no paper counterpart). Requests
+ * wait in a FIFO queue and are admitted while a slot is free and the device
+ * memory the slots hold stays within the byte budget; every admitted request
+ * runs asynchronously on its slot's own stream, so admitted requests overlap
+ * on the GPU (continuous batching). The host never blocks on the device
+ * except in ng_serve_wait / ng_serve, whose waits are bounded.
+ */
+enum { NG_REQ_FORCE = 0, NG_REQ_STEPS = 1 };
+
+typedef struct {
+  int32_t kind;          /* NG_REQ_FORCE: acceleration at pos; NG_REQ_STEPS: nsteps KDK steps */
+  int32_t nsteps;
+  double dt;
+  ng_params params;
+  int64_t n;
+  /* HOST arrays (pinned memory lets the copies overlap), layouts as above;
+   * they must stay valid until the request completes. vel may be NULL
+   * (zero velocities). */
+  const double* pos;
+  const float* vel;
+  const uint8_t* type;
+  const float* mass;
+  /* HOST outputs, each optional: acc_out float[3][n] (acceleration at the
+   * final positions); pos_out / vel_out (NG_REQ_STEPS only). */
+  double* pos_out;
+  float* vel_out;
+  float* acc_out;
+} ng_request;
+
+typedef struct {
+  int32_t status;        /* 1 pending, NG_OK done, or an NG_E* code */
+  int32_t reserved;
+  double t_submit;       /* seconds on a monotonic clock */
+  double t_admit;
+  double t_done;
+} ng_result;
+
+typedef struct ng_server ng_server;
+
+/* slots: concurrent requests (1..256); hbm_budget: bytes the slots may hold. */
+int ng_serve_create(ng_server** out, int slots, size_t hbm_budget);
+int ng_serve_destroy(ng_server* s);
+/* Queue a request (validated on the host: NG_EINVAL; NG_EBUSY if it alone
+ * exceeds the budget). *out is owned by the caller and updated in place. */
+int ng_serve_submit(ng_server* s, const ng_request* r, ng_result* out, int64_t* id);
+/* Cancel a request that has not been admitted yet (NG_ESTATE otherwise). */
+int ng_serve_cancel(ng_server* s, int64_t id);
+/* Non-blocking: collect finished requests, admit queued ones. */
+int ng_serve_poll(ng_server* s, int* ncompleted);
+/* Requests submitted and not finished. */
+int ng_serve_pending(const ng_server* s);
+/* Poll until nothing is pending or timeout_s elapses (NG_ETIMEOUT). */
+int ng_serve_wait(ng_server* s, double timeout_s);
+/* Run a trace: request k is submitted arrival_s[k] seconds after the call
+ * starts (NULL: all at once), then everything is polled to completion within
+ * timeout_s (NG_ETIMEOUT). res[k] receives each request's status and times
+ * (t_submit = scheduled arrival). */
+int ng_serve(ng_server* s, const ng_request* reqs, ng_result* res, int nreq,
+             const double* arrival_s, double timeout_s);
+const char* ng_serve_last_error(const ng_server* s);
+/* Device bytes the server budgets for a request (particle arrays, sort and
+ * tree buffers, PM meshes). */
+size_t ng_serve_request_bytes(const ng_request* r);
+
 /*
  * Number of CUDA kernels this context has launched so far (host-side count,
  * library kernels only; cuFFT's own kernels are not included). A captured

@@ -40,6 +40,27 @@ class NgParams(ctypes.Structure):
     ]
 
 
+NG_REQ_FORCE, NG_REQ_STEPS = 0, 1
+
+
+class NgRequest(ctypes.Structure):
+    """Mirror of ``ng_request`` (host arrays given as addresses)."""
+
+    _fields_ = [("kind", ctypes.c_int32), ("nsteps", ctypes.c_int32), ("dt", ctypes.c_double),
+                ("params", NgParams), ("n", ctypes.c_int64),
+                ("pos", ctypes.c_void_p), ("vel", ctypes.c_void_p), ("type", ctypes.c_void_p),
+                ("mass", ctypes.c_void_p), ("pos_out", ctypes.c_void_p),
+                ("vel_out", ctypes.c_void_p), ("acc_out", ctypes.c_void_p)]
+
+
+class NgResult(ctypes.Structure):
+    """Mirror of ``ng_result``."""
+
+    _fields_ = [("status", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double),
+                ("t_done", ctypes.c_double)]
+
+
 class NgError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"ngravs error {code}: {msg}")
@@ -69,12 +90,37 @@ def lib():
         L.ng_tree_export.argtypes = [vp, ctypes.POINTER(i64)] + [vp] * 9
         L.ng_type_order.argtypes = [vp, vp, vp]
         L.ng_launch_count.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64)]
+        L.ng_batch_create.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(NgParams), vp]
+        L.ng_batch_destroy.argtypes = [vp]
+        L.ng_batch_step.argtypes = [vp, vp, vp, vp, vp, vp, vp, i32, i32, d]
+        L.ng_batch_size.argtypes = [vp]
+        L.ng_batch_walk_launches.argtypes = [vp]
+        L.ng_batch_launch_count.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64)]
+        L.ng_batch_last_error.argtypes = [vp]
+        L.ng_batch_last_error.restype = ctypes.c_char_p
+        L.ng_serve_create.argtypes = [ctypes.POINTER(vp), i32, ctypes.c_size_t]
+        L.ng_serve_destroy.argtypes = [vp]
+        L.ng_serve_submit.argtypes = [vp, ctypes.POINTER(NgRequest), ctypes.POINTER(NgResult),
+                                      ctypes.POINTER(i64)]
+        L.ng_serve_cancel.argtypes = [vp, i64]
+        L.ng_serve_poll.argtypes = [vp, ctypes.POINTER(i32)]
+        L.ng_serve_pending.argtypes = [vp]
+        L.ng_serve_wait.argtypes = [vp, d]
+        L.ng_serve.argtypes = [vp, ctypes.POINTER(NgRequest), ctypes.POINTER(NgResult), i32, vp, d]
+        L.ng_serve_request_bytes.argtypes = [ctypes.POINTER(NgRequest)]
+        L.ng_serve_request_bytes.restype = ctypes.c_size_t
+        L.ng_serve_last_error.argtypes = [vp]
+        L.ng_serve_last_error.restype = ctypes.c_char_p
         L.ng_last_error.argtypes = [vp]
         L.ng_last_error.restype = ctypes.c_char_p
         L.ng_version.restype = ctypes.c_char_p
         for f in ("ng_create", "ng_destroy", "ng_set_stream", "ng_build_tree", "ng_tree_force",
                   "ng_count_interactions", "ng_pm_force", "ng_step", "ng_tree_export",
-                  "ng_type_order", "ng_launch_count"):
+                  "ng_type_order", "ng_launch_count", "ng_batch_create", "ng_batch_destroy",
+                  "ng_batch_step", "ng_batch_size", "ng_batch_walk_launches",
+                  "ng_batch_launch_count", "ng_serve_create", "ng_serve_destroy",
+                  "ng_serve_submit", "ng_serve_cancel", "ng_serve_poll", "ng_serve_pending",
+                  "ng_serve_wait", "ng_serve"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -84,7 +130,12 @@ def exported_symbols():
     """Names the header declares (used by the ABI test)."""
     return ["ng_create", "ng_destroy", "ng_set_stream", "ng_build_tree", "ng_tree_force",
             "ng_count_interactions", "ng_pm_force", "ng_step", "ng_tree_export", "ng_type_order",
-            "ng_launch_count", "ng_last_error", "ng_version"]
+            "ng_launch_count", "ng_last_error", "ng_version", "ng_batch_create",
+            "ng_batch_destroy", "ng_batch_step", "ng_batch_size", "ng_batch_walk_launches",
+            "ng_batch_launch_count", "ng_batch_last_error", "ng_serve_create",
+            "ng_serve_destroy", "ng_serve_submit", "ng_serve_cancel", "ng_serve_poll",
+            "ng_serve_pending", "ng_serve_wait", "ng_serve", "ng_serve_last_error",
+            "ng_serve_request_bytes"]
 
 
 def _check(ctx, code):
@@ -207,6 +258,110 @@ def ng_launch_count(ctx):
     v = ctypes.c_uint64(0)
     _check(ctx, lib().ng_launch_count(ctx, ctypes.byref(v)))
     return int(v.value)
+
+
+def _bcheck(b, code):
+    if code != NG_OK:
+        msg = lib().ng_batch_last_error(b) if b else None
+        if not msg:
+            msg = lib().ng_last_error(None)
+        raise NgError(code, msg.decode() if msg else "")
+
+
+def ng_batch_create(params_list, stream=None):
+    arr = (NgParams * len(params_list))(*params_list)
+    b = ctypes.c_void_p()
+    _bcheck(None, lib().ng_batch_create(ctypes.byref(b), len(params_list), arr, _stream(stream)))
+    return b
+
+
+def ng_batch_destroy(b):
+    lib().ng_batch_destroy(b)
+
+
+def ng_batch_step(b, pos, vel, typ, mass, acc, acc_valid, nsteps, dt):
+    """Each argument is a list of torch CUDA tensors, one per simulation."""
+    S = len(pos)
+    n = (ctypes.c_int64 * S)(*[t.numel() for t in typ])
+    P = lambda ts: (ctypes.c_void_p * S)(*[t.data_ptr() for t in ts])
+    _bcheck(b, lib().ng_batch_step(b, n, P(pos), P(vel), P(typ), P(mass), P(acc),
+                                   int(bool(acc_valid)), int(nsteps), float(dt)))
+
+
+def ng_batch_walk_launches(b):
+    return int(lib().ng_batch_walk_launches(b))
+
+
+def ng_batch_launch_count(b):
+    v = ctypes.c_uint64(0)
+    _bcheck(b, lib().ng_batch_launch_count(b, ctypes.byref(v)))
+    return int(v.value)
+
+
+def _scheck(s, code):
+    if code != NG_OK:
+        msg = lib().ng_serve_last_error(s) if s else b""
+        raise NgError(code, msg.decode() if msg else "")
+
+
+def ng_serve_create(slots, hbm_budget):
+    s = ctypes.c_void_p()
+    _scheck(None, lib().ng_serve_create(ctypes.byref(s), int(slots), int(hbm_budget)))
+    return s
+
+
+def ng_serve_destroy(s):
+    lib().ng_serve_destroy(s)
+
+
+def ng_serve_submit(s, req: NgRequest, res: NgResult):
+    i = ctypes.c_int64(-1)
+    _scheck(s, lib().ng_serve_submit(s, ctypes.byref(req), ctypes.byref(res), ctypes.byref(i)))
+    return int(i.value)
+
+
+def ng_serve_cancel(s, rid):
+    _scheck(s, lib().ng_serve_cancel(s, int(rid)))
+
+
+def ng_serve_poll(s):
+    k = ctypes.c_int(0)
+    _scheck(s, lib().ng_serve_poll(s, ctypes.byref(k)))
+    return int(k.value)
+
+
+def ng_serve_pending(s):
+    return int(lib().ng_serve_pending(s))
+
+
+def ng_serve_wait(s, timeout_s):
+    _scheck(s, lib().ng_serve_wait(s, float(timeout_s)))
+
+
+def ng_serve(s, reqs, results, arrival_s=None, timeout_s=600.0):
+    """reqs / results: ctypes arrays of NgRequest / NgResult; arrival_s: numpy float64."""
+    arr = None if arrival_s is None else arrival_s.ctypes.data_as(ctypes.c_void_p)
+    _scheck(s, lib().ng_serve(s, reqs, results, len(reqs), arr, float(timeout_s)))
+
+
+def ng_serve_request_bytes(req: NgRequest):
+    return int(lib().ng_serve_request_bytes(ctypes.byref(req)))
+
+
+def make_request(kind, params: NgParams, pos, typ, mass, vel=None, nsteps=0, dt=0.0,
+                 pos_out=None, vel_out=None, acc_out=None) -> NgRequest:
+    """Request over HOST arrays (numpy or pinned torch CPU tensors); the caller
+    keeps them alive until the request completes."""
+    def addr(a):
+        if a is None:
+            return None
+        return a.data_ptr() if hasattr(a, "data_ptr") else a.ctypes.data
+    r = NgRequest()
+    r.kind, r.nsteps, r.dt, r.params = int(kind), int(nsteps), float(dt), params
+    r.n = int(typ.shape[0])
+    r.pos, r.vel, r.type, r.mass = addr(pos), addr(vel), addr(typ), addr(mass)
+    r.pos_out, r.vel_out, r.acc_out = addr(pos_out), addr(vel_out), addr(acc_out)
+    return r
 
 
 def ng_version():

@@ -123,8 +123,11 @@ int build_tables(ng_ctx* c) {
     t[2 * ncut] = 0.f;
     t[2 * ncut + 1] = 0.f;
   }
+  c->h_tab = h;
   NG_TRY(ensure(c, c->d_tab, h.size() * sizeof(float)));
-  NG_CUDA(c, cudaMemcpy(c->d_tab.p, h.data(), h.size() * sizeof(float), cudaMemcpyHostToDevice));
+  // stream-ordered upload from the context's own host copy (it outlives the copy)
+  NG_CUDA(c, cudaMemcpyAsync(c->d_tab.p, c->h_tab.data(), h.size() * sizeof(float),
+                             cudaMemcpyHostToDevice, c->stream));
   return NG_OK;
 }
 
@@ -145,13 +148,28 @@ __global__ void k_drift(int64_t m, double* __restrict__ pos, const float* __rest
   }
 }
 
+int launch_kick(ng_ctx* c, int64_t n, float* vel, const float* acc, double h) {
+  k_kick<<<device_grid(c, 8), 256, 0, c->stream>>>(3 * n, vel, acc, (float)h);
+  c->launches += 1;
+  NG_CUDA(c, cudaGetLastError());
+  return NG_OK;
+}
+
+int launch_drift(ng_ctx* c, int64_t n, double* pos, const float* vel, double dt) {
+  k_drift<<<device_grid(c, 8), 256, 0, c->stream>>>(3 * n, pos, vel, dt, c->L, 1.0 / c->L,
+                                                    box_is_pow2(c->L));
+  c->launches += 1;
+  NG_CUDA(c, cudaGetLastError());
+  return NG_OK;
+}
+
 // ------------------------------------------------------------ pipeline
 
 static size_t node_bytes(int D) {
   return 1 + 8 + 4 + 4 + 4 + 1 + 4 + (size_t)D * 32 + (size_t)D * 4 + 16 * 3 + (size_t)D * 16;
 }
 
-static int alloc_nodes(ng_ctx* c, int64_t cap) {
+int alloc_nodes(ng_ctx* c, int64_t cap) {
   const int D = c->p.D;
   NG_TRY(ensure(c, c->n_level, cap));
   NG_TRY(ensure(c, c->n_prefix, cap * 8));
@@ -171,7 +189,7 @@ static int alloc_nodes(ng_ctx* c, int64_t cap) {
   return NG_OK;
 }
 
-static int alloc_bodies(ng_ctx* c, int64_t n) {
+int alloc_bodies(ng_ctx* c, int64_t n) {
   NG_TRY(ensure(c, c->body, n * 16));
   NG_TRY(ensure(c, c->bleaf, n * 4));
   NG_TRY(ensure(c, c->groups, n * 8));
@@ -181,7 +199,7 @@ static int alloc_bodies(ng_ctx* c, int64_t n) {
 }
 
 // Everything after the sort; no host synchronisation.
-static int tree_stages(ng_ctx* c) {
+int tree_stages(ng_ctx* c) {
   NG_TRY(build_octree(c));
   NG_TRY(reduce_monopoles(c));
   NG_TRY(build_groups(c));
@@ -189,13 +207,13 @@ static int tree_stages(ng_ctx* c) {
   return NG_OK;
 }
 
-static int read_status(ng_ctx* c, uint32_t* st) {
+int read_status(ng_ctx* c, uint32_t* st) {
   NG_CUDA(c, cudaMemcpyAsync(st, c->status.p, ST_COUNT * 4, cudaMemcpyDeviceToHost, c->stream));
   NG_CUDA(c, cudaStreamSynchronize(c->stream));
   return NG_OK;
 }
 
-static int check_flags(ng_ctx* c, uint32_t flags) {
+int check_flags(ng_ctx* c, uint32_t flags) {
   if (flags & SF_NODE_OVERFLOW) return fail(c, NG_ENOMEM, "tree node capacity exceeded");
   if (flags & SF_STACK_OVERFLOW) return fail(c, NG_ENOMEM, "walk stack capacity exceeded");
   if (flags & SF_GROUP_OVERFLOW) return fail(c, NG_ENOMEM, "walk group capacity exceeded");
@@ -205,8 +223,8 @@ static int check_flags(ng_ctx* c, uint32_t flags) {
 }
 
 // Sort + tree with capacity sizing (synchronises once per attempt).
-static int build_checked(ng_ctx* c, int64_t n, const double* pos, const uint8_t* type,
-                         const float* mass) {
+int build_checked(ng_ctx* c, int64_t n, const double* pos, const uint8_t* type,
+                  const float* mass) {
   c->n = n;
   c->built = false;
   NG_TRY(alloc_bodies(c, n));
@@ -240,7 +258,7 @@ static int build_checked(ng_ctx* c, int64_t n, const double* pos, const uint8_t*
 }
 
 // Short + long acceleration into acc (no host synchronisation).
-static int force_stages(ng_ctx* c, float* acc) {
+int force_stages(ng_ctx* c, float* acc) {
   if (c->p.pm_mesh > 0) {
     NG_TRY(pm_force(c, acc, false));
     NG_TRY(launch_walk(c, acc, true, false));
@@ -252,7 +270,7 @@ static int force_stages(ng_ctx* c, float* acc) {
 
 static bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
 
-static int validate(ng_ctx* c, const ng_params* p) {
+int validate(ng_ctx* c, const ng_params* p) {
   if (!p) return fail(c, NG_EINVAL, "params is NULL");
   if (p->D < 1 || p->D > NG_MAX_SPECIES) return fail(c, NG_EINVAL, "D=%d outside 1..6", p->D);
   if (!(p->box > 0) || !std::isfinite(p->box)) return fail(c, NG_EINVAL, "box must be > 0");
@@ -280,6 +298,23 @@ static int validate(ng_ctx* c, const ng_params* p) {
   if (!(p->rcut_over_rs * rs < 0.5 * p->box))
     return fail(c, NG_EINVAL, "r_cut = %.4g must be below box/2", p->rcut_over_rs * rs);
   return NG_OK;
+}
+
+int ctx_configure(ng_ctx* c, const ng_params* p) {
+  NG_TRY(validate(c, p));
+  c->p = *p;
+  if (c->p.leaf_size == 0) c->p.leaf_size = 8;
+  if (c->p.group_size == 0) c->p.group_size = 32;
+  if (c->p.group_cell == 0) c->p.group_cell = c->p.group_size;
+  c->L = p->box;
+  c->rs = p->pm_mesh > 0 ? p->asmth * p->box / p->pm_mesh : p->asmth * p->box;
+  c->rcut = p->rcut_over_rs * c->rs;
+  c->built = false;
+  if (c->step_exec) {
+    cudaGraphExecDestroy(c->step_exec);
+    c->step_exec = nullptr;
+  }
+  return build_tables(c);
 }
 
 }  // namespace ng
@@ -337,14 +372,17 @@ int ng_destroy(ng_ctx* c) {
   if (!c) return NG_OK;
   if (c->step_exec) cudaGraphExecDestroy(c->step_exec);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
-  if (c->plan_r2c) cufftDestroy(c->plan_r2c);
-  if (c->plan_c2r) cufftDestroy(c->plan_c2r);
+  for (const auto& pl : c->plans) {
+    cufftDestroy(pl.r2c);
+    cufftDestroy(pl.c2r);
+  }
   DevBuf* bufs[] = {&c->d_tab, &c->keys_a, &c->keys_b, &c->vals_a, &c->vals_b, &c->blockhist,
                     &c->skeys, &c->perm, &c->spos, &c->smass, &c->stype, &c->body, &c->bleaf,
                     &c->tperm, &c->scan_part, &c->n_level, &c->n_prefix, &c->n_first,
                     &c->n_count, &c->n_child, &c->n_nchild, &c->n_tmp, &c->n_off, &c->n_m64,
                     &c->n_cnt, &c->n_geo, &c->n_com, &c->n_link, &c->n_mono, &c->groups,
-                    &c->status, &c->counter, &c->acc_tmp, &c->rho, &c->rhok, &c->phi};
+                    &c->status, &c->counter, &c->acc_tmp, &c->rho, &c->rhok, &c->phi,
+                    &c->walk_desc, &c->walk_prefix};
   for (DevBuf* b : bufs) release(*b);
   delete c;
   return NG_OK;

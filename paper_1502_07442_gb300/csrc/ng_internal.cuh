@@ -51,9 +51,8 @@ constexpr int kWalkMaxWarps = 32;
 // budget follows (65536 / threads).
 __host__ __device__ constexpr int walk_warps(int D) { return D <= 3 ? 32 : D == 4 ? 24 : D == 5 ? 20 : 16; }
 
-// Device view of the short-range walk inputs.
-struct WalkArgs {
-  // tree
+// Per-simulation inputs of the walk (device memory, one per simulation).
+struct __align__(16) WalkDesc {
   const float4* geo;        // [node] centre (box units), half side
   const float4* com;        // [node] all-species centre of mass - centre, total mass
   const int4* link;         // [node] child_first, nchild, body_first, body_count
@@ -61,28 +60,33 @@ struct WalkArgs {
   const float4* body;       // [sorted body] offset from its leaf centre, mass
   const uint8_t* btype;     // [sorted body] species
   const uint32_t* bleaf;    // [sorted body] leaf node holding the body
-  const double* spos;       // [3][n] sorted wrapped positions (box units * L)
   const int2* groups;       // [group] first body, count
   const uint32_t* perm;     // sorted -> caller index
-  uint32_t* status;         // device status words
-  // tables
-  const float2* tab;        // [law][ncut + 1] segment {c0, c1}
-  int tab_entries;          // ncut + 1
-  int ncut;
-  int8_t tabid[kMaxD][kMaxD];
-  float G[kMaxD][kMaxD];
-  // geometry
+  uint32_t* status;         // device status words of the simulation
+  float* acc;               // [3][n] caller order
   int64_t n;
-  double L, invL;           // box side and its inverse
-  double inv_dr;            // table units per box unit
+  int accumulate;           // add into acc instead of overwriting
+  float s_tab;              // table units per box unit
   float rcut_box;           // cut-off in box units
   float theta2;
   float eps2_tab;           // softening^2 in table units^2
   float out_scale;          // converts accumulated table-unit sums to acceleration
-  // outputs
-  float* acc;               // [3][n] caller order
+  int8_t tabid[kMaxD][kMaxD];
+  float G[kMaxD][kMaxD];
+};
+
+// Kernel parameters of one walk launch over one or more simulations that
+// share the species count and the law table.
+struct WalkLaunch {
+  const WalkDesc* descs;
+  int ndesc;
+  const uint32_t* gprefix;  // [ndesc + 1] group prefix
+  uint32_t* work;           // work-queue counter
+  const float2* tab;        // [law][ncut + 1] segment {c0, c1}
+  int tab_entries;          // ncut + 1
+  int ncut;
+  int nlaws;
   unsigned long long* counter;  // executed interaction counter (optional)
-  int accumulate;           // add into acc instead of overwriting
 };
 
 }  // namespace ng
@@ -104,6 +108,7 @@ struct ng_ctx {
   int8_t tabid[ng::kMaxD][ng::kMaxD]{};
   double dr_phys = 0;                 // table spacing (physical length)
   ng::DevBuf d_tab;
+  std::vector<float> h_tab;           // host copy (tables of a batch are matched on it)
 
   // particles of the last build
   int64_t n = 0;
@@ -118,13 +123,16 @@ struct ng_ctx {
   ng::DevBuf n_m64, n_cnt, n_geo, n_com, n_link, n_mono;
   ng::DevBuf groups;
   ng::DevBuf status;     // uint32[ST_COUNT]
+  ng::DevBuf walk_desc, walk_prefix;
+  ng::WalkDesc h_walk_desc{};
   ng::DevBuf counter;    // unsigned long long
   ng::DevBuf acc_tmp;    // float[3][n] scratch for summing short + long
 
-  // PM
-  int pm_ready = 0;
-  int pm_n = 0;
-  cufftHandle plan_r2c = 0, plan_c2r = 0;
+  // PM: cuFFT plans cached per (mesh, species count); a context reused for
+  // requests of other sizes keeps its plans
+  struct Plan { int N, D; cufftHandle r2c, c2r; };
+  std::vector<Plan> plans;
+  cufftHandle plan_r2c = 0, plan_c2r = 0;   // the plans of the current (mesh, D)
   ng::DevBuf rho, rhok, phi;
 
   // kernels this library has launched (host-side count)
@@ -180,6 +188,9 @@ int build_octree(ng_ctx* c);                  // needs sorted bodies
 int reduce_monopoles(ng_ctx* c);              // needs octree
 int build_groups(ng_ctx* c);                  // needs octree
 int launch_walk(ng_ctx* c, float* acc, bool accumulate, bool count);
+void fill_walk_desc(ng_ctx* c, float* acc, bool accumulate, WalkDesc* d);
+int launch_walk_descs(ng_ctx* c, cudaStream_t stream, const WalkDesc* d_descs, int ndesc,
+                      uint32_t* d_prefix, uint32_t* d_work, unsigned long long* counter);
 int launch_count(ng_ctx* c, int64_t* counts);  // per-particle walk counts
 int pm_force(ng_ctx* c, float* acc, bool accumulate);
 int type_order(ng_ctx* c);
@@ -189,6 +200,23 @@ int build_tables(ng_ctx* c);
 double short_law_factor(int law, double a, double l, double rs, double rho);
 
 int device_grid(ng_ctx* c, int per_sm);
+
+// Pipeline pieces shared by the single-simulation calls and the batch
+// runtime (ng_api.cu).
+int build_checked(ng_ctx* c, int64_t n, const double* pos, const uint8_t* type, const float* mass);
+int tree_stages(ng_ctx* c);
+int force_stages(ng_ctx* c, float* acc);
+int launch_kick(ng_ctx* c, int64_t n, float* vel, const float* acc, double h);
+int launch_drift(ng_ctx* c, int64_t n, double* pos, const float* vel, double dt);
+int alloc_nodes(ng_ctx* c, int64_t cap);
+int read_status(ng_ctx* c, uint32_t* st);      // synchronises c->stream
+int alloc_bodies(ng_ctx* c, int64_t n);
+// (Re)configure an existing context for new parameters: validation and the
+// law tables (uploaded on c->stream); buffers and cuFFT plans are kept.
+int ctx_configure(ng_ctx* c, const ng_params* p);
+// Host-only validation of a parameter block (message on c).
+int validate(ng_ctx* c, const ng_params* p);
+int check_flags(ng_ctx* c, uint32_t flags);
 bool box_is_pow2(double L);   // L = 2^k: x / L == x * (1 / L) exactly
 
 }  // namespace ng

@@ -153,23 +153,29 @@ __global__ void k_pm_interp(int64_t n, const double* __restrict__ spos,
 
 static int pm_setup(ng_ctx* c) {
   const int N = c->p.pm_mesh, D = c->p.D;
-  if (c->pm_ready && c->pm_n == N) return NG_OK;
   const size_t N3 = (size_t)N * N * N;
   const size_t modes = (size_t)N * N * (N / 2 + 1);
   NG_TRY(ensure(c, c->rho, (size_t)D * N3 * sizeof(float)));
   NG_TRY(ensure(c, c->rhok, (size_t)D * modes * sizeof(cufftComplex)));
   NG_TRY(ensure(c, c->phi, (size_t)D * N3 * sizeof(float)));
+  for (const auto& pl : c->plans)
+    if (pl.N == N && pl.D == D) {
+      c->plan_r2c = pl.r2c;
+      c->plan_c2r = pl.c2r;
+      return NG_OK;
+    }
   int dims[3] = {N, N, N};
-  if (c->plan_r2c) cufftDestroy(c->plan_r2c);
-  if (c->plan_c2r) cufftDestroy(c->plan_c2r);
-  c->plan_r2c = c->plan_c2r = 0;
-  if (cufftPlanMany(&c->plan_r2c, 3, dims, nullptr, 1, (int)N3, nullptr, 1, (int)modes,
+  ng_ctx::Plan pl{N, D, 0, 0};
+  if (cufftPlanMany(&pl.r2c, 3, dims, nullptr, 1, (int)N3, nullptr, 1, (int)modes,
                     CUFFT_R2C, D) != CUFFT_SUCCESS ||
-      cufftPlanMany(&c->plan_c2r, 3, dims, nullptr, 1, (int)modes, nullptr, 1, (int)N3,
-                    CUFFT_C2R, D) != CUFFT_SUCCESS)
+      cufftPlanMany(&pl.c2r, 3, dims, nullptr, 1, (int)modes, nullptr, 1, (int)N3,
+                    CUFFT_C2R, D) != CUFFT_SUCCESS) {
+    if (pl.r2c) cufftDestroy(pl.r2c);
     return fail(c, NG_ECUDA, "cuFFT plan creation failed for a %d^3 mesh, batch %d", N, D);
-  c->pm_ready = 1;
-  c->pm_n = N;
+  }
+  c->plans.push_back(pl);
+  c->plan_r2c = pl.r2c;
+  c->plan_c2r = pl.c2r;
   return NG_OK;
 }
 

@@ -1,0 +1,354 @@
+// Serving runtime (no paper counterpart): a stream of independent force
+// evaluations and short integrations, each a full ngravs solve.
+//
+// Continuous batching: requests wait in a FIFO host queue and are admitted
+// as soon as a slot is free and the device memory the slots hold stays
+// within the byte budget. Every slot owns a context (reconfigured per
+// request, buffers and cuFFT plans kept), a stream and the request's device
+// arrays; an admitted request runs entirely asynchronously on its slot's
+// stream (copy in, tree + PM + walk, the KDK steps, copy out, event), so the
+// work of all admitted requests overlaps on the GPU. Completion is detected
+// by event queries; the status words copied out with the result reveal a
+// tree-capacity overflow, after which the request is rerun with more room.
+// The host loop never blocks on the device except in bounded waits.
+#include <algorithm>
+#include <chrono>
+#include <cstring>
+#include <deque>
+#include <new>
+#include <thread>
+
+#include "ng_internal.cuh"
+
+using namespace ng;
+
+namespace {
+
+double now_s() {
+  using namespace std::chrono;
+  return duration<double>(steady_clock::now().time_since_epoch()).count();
+}
+
+struct Slot {
+  ng_ctx* ctx = nullptr;
+  cudaStream_t stream = nullptr;
+  cudaEvent_t done = nullptr;
+  DevBuf pos, vel, acc, type, mass;
+  uint32_t* h_status = nullptr;       // pinned copy of the status words
+  int64_t req = -1;                   // request in flight (-1: free)
+  size_t bytes = 0;                   // device bytes this slot holds (high-water estimate)
+  int retries = 0;
+};
+
+struct Req {
+  ng_request r;
+  ng_result* out;
+  int state;                          // 0 queued, 1 running, 2 done, 3 cancelled/failed
+};
+
+// Device bytes a request needs in a slot (particle arrays, sort and tree
+// buffers for a node capacity of n + 1024, PM meshes).
+size_t request_bytes(const ng_request& q) {
+  const size_t n = (size_t)q.n, D = (size_t)q.params.D, N = (size_t)q.params.pm_mesh;
+  const size_t body = 53 + 100;
+  const size_t node = 74 + 52 * D;
+  const size_t pm = N ? D * N * N * (N + 2) * 4 * 2 + D * N * N * N * 4 : 0;
+  return n * body + (n + 1024) * node + pm + (1 << 20);
+}
+
+}  // namespace
+
+struct ng_server {
+  std::vector<Slot> slots;
+  std::deque<int64_t> queue;
+  std::vector<Req> reqs;
+  size_t budget = 0;
+  int64_t completed = 0;
+  std::string err;
+};
+
+namespace {
+
+int sfail(ng_server* s, int code, const char* msg) {
+  s->err = msg;
+  return code;
+}
+
+// Enqueue the whole request on the slot's stream.
+int launch_request(ng_server* s, Slot& sl, Req& q) {
+  ng_ctx* c = sl.ctx;
+  c->stream = sl.stream;
+  const ng_request& r = q.r;
+  const int64_t n = r.n;
+  int rc = NG_OK;
+  if (std::memcmp(&c->p, &r.params, sizeof(ng_params)) != 0 || c->h_tab.empty()) {
+    rc = ctx_configure(c, &r.params);
+    if (rc != NG_OK) return rc;
+  }
+  NG_TRY(ensure(c, sl.pos, n * 24));
+  NG_TRY(ensure(c, sl.vel, n * 12));
+  NG_TRY(ensure(c, sl.acc, n * 12));
+  NG_TRY(ensure(c, sl.type, n));
+  NG_TRY(ensure(c, sl.mass, n * 4));
+  NG_TRY(alloc_bodies(c, n));
+  const int64_t want_nodes = n + 1024;
+  if (c->cap_nodes < want_nodes) NG_TRY(alloc_nodes(c, want_nodes));
+  double* pos = as<double>(sl.pos);
+  float* vel = as<float>(sl.vel);
+  float* acc = as<float>(sl.acc);
+  uint8_t* type = as<uint8_t>(sl.type);
+  float* mass = as<float>(sl.mass);
+  NG_CUDA(c, cudaMemcpyAsync(pos, r.pos, n * 24, cudaMemcpyHostToDevice, sl.stream));
+  NG_CUDA(c, cudaMemcpyAsync(type, r.type, n, cudaMemcpyHostToDevice, sl.stream));
+  NG_CUDA(c, cudaMemcpyAsync(mass, r.mass, n * 4, cudaMemcpyHostToDevice, sl.stream));
+  if (r.kind == NG_REQ_STEPS) {
+    if (r.vel) NG_CUDA(c, cudaMemcpyAsync(vel, r.vel, n * 12, cudaMemcpyHostToDevice, sl.stream));
+    else NG_CUDA(c, cudaMemsetAsync(vel, 0, n * 12, sl.stream));
+  }
+  NG_CUDA(c, cudaMemsetAsync(c->status.p, 0, ST_COUNT * 4, sl.stream));
+  c->n = n;
+  // force at the input positions
+  NG_TRY(sort_bodies(c, n, pos, type, mass));
+  NG_TRY(tree_stages(c));
+  NG_TRY(force_stages(c, acc));
+  if (r.kind == NG_REQ_STEPS) {
+    for (int st = 0; st < r.nsteps; ++st) {
+      NG_TRY(launch_kick(c, n, vel, acc, 0.5 * r.dt));
+      NG_TRY(launch_drift(c, n, pos, vel, r.dt));
+      NG_TRY(sort_bodies(c, n, pos, type, mass));
+      NG_TRY(tree_stages(c));
+      NG_TRY(force_stages(c, acc));
+      NG_TRY(launch_kick(c, n, vel, acc, 0.5 * r.dt));
+    }
+    if (r.pos_out) NG_CUDA(c, cudaMemcpyAsync(r.pos_out, pos, n * 24, cudaMemcpyDeviceToHost, sl.stream));
+    if (r.vel_out) NG_CUDA(c, cudaMemcpyAsync(r.vel_out, vel, n * 12, cudaMemcpyDeviceToHost, sl.stream));
+  }
+  if (r.acc_out) NG_CUDA(c, cudaMemcpyAsync(r.acc_out, acc, n * 12, cudaMemcpyDeviceToHost, sl.stream));
+  NG_CUDA(c, cudaMemcpyAsync(sl.h_status, c->status.p, ST_COUNT * 4, cudaMemcpyDeviceToHost, sl.stream));
+  NG_CUDA(c, cudaEventRecord(sl.done, sl.stream));
+  (void)s;
+  return NG_OK;
+}
+
+size_t held_bytes(const ng_server* s) {
+  size_t t = 0;
+  for (const Slot& sl : s->slots) t += sl.bytes;
+  return t;
+}
+
+// Admit queued requests (FIFO) while a slot is free and the budget holds.
+int admit(ng_server* s) {
+  while (!s->queue.empty()) {
+    const int64_t id = s->queue.front();
+    Req& q = s->reqs[id];
+    if (q.state != 0) {
+      s->queue.pop_front();
+      continue;
+    }
+    const size_t need = request_bytes(q.r);
+    int pick = -1;
+    for (size_t k = 0; k < s->slots.size(); ++k) {
+      Slot& sl = s->slots[k];
+      if (sl.req >= 0) continue;
+      const size_t after = held_bytes(s) - sl.bytes + std::max(sl.bytes, need);
+      if (after <= s->budget) {
+        pick = (int)k;
+        break;
+      }
+    }
+    if (pick < 0) return NG_OK;           // wait for a slot or for memory
+    Slot& sl = s->slots[pick];
+    s->queue.pop_front();
+    sl.bytes = std::max(sl.bytes, need);
+    sl.req = id;
+    sl.retries = 0;
+    q.state = 1;
+    q.out->t_admit = now_s();
+    const int rc = launch_request(s, sl, q);
+    if (rc != NG_OK) {
+      // the slot's stream may hold part of the request: let it drain
+      cudaStreamSynchronize(sl.stream);
+      cudaGetLastError();
+      q.state = 3;
+      q.out->status = rc;
+      q.out->t_done = now_s();
+      sl.req = -1;
+      s->completed++;
+    }
+  }
+  return NG_OK;
+}
+
+// Collect finished requests; returns the number completed by this call.
+int reap(ng_server* s) {
+  int got = 0;
+  for (Slot& sl : s->slots) {
+    if (sl.req < 0) continue;
+    const cudaError_t e = cudaEventQuery(sl.done);
+    if (e == cudaErrorNotReady) continue;
+    Req& q = s->reqs[sl.req];
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      q.out->status = NG_ECUDA;
+    } else if ((sl.h_status[ST_FLAGS] & SF_NODE_OVERFLOW) && sl.retries < 4) {
+      // rerun with room for the node count the build reported
+      ng_ctx* c = sl.ctx;
+      const int64_t need = (int64_t)sl.h_status[ST_NODES_NEEDED];
+      if (alloc_nodes(c, std::max<int64_t>(2 * need, 2 * c->cap_nodes)) == NG_OK) {
+        sl.retries++;
+        if (launch_request(s, sl, q) == NG_OK) continue;
+      }
+      q.out->status = NG_ENOMEM;
+    } else {
+      q.out->status = sl.h_status[ST_FLAGS] ? check_flags(sl.ctx, sl.h_status[ST_FLAGS]) : NG_OK;
+    }
+    q.state = q.out->status == NG_OK ? 2 : 3;
+    q.out->t_done = now_s();
+    sl.req = -1;
+    s->completed++;
+    got++;
+  }
+  return got;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ng_serve_create(ng_server** out, int slots, size_t hbm_budget) {
+  if (!out || slots < 1 || slots > 256 || hbm_budget == 0) return NG_EINVAL;
+  *out = nullptr;
+  ng_server* s = new (std::nothrow) ng_server();
+  if (!s) return NG_ENOMEM;
+  s->budget = hbm_budget;
+  ng_params p{};
+  p.D = 1;
+  p.G[0][0] = 1.0;
+  p.eps = 1e-3;
+  p.box = 1.0;
+  p.asmth = 0.05;
+  p.rcut_over_rs = 4.5;
+  p.theta = 0.5;
+  for (int k = 0; k < slots; ++k) {
+    Slot sl;
+    if (cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess ||
+        cudaHostAlloc((void**)&sl.h_status, ST_COUNT * 4, cudaHostAllocDefault) != cudaSuccess ||
+        ng_create(&sl.ctx, &p, sl.stream) != NG_OK) {
+      cudaGetLastError();
+      s->slots.push_back(sl);
+      ng_serve_destroy(s);
+      return NG_ECUDA;
+    }
+    s->slots.push_back(sl);
+  }
+  *out = s;
+  return NG_OK;
+}
+
+int ng_serve_destroy(ng_server* s) {
+  if (!s) return NG_OK;
+  for (Slot& sl : s->slots) {
+    if (sl.stream) cudaStreamSynchronize(sl.stream);
+    if (sl.ctx) {
+      release(sl.pos);
+      release(sl.vel);
+      release(sl.acc);
+      release(sl.type);
+      release(sl.mass);
+      ng_destroy(sl.ctx);
+    }
+    if (sl.h_status) cudaFreeHost(sl.h_status);
+    if (sl.done) cudaEventDestroy(sl.done);
+    if (sl.stream) cudaStreamDestroy(sl.stream);
+  }
+  delete s;
+  return NG_OK;
+}
+
+int ng_serve_submit(ng_server* s, const ng_request* r, ng_result* out, int64_t* id) {
+  if (!s || !r || !out) return NG_EINVAL;
+  std::memset(out, 0, sizeof(*out));
+  out->t_submit = now_s();
+  if (r->n < 1 || r->n >= ((int64_t)1 << 31) || !r->pos || !r->type || !r->mass ||
+      (r->kind != NG_REQ_FORCE && r->kind != NG_REQ_STEPS) ||
+      (r->kind == NG_REQ_STEPS && (r->nsteps < 0 || r->nsteps > 100000)))
+    return sfail(s, NG_EINVAL, "malformed request (n, arrays, kind or nsteps)");
+  ng_ctx probe;   // host-only validation, no device work
+  if (validate(&probe, &r->params) != NG_OK) return sfail(s, NG_EINVAL, probe.err.c_str());
+  if (request_bytes(*r) > s->budget)
+    return sfail(s, NG_EBUSY, "request larger than the whole device byte budget");
+  Req q{*r, out, 0};
+  s->reqs.push_back(q);
+  const int64_t k = (int64_t)s->reqs.size() - 1;
+  s->queue.push_back(k);
+  out->status = 1;                    // pending
+  if (id) *id = k;
+  return NG_OK;
+}
+
+int ng_serve_cancel(ng_server* s, int64_t id) {
+  if (!s || id < 0 || id >= (int64_t)s->reqs.size()) return NG_EINVAL;
+  Req& q = s->reqs[id];
+  if (q.state != 0) return NG_ESTATE;   // admitted work is not interrupted
+  q.state = 3;
+  q.out->status = NG_ESTATE;
+  q.out->t_done = now_s();
+  s->completed++;
+  return NG_OK;
+}
+
+int ng_serve_poll(ng_server* s, int* ncompleted) {
+  if (!s) return NG_EINVAL;
+  const int got = reap(s);
+  admit(s);
+  if (ncompleted) *ncompleted = got;
+  return NG_OK;
+}
+
+int ng_serve_pending(const ng_server* s) {
+  if (!s) return 0;
+  return (int)((int64_t)s->reqs.size() - s->completed);
+}
+
+int ng_serve_wait(ng_server* s, double timeout_s) {
+  if (!s) return NG_EINVAL;
+  const double t0 = now_s();
+  while (ng_serve_pending(s) > 0) {
+    ng_serve_poll(s, nullptr);
+    if (ng_serve_pending(s) == 0) break;
+    if (now_s() - t0 > timeout_s) return sfail(s, NG_ETIMEOUT, "wait timed out");
+    std::this_thread::sleep_for(std::chrono::microseconds(50));
+  }
+  return NG_OK;
+}
+
+int ng_serve(ng_server* s, const ng_request* reqs, ng_result* res, int nreq,
+             const double* arrival_s, double timeout_s) {
+  if (!s || !reqs || !res || nreq < 0) return NG_EINVAL;
+  const double t0 = now_s();
+  int next = 0;
+  while (next < nreq || ng_serve_pending(s) > 0) {
+    const double t = now_s() - t0;
+    while (next < nreq && (!arrival_s || arrival_s[next] <= t)) {
+      const int rc = ng_serve_submit(s, &reqs[next], &res[next], nullptr);
+      if (rc != NG_OK) {
+        res[next].status = rc;
+        res[next].t_done = now_s();
+      }
+      if (arrival_s) res[next].t_submit = t0 + arrival_s[next];
+      ++next;
+    }
+    int got = 0;
+    ng_serve_poll(s, &got);
+    if (now_s() - t0 > timeout_s) return sfail(s, NG_ETIMEOUT, "trace timed out");
+    if (!got) std::this_thread::sleep_for(std::chrono::microseconds(20));
+  }
+  return NG_OK;
+}
+
+const char* ng_serve_last_error(const ng_server* s) { return s ? s->err.c_str() : "no server"; }
+
+size_t ng_serve_request_bytes(const ng_request* r) { return r ? request_bytes(*r) : 0; }
+
+}  // extern "C"

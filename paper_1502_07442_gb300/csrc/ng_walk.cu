@@ -26,6 +26,7 @@ namespace ng {
 
 template <int D>
 struct __align__(16) WarpSmem {
+  WalkDesc desc;              // batched launches: the current item's simulation
   float4 list[D][kListCap];   // records per active species, table units
   float4 leafc[32];           // opened leaves: centre offset from the origin (box units)
   int2 leafb[32];             // opened leaves: first body, body count
@@ -38,41 +39,57 @@ constexpr int kMagicBits = 0x4B000000;
 
 __device__ __forceinline__ float wrap_unit(float d) { return d - rintf(d); }
 
+// Each warp copies its item's descriptor (one per simulation) from device
+// memory into shared memory and reads the fields from there.
+#define DESC(f) (ws->desc.f)
+
 template <int D>
-__global__ void __launch_bounds__(walk_warps(D) * 32, 1) k_walk(WalkArgs a, int nlaws) {
+__global__ void __launch_bounds__(walk_warps(D) * 32, 1) k_walk(WalkLaunch L) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2* tab = reinterpret_cast<float2*>(smem_raw);
-  const int ntab = nlaws * a.tab_entries;
-  for (int i = threadIdx.x; i < ntab; i += blockDim.x) tab[i] = a.tab[i];
+  const int ntab = L.nlaws * L.tab_entries;
+  for (int i = threadIdx.x; i < ntab; i += blockDim.x) tab[i] = L.tab[i];
   const size_t tab_bytes = ((size_t)ntab * sizeof(float2) + 15) & ~(size_t)15;
   WarpSmem<D>* ws = reinterpret_cast<WarpSmem<D>*>(smem_raw + tab_bytes) + (threadIdx.x >> 5);
   __syncthreads();
 
   const int lane = threadIdx.x & 31;
   const uint32_t lt = (1u << lane) - 1u;
-  if (a.status[ST_FLAGS] & SF_NODE_OVERFLOW) return;   // truncated tree: do not walk it
-  const uint32_t nnodes = a.status[ST_LEVELS + kMaxLevel + 1];
-  uint32_t ngroups = a.status[ST_NGROUPS];
-  if (ngroups > (uint32_t)a.n) ngroups = (uint32_t)a.n;
-  const float rc2 = a.rcut_box * a.rcut_box;
-  const float s_tab = (float)a.inv_dr;
-  const int clampbits = kMagicBits + a.ncut;
-  const float eps2 = a.eps2_tab;
+  const uint32_t total_groups = L.gprefix[L.ndesc];
+  const int clampbits = kMagicBits + L.ncut;
   unsigned long long nint = 0;
 
   while (true) {
+    // one work item = one group of one simulation (all simulations of the
+    // launch share the law table and the species count)
     uint32_t g = 0;
-    if (lane == 0) g = atomicAdd(&a.status[ST_WORK], 1u);
+    if (lane == 0) g = atomicAdd(L.work, 1u);
     g = __shfl_sync(0xffffffffu, g, 0);
-    if (g >= ngroups) break;
-    const int2 gr = a.groups[g];
+    if (g >= total_groups) break;
+    int lo_s = 0, hi_s = L.ndesc - 1;
+    while (lo_s < hi_s) {
+      const int mid = (lo_s + hi_s + 1) >> 1;
+      if (L.gprefix[mid] <= g) lo_s = mid; else hi_s = mid - 1;
+    }
+    __syncwarp();
+    {
+      const int4* src = reinterpret_cast<const int4*>(L.descs + lo_s);
+      int4* dst = reinterpret_cast<int4*>(&ws->desc);
+      for (int i = lane; i < (int)(sizeof(WalkDesc) / 16); i += 32) dst[i] = src[i];
+    }
+    __syncwarp();
+    const uint32_t nnodes = DESC(status)[ST_LEVELS + kMaxLevel + 1];
+    const float rc2 = DESC(rcut_box) * DESC(rcut_box);
+    const float s_tab = DESC(s_tab);
+    const float eps2 = DESC(eps2_tab);
+    const int2 gr = DESC(groups)[g - L.gprefix[lo_s]];
     const int nact = gr.y;
     const bool active = lane < nact;
     const int64_t p = gr.x + (active ? lane : 0);
-    const int s = a.btype[p];
+    const int s = DESC(btype)[p];
     float ox, oy, oz, gx, gy, gz;
-    const float4 lg = a.geo[a.bleaf[p]];
-    const float4 bd = a.body[p];
+    const float4 lg = DESC(geo)[DESC(bleaf)[p]];
+    const float4 bd = DESC(body)[p];
     {
       // bounding box (box units, FP32; no FP64 in the walk) relative to the
       // leaf centre of the group's first body; group bodies lie in one cell
@@ -127,7 +144,7 @@ __global__ void __launch_bounds__(walk_warps(D) * 32, 1) k_walk(WalkArgs a, int 
 #pragma unroll
         for (int q = 0; q < D; ++q) cnt = (q == t) ? lc[q] : cnt;
         if (cnt > kListCap - 32 || (drain && cnt > 0)) {
-          const float2* __restrict__ T = tab + (int)a.tabid[s][t] * a.tab_entries;
+          const float2* __restrict__ T = tab + (int)DESC(tabid[s][t]) * L.tab_entries;
           const float4* __restrict__ list = ws->list[t];
           float sx = 0.f, sy = 0.f, sz = 0.f;
           __syncwarp();
@@ -179,8 +196,8 @@ __global__ void __launch_bounds__(walk_warps(D) * 32, 1) k_walk(WalkArgs a, int 
           }
           const int b = ws->leafb[lo].x + (f - ws->leafo[lo]);
           const float4 lc4 = ws->leafc[lo];
-          const float4 bb = a.body[b];
-          bt = a.btype[b];
+          const float4 bb = DESC(body)[b];
+          bt = DESC(btype)[b];
           rec = make_float4((lc4.x + bb.x) * s_tab, (lc4.y + bb.y) * s_tab, (lc4.z + bb.z) * s_tab, bb.w);
         }
 #pragma unroll
@@ -210,9 +227,9 @@ __global__ void __launch_bounds__(walk_warps(D) * 32, 1) k_walk(WalkArgs a, int 
       float dcx = 0.f, dcy = 0.f, dcz = 0.f;
       int4 lk = make_int4(0, 0, 0, 0);
       if (node >= 0) {
-        const float4 ge = a.geo[node];
-        const float4 cm = a.com[node];
-        lk = a.link[node];
+        const float4 ge = DESC(geo)[node];
+        const float4 cm = DESC(com)[node];
+        lk = DESC(link)[node];
         dcx = wrap_unit(ge.x - ox);
         dcy = wrap_unit(ge.y - oy);
         dcz = wrap_unit(ge.z - oz);
@@ -226,7 +243,7 @@ __global__ void __launch_bounds__(walk_warps(D) * 32, 1) k_walk(WalkArgs a, int 
           const float ez = fmaxf(0.f, fabsf(dcz + cm.z) - gz);
           const float dd2 = ex * ex + ey * ey + ez * ez;
           const float side = 2.f * ge.w;
-          if (d2min > 0.f && side * side < a.theta2 * dd2) cls = 1;
+          if (d2min > 0.f && side * side < DESC(theta2) * dd2) cls = 1;
           else cls = lk.y == 0 ? 2 : 3;
         }
       }
@@ -235,7 +252,7 @@ __global__ void __launch_bounds__(walk_warps(D) * 32, 1) k_walk(WalkArgs a, int 
 #pragma unroll
         for (int t = 0; t < D; ++t) {
           float4 mo = make_float4(0.f, 0.f, 0.f, 0.f);
-          if (cls == 1) mo = a.mono[(size_t)node * D + t];
+          if (cls == 1) mo = DESC(mono)[(size_t)node * D + t];
           const bool has = mo.w > 0.f;
           const uint32_t b = __ballot_sync(0xffffffffu, has);
           if (has)
@@ -284,34 +301,77 @@ __global__ void __launch_bounds__(walk_warps(D) * 32, 1) k_walk(WalkArgs a, int 
     }
     __syncwarp();
     if (overflow) {
-      if (lane == 0) atomicOr(&a.status[ST_FLAGS], (uint32_t)SF_STACK_OVERFLOW);
+      if (lane == 0) atomicOr(&DESC(status)[ST_FLAGS], (uint32_t)SF_STACK_OVERFLOW);
       continue;
     }
     if (active) {
       float fx = 0.f, fy = 0.f, fz = 0.f;
 #pragma unroll
       for (int t = 0; t < D; ++t) {
-        const float G = a.G[s][t];
+        const float G = DESC(G[s][t]);
         fx = fmaf(G, ax[t], fx);
         fy = fmaf(G, ay[t], fy);
         fz = fmaf(G, az[t], fz);
       }
-      const uint32_t i = a.perm[p];
-      fx *= a.out_scale;
-      fy *= a.out_scale;
-      fz *= a.out_scale;
-      if (a.accumulate) {
-        a.acc[i] += fx;
-        a.acc[a.n + i] += fy;
-        a.acc[2 * a.n + i] += fz;
+      const uint32_t i = DESC(perm)[p];
+      float* acc = DESC(acc);
+      const int64_t nb = DESC(n);
+      fx *= DESC(out_scale);
+      fy *= DESC(out_scale);
+      fz *= DESC(out_scale);
+      if (DESC(accumulate)) {
+        acc[i] += fx;
+        acc[nb + i] += fy;
+        acc[2 * nb + i] += fz;
       } else {
-        a.acc[i] = fx;
-        a.acc[a.n + i] = fy;
-        a.acc[2 * a.n + i] = fz;
+        acc[i] = fx;
+        acc[nb + i] = fy;
+        acc[2 * nb + i] = fz;
       }
     }
   }
-  if (a.counter && lane == 0 && nint) atomicAdd(a.counter, nint);
+  if (L.counter && lane == 0 && nint) atomicAdd(L.counter, nint);
+}
+
+#undef DESC
+
+// Group-count prefix over the descriptors of one launch; zero work counter.
+// Simulations whose tree overflowed contribute no groups.
+__global__ void __launch_bounds__(1024) k_walk_prep(const WalkDesc* __restrict__ descs, int ndesc,
+                                                    uint32_t* gprefix, uint32_t* work) {
+  __shared__ uint32_t part[1024];
+  const int per = (ndesc + 1023) / 1024;
+  const int b0 = threadIdx.x * per;
+  uint32_t sum = 0;
+  for (int i = b0; i < b0 + per && i < ndesc; ++i) {
+    const uint32_t* st = descs[i].status;
+    uint32_t ng = st[ST_NGROUPS];
+    if (ng > (uint64_t)descs[i].n) ng = (uint32_t)descs[i].n;
+    if (st[ST_FLAGS] & SF_NODE_OVERFLOW) ng = 0;
+    sum += ng;
+  }
+  part[threadIdx.x] = sum;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t run = 0;
+    for (int t = 0; t < 1024; ++t) {
+      const uint32_t v = part[t];
+      part[t] = run;
+      run += v;
+    }
+    gprefix[ndesc] = run;
+    *work = 0;
+  }
+  __syncthreads();
+  uint32_t run = part[threadIdx.x];
+  for (int i = b0; i < b0 + per && i < ndesc; ++i) {
+    gprefix[i] = run;
+    const uint32_t* st = descs[i].status;
+    uint32_t ng = st[ST_NGROUPS];
+    if (ng > (uint64_t)descs[i].n) ng = (uint32_t)descs[i].n;
+    if (st[ST_FLAGS] & SF_NODE_OVERFLOW) ng = 0;
+    run += ng;
+  }
 }
 
 template <int D>
@@ -321,65 +381,90 @@ static size_t walk_smem(int nlaws, int entries, int nwarps) {
 }
 
 template <int D>
-static int launch_walk_d(ng_ctx* c, WalkArgs& a) {
+static int launch_walk_d(ng_ctx* c, cudaStream_t stream, const WalkLaunch& L) {
   int nwarps = walk_warps(D);
-  while (nwarps > 1 && walk_smem<D>(c->nlaws, a.tab_entries, nwarps) > c->smem_optin) --nwarps;
-  const size_t smem = walk_smem<D>(c->nlaws, a.tab_entries, nwarps);
+  while (nwarps > 1 && walk_smem<D>(L.nlaws, L.tab_entries, nwarps) > c->smem_optin) --nwarps;
+  const size_t smem = walk_smem<D>(L.nlaws, L.tab_entries, nwarps);
   if (smem > c->smem_optin)
     return fail(c, NG_ENOMEM, "walk needs %zu B shared memory (max %zu)", smem, c->smem_optin);
   NG_CUDA(c, cudaFuncSetAttribute(k_walk<D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)smem));
   int per_sm = 0;
-  NG_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walk<D>, nwarps * 32, smem));
+  NG_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walk<D>, nwarps * 32,
+                                                           smem));
   if (per_sm < 1) per_sm = 1;
-  k_walk<D><<<c->nsm * per_sm, nwarps * 32, smem, c->stream>>>(a, c->nlaws);
+  k_walk<D><<<c->nsm * per_sm, nwarps * 32, smem, stream>>>(L);
   c->launches += 1;
   NG_CUDA(c, cudaGetLastError());
   return NG_OK;
 }
 
-int launch_walk(ng_ctx* c, float* acc, bool accumulate, bool count) {
-  WalkArgs a{};
-  a.geo = as<float4>(c->n_geo);
-  a.com = as<float4>(c->n_com);
-  a.link = as<int4>(c->n_link);
-  a.mono = as<float4>(c->n_mono);
-  a.body = as<float4>(c->body);
-  a.btype = as<uint8_t>(c->stype);
-  a.bleaf = as<uint32_t>(c->bleaf);
-  a.spos = as<double>(c->spos);
-  a.groups = as<int2>(c->groups);
-  a.perm = as<uint32_t>(c->vals_a);
-  a.status = as<uint32_t>(c->status);
-  a.tab = as<float2>(c->d_tab);
-  a.tab_entries = c->ncut + 1;
-  a.ncut = c->ncut;
+void fill_walk_desc(ng_ctx* c, float* acc, bool accumulate, WalkDesc* d) {
+  d->geo = as<float4>(c->n_geo);
+  d->com = as<float4>(c->n_com);
+  d->link = as<int4>(c->n_link);
+  d->mono = as<float4>(c->n_mono);
+  d->body = as<float4>(c->body);
+  d->btype = as<uint8_t>(c->stype);
+  d->bleaf = as<uint32_t>(c->bleaf);
+  d->groups = as<int2>(c->groups);
+  d->perm = as<uint32_t>(c->vals_a);
+  d->status = as<uint32_t>(c->status);
+  d->acc = acc;
+  d->n = c->n;
+  d->accumulate = accumulate ? 1 : 0;
+  d->s_tab = (float)(c->L / c->dr_phys);
+  d->rcut_box = (float)(c->rcut / c->L);
+  d->theta2 = (float)(c->p.theta * c->p.theta);
+  const double eps_tab = c->p.eps / c->dr_phys;
+  d->eps2_tab = (float)(eps_tab * eps_tab);
+  d->out_scale = (float)(1.0 / (c->dr_phys * c->dr_phys));
   for (int i = 0; i < kMaxD; ++i)
     for (int j = 0; j < kMaxD; ++j) {
-      a.tabid[i][j] = c->tabid[i][j];
-      a.G[i][j] = (float)c->p.G[i][j];
+      d->tabid[i][j] = c->tabid[i][j];
+      d->G[i][j] = (float)c->p.G[i][j];
     }
-  a.n = c->n;
-  a.L = c->L;
-  a.invL = 1.0 / c->L;
-  a.inv_dr = c->L / c->dr_phys;
-  a.rcut_box = (float)(c->rcut / c->L);
-  a.theta2 = (float)(c->p.theta * c->p.theta);
-  const double eps_tab = c->p.eps / c->dr_phys;
-  a.eps2_tab = (float)(eps_tab * eps_tab);
-  a.out_scale = (float)(1.0 / (c->dr_phys * c->dr_phys));
-  a.acc = acc;
-  a.counter = count ? as<unsigned long long>(c->counter) : nullptr;
-  a.accumulate = accumulate ? 1 : 0;
-  NG_CUDA(c, cudaMemsetAsync(as<uint32_t>(c->status) + ST_WORK, 0, sizeof(uint32_t), c->stream));
+}
+
+static int dispatch_walk(ng_ctx* c, cudaStream_t stream, const WalkLaunch& L) {
   switch (c->p.D) {
-    case 1: return launch_walk_d<1>(c, a);
-    case 2: return launch_walk_d<2>(c, a);
-    case 3: return launch_walk_d<3>(c, a);
-    case 4: return launch_walk_d<4>(c, a);
-    case 5: return launch_walk_d<5>(c, a);
-    default: return launch_walk_d<6>(c, a);
+    case 1: return launch_walk_d<1>(c, stream, L);
+    case 2: return launch_walk_d<2>(c, stream, L);
+    case 3: return launch_walk_d<3>(c, stream, L);
+    case 4: return launch_walk_d<4>(c, stream, L);
+    case 5: return launch_walk_d<5>(c, stream, L);
+    default: return launch_walk_d<6>(c, stream, L);
   }
+}
+
+int launch_walk_descs(ng_ctx* c, cudaStream_t stream, const WalkDesc* d_descs, int ndesc,
+                      uint32_t* d_prefix, uint32_t* d_work, unsigned long long* counter) {
+  k_walk_prep<<<1, 1024, 0, stream>>>(d_descs, ndesc, d_prefix, d_work);
+  c->launches += 1;
+  NG_CUDA(c, cudaGetLastError());
+  WalkLaunch L;
+  L.descs = d_descs;
+  L.ndesc = ndesc;
+  L.gprefix = d_prefix;
+  L.work = d_work;
+  L.tab = as<float2>(c->d_tab);
+  L.tab_entries = c->ncut + 1;
+  L.ncut = c->ncut;
+  L.nlaws = c->nlaws;
+  L.counter = counter;
+  return dispatch_walk(c, stream, L);
+}
+
+int launch_walk(ng_ctx* c, float* acc, bool accumulate, bool count) {
+  NG_TRY(ensure(c, c->walk_desc, sizeof(WalkDesc)));
+  NG_TRY(ensure(c, c->walk_prefix, 4 * sizeof(uint32_t)));
+  // the host copy lives in the context, so a captured copy stays valid
+  fill_walk_desc(c, acc, accumulate, &c->h_walk_desc);
+  NG_CUDA(c, cudaMemcpyAsync(c->walk_desc.p, &c->h_walk_desc, sizeof(WalkDesc),
+                             cudaMemcpyHostToDevice, c->stream));
+  uint32_t* pre = as<uint32_t>(c->walk_prefix);
+  return launch_walk_descs(c, c->stream, as<WalkDesc>(c->walk_desc), 1, pre, pre + 2,
+                           count ? as<unsigned long long>(c->counter) : nullptr);
 }
 
 // ------------------------------------------------ per-particle count walk

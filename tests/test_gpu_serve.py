@@ -1,0 +1,153 @@
+"""Serving: requests that run concurrently (continuous batching over slots
+and streams) give the same results as each request served alone; admission
+respects the byte budget; queued requests can be cancelled; malformed
+requests are rejected on the host; bounded waits time out into a status.
+Same-result tolerance: the walk is deterministic, the CIC atomics may add in
+another order (99 % of bodies within 1e-5 relative, all within 1e-3)."""
+import numpy as np
+import pytest
+
+from common import ng_params, small_clustered
+from paper_1502_07442_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ng():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1502_07442_gb300 import binding, build
+    build.build()
+    return binding
+
+
+def _workload(seed, count=10):
+    rng = inputs.rng_for(seed)
+    out = []
+    for k in range(count):
+        n = inputs.log_uniform_int(rng, 10, 14)
+        D = int(rng.integers(1, 7))
+        w = small_clustered(n, D, seed * 100 + k, mesh=inputs.serve_mesh(n))
+        kind = int(k % 2)
+        out.append(dict(w=w, kind=kind, nsteps=4 if kind else 0))
+    return out
+
+
+def _run(ng, items, slots, budget, cancel=None):
+    reqs = (ng.NgRequest * len(items))()
+    res = (ng.NgResult * len(items))()
+    outs = []
+    for i, it in enumerate(items):
+        w = it["w"]
+        n = w["type"].size
+        acc = np.zeros((3, n), np.float32)
+        pos = np.zeros((3, n))
+        vel = np.zeros((3, n), np.float32)
+        outs.append(dict(acc=acc, pos=pos, vel=vel))
+        reqs[i] = ng.make_request(it["kind"], ng_params(w["params"]), w["pos"], w["type"], w["mass"],
+                                  nsteps=it["nsteps"], dt=1e-3, pos_out=pos, vel_out=vel, acc_out=acc)
+    s = ng.ng_serve_create(slots, budget)
+    try:
+        if cancel is None:
+            ng.ng_serve(s, reqs, res, None, 300.0)
+        else:
+            ids = [ng.ng_serve_submit(s, reqs[i], res[i]) for i in range(len(items))]
+            ng.ng_serve_cancel(s, ids[cancel])
+            ng.ng_serve_wait(s, 300.0)
+    finally:
+        ng.ng_serve_destroy(s)
+    return outs, res
+
+
+def _close(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    rel = np.linalg.norm(a - b, axis=0) / np.maximum(np.linalg.norm(b, axis=0), 1e-30)
+    return np.percentile(rel, 99) <= 1e-5 and rel.max() <= 1e-3
+
+
+def test_mix_equals_alone(ng):
+    items = _workload(81)
+    mixed, res = _run(ng, items, slots=6, budget=8 << 30)
+    assert all(r.status == 0 for r in res)
+    # overlapping service: some request was admitted before an earlier one finished
+    assert any(res[i].t_admit < res[i - 1].t_done for i in range(1, len(items)))
+    for it, got in zip(items, mixed):
+        alone, r1 = _run(ng, [it], slots=1, budget=8 << 30)
+        assert r1[0].status == 0
+        assert _close(got["acc"], alone[0]["acc"])
+        if it["kind"]:
+            w = it["w"]
+            assert _close(got["vel"], alone[0]["vel"])
+            moved = alone[0]["pos"] - w["pos"]
+            d = got["pos"] - alone[0]["pos"]
+            rel = np.linalg.norm(d - np.rint(d), axis=0) / np.maximum(
+                np.linalg.norm(moved - np.rint(moved), axis=0), 1e-300)
+            assert np.percentile(rel, 99) <= 1e-5 and rel.max() <= 1e-3
+
+
+def test_tight_budget_holds_and_completes(ng):
+    items = _workload(82, count=6)
+    sizes = []
+    for it in items:
+        w = it["w"]
+        sizes.append(ng.ng_serve_request_bytes(
+            ng.make_request(it["kind"], ng_params(w["params"]), w["pos"], w["type"], w["mass"])))
+    budget = int(1.2 * max(sizes))                 # at most one or two requests at once
+    mixed, _ = _run(ng, items, slots=6, budget=8 << 30)
+    tight, res = _run(ng, items, slots=6, budget=budget)
+    assert all(r.status == 0 for r in res)
+    # at every admission, the requests then running fit in the budget
+    for i in range(len(items)):
+        t = res[i].t_admit
+        running = [j for j in range(len(items)) if res[j].t_admit <= t < res[j].t_done]
+        assert sum(sizes[j] for j in running) <= budget
+    for x, y in zip(mixed, tight):
+        assert _close(x["acc"], y["acc"])
+
+
+def test_cancel_and_reject(ng):
+    items = _workload(83, count=4)
+    outs, res = _run(ng, items, slots=1, budget=1 << 27, cancel=3)
+    assert [r.status for r in res[:3]] == [0, 0, 0]
+    assert res[3].status == ng.NG_ESTATE
+    s = ng.ng_serve_create(2, 1 << 30)
+    try:
+        w = items[0]["w"]
+        bad = ng.make_request(0, ng_params(w["params"]), w["pos"], w["type"], w["mass"])
+        bad.n = 0
+        with pytest.raises(ng.NgError) as e:
+            ng.ng_serve_submit(s, bad, ng.NgResult())
+        assert e.value.code == ng.NG_EINVAL
+        p = ng_params(w["params"])
+        p.D = 7
+        with pytest.raises(ng.NgError) as e:
+            ng.ng_serve_submit(s, ng.make_request(0, p, w["pos"], w["type"], w["mass"]), ng.NgResult())
+        assert e.value.code == ng.NG_EINVAL
+        big = ng.make_request(0, ng_params(w["params"]), w["pos"], w["type"], w["mass"])
+        big.n = 1 << 30
+        with pytest.raises(ng.NgError) as e:
+            ng.ng_serve_submit(s, big, ng.NgResult())
+        assert e.value.code == ng.NG_EBUSY
+    finally:
+        ng.ng_serve_destroy(s)
+
+
+def test_bounded_wait_times_out_into_status(ng):
+    w = small_clustered(60000, 3, 84, mesh=64)
+    s = ng.ng_serve_create(1, 8 << 30)
+    acc = np.zeros((3, 60000), np.float32)
+    r = ng.make_request(1, ng_params(w["params"]), w["pos"], w["type"], w["mass"], nsteps=3,
+                        dt=1e-3, acc_out=acc)
+    res = ng.NgResult()
+    try:
+        ng.ng_serve_submit(s, r, res)
+        with pytest.raises(ng.NgError) as e:
+            ng.ng_serve_wait(s, 0.0)
+        assert e.value.code == ng.NG_ETIMEOUT
+        ng.ng_serve_wait(s, 300.0)                  # the context stays usable
+        assert res.status == 0 and np.isfinite(acc).all()
+    finally:
+        ng.ng_serve_destroy(s)
