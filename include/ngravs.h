@@ -299,6 +299,25 @@ size_t ng_serve_request_bytes(const ng_request* r);
  */
 int ng_launch_count(const ng_ctx* ctx, uint64_t* out);
 
+/*
+ * Sorted keys and permutation without any allocation (the paper has no
+ * counterpart: this is for callers that cannot call cudaMalloc, e.g. code
+ * running while another framework holds the memory pool, or a host that
+ * only lends the library its own buffers). Computes exactly the keys_out /
+ * perm_out of ng_build_tree (same wrap, 63-bit key, stable order) for
+ * 1 <= n <= 2^18 bodies, with its scratch in one fixed device array of about
+ * 3.4 MB that every GPU loading the library holds until the process exits.
+ * pos (double[3][n]), type (uint8[n]), keys_out (uint64[n]) and perm_out
+ * (uint32[n]) are caller DEVICE arrays; stream as in ng_create. Returns
+ * NG_EINVAL for n outside [1, 2^18], NULL arrays or box <= 0, NG_ECUDA if a
+ * CUDA call fails. The first call on a device looks the scratch address up
+ * (cudaGetSymbolAddress) and should come before any stream capture. All
+ * calls share the one scratch array: calls whose work overlaps on the GPU
+ * (other streams or host threads) race on it. Asynchronous on the stream.
+ */
+int ng_sort_keys_noalloc(int64_t n, const double* pos, const uint8_t* type, double box,
+                         uint64_t* keys_out, uint32_t* perm_out, void* stream);
+
 /* Message describing the last error on ctx (never NULL); with ctx == NULL,
  * the message of the last failed ng_create on the calling thread. */
 const char* ng_last_error(const ng_ctx* ctx);

@@ -107,6 +107,8 @@ def lib():
         L.ng_serve_pending.argtypes = [vp]
         L.ng_serve_wait.argtypes = [vp, d]
         L.ng_serve.argtypes = [vp, ctypes.POINTER(NgRequest), ctypes.POINTER(NgResult), i32, vp, d]
+        L.ng_sort_keys_noalloc.argtypes = [i64, vp, vp, d, vp, vp, vp]
+        L.ng_sort_keys_noalloc.restype = ctypes.c_int
         L.ng_serve_request_bytes.argtypes = [ctypes.POINTER(NgRequest)]
         L.ng_serve_request_bytes.restype = ctypes.c_size_t
         L.ng_serve_last_error.argtypes = [vp]
@@ -135,7 +137,7 @@ def exported_symbols():
             "ng_batch_launch_count", "ng_batch_last_error", "ng_serve_create",
             "ng_serve_destroy", "ng_serve_submit", "ng_serve_cancel", "ng_serve_poll",
             "ng_serve_pending", "ng_serve_wait", "ng_serve", "ng_serve_last_error",
-            "ng_serve_request_bytes"]
+            "ng_serve_request_bytes", "ng_sort_keys_noalloc"]
 
 
 def _check(ctx, code):
@@ -362,6 +364,13 @@ def make_request(kind, params: NgParams, pos, typ, mass, vel=None, nsteps=0, dt=
     r.pos, r.vel, r.type, r.mass = addr(pos), addr(vel), addr(typ), addr(mass)
     r.pos_out, r.vel_out, r.acc_out = addr(pos_out), addr(vel_out), addr(acc_out)
     return r
+
+
+def ng_sort_keys_noalloc(pos, typ, keys_out, perm_out, box=1.0, stream=None):
+    """Sorted keys and permutation with no allocation (n <= 2^18); returns the
+    status code."""
+    return int(lib().ng_sort_keys_noalloc(typ.numel(), _ptr(pos), _ptr(typ), float(box),
+                                          _ptr(keys_out), _ptr(perm_out), _stream(stream)))
 
 
 def ng_version():
