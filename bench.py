@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline leg")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-tune", action="store_true", help="skip the leaf/group autotuner")
     return ap.parse_args()
 
 
@@ -175,6 +176,10 @@ def workload_config(w, args):
 def main():
     args = parse()
     ws, rank, local = dist_env()
+    if args.workload == "batch64":
+        return bench_batch(args, ws, rank, local)
+    if args.workload == "serve2000":
+        return bench_serve(args, ws, rank, local)
     from paper_1502_07442_gb300 import inputs
     w = inputs.workload(args.workload, n=args.n, seed=None if rank == 0 else 1002 + 7919 * rank)
     if args.impl == "reference":
@@ -195,6 +200,13 @@ def main():
     vel = torch.from_numpy(w["vel"]).to(dev)
     acc = torch.zeros((3, n), dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
+    tuned = None
+    if not args.no_tune:
+        from paper_1502_07442_gb300 import autotune
+        best, trials = autotune.tune(w["params"], pos, typ, mass, stream=stream)
+        w["params"] = dict(w["params"], leaf_size=best["leaf_size"], group_cell=best["group_cell"])
+        tuned = {"leaf_size": best["leaf_size"], "group_cell": best["group_cell"],
+                 "trials": len(trials), "build_plus_walk_ms": round(best["ms"], 2)}
     sim = ng.Simulation(ng.params_from_workload(w["params"]), stream)
     dt = float(w["dt"])
 
@@ -294,10 +306,140 @@ def main():
                 "dtype": "f32", "data": "synthetic", "config": workload_config(w, args),
                 "interactions_per_step": count, "particles_per_s": n * args.steps * ws / (ms / 1e3),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
-                "gpu_launches": int(launches)}
+                "gpu_launches": int(launches), "autotune": tuned}
         print(json.dumps(line))
     if ws > 1:
         torch.distributed.destroy_process_group()
+
+
+def bench_batch(args, ws, rank, local):
+    """64 independent simulations (N log-uniform in [2^12, 2^18], D uniform in
+    1..6, Newtonian couplings in [0.5, 1.5], PM 64^3) advanced together: each
+    batch step is one captured graph with one persistent walk launch per
+    species-count class."""
+    import torch
+    from paper_1502_07442_gb300 import binding as ng, inputs
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    specs = inputs.batch_specs(seed=1003 + 7919 * rank)
+    state = []
+    params = []
+    counts = []
+    for sp in specs:
+        x = dict(pos=torch.from_numpy(sp["pos"]).to(dev), vel=torch.from_numpy(sp["vel"]).to(dev),
+                 typ=torch.from_numpy(sp["type"]).to(dev), mass=torch.from_numpy(sp["mass"]).to(dev))
+        x["acc"] = torch.zeros((3, sp["type"].size), dtype=torch.float32, device=dev)
+        state.append(x)
+        p = ng.params_from_workload(sp["params"])
+        params.append(p)
+    b = ng.ng_batch_create(params)
+    L = lambda k: [x[k] for x in state]
+    ng.ng_batch_step(b, L("pos"), L("vel"), L("typ"), L("mass"), L("acc"), False, args.warmup, 1e-3)
+    # algorithmic interactions per simulation at the start of the timed region
+    for x, p in zip(state, params):
+        s = ng.Simulation(p)
+        ng.ng_build_tree(s.ctx, x["pos"], x["typ"], x["mass"])
+        counts.append(ng.ng_count_interactions(s.ctx))
+        s.close()
+    torch.cuda.synchronize()
+    l0 = ng.ng_batch_launch_count(b)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        e0.record()
+        ng.ng_batch_step(b, L("pos"), L("vel"), L("typ"), L("mass"), L("acc"), True, args.steps, 1e-3)
+        e1.record()
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    nbodies = sum(x["typ"].numel() for x in state)
+    line = {"metric": "particle-node interactions/s", "value": sum(counts) * args.steps / (ms / 1e3),
+            "unit": "interactions/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "batch64", "simulations": len(specs), "bodies": int(nbodies),
+                       "n_range": [int(min(x["typ"].numel() for x in state)),
+                                   int(max(x["typ"].numel() for x in state))],
+                       "pm_mesh": 64, "walk_launches_per_step": ng.ng_batch_walk_launches(b),
+                       "step": "one graph: per-simulation sort/tree/PM on 8 streams, one walk per D class"},
+            "particles_per_s": nbodies * args.steps / (ms / 1e3), "clocks": clk.summary(),
+            "gpu_launches": int(ng.ng_batch_launch_count(b) - l0)}
+    ng.ng_batch_destroy(b)
+    if rank == 0:
+        print(json.dumps(line))
+
+
+def bench_serve(args, ws, rank, local):
+    """2000 requests (Poisson, 200 req/s; half force evaluations, half 10-step
+    integrations; N log-uniform in [2^10, 2^20]; D uniform in 1..6; Newtonian
+    couplings in [0.5, 1.5]; PM mesh clamp(next_pow2(N^(1/3)), 32, 128);
+    120 GB byte budget). Reports p50/p99 latency under the Poisson trace and
+    the saturated throughput against one-at-a-time solves (one slot)."""
+    import torch
+    from paper_1502_07442_gb300 import binding as ng, inputs
+    torch.cuda.set_device(local)
+    nreq = 2000 if args.n is None else int(args.n)
+    rng = inputs.rng_for(1004 + 7919 * rank)
+    pool = []
+    for k in range(96):                      # distinct inputs, reused round-robin
+        n = inputs.log_uniform_int(rng, 10, 20)
+        D = int(rng.integers(1, 7))
+        sub = inputs.rng_for(1004000 + k)
+        pos = inputs.clustered(n, sub, nspheres=max(1, n // 4096))
+        typ = inputs.species_uniform(n, D, sub)
+        coup = inputs.newton_couplings(D, sub)
+        mesh = inputs.serve_mesh(n)
+        rs = 1.25 / mesh
+        prm = dict(D=D, G=coup["G"], law=coup["law"], ya=coup["ya"], yl=coup["yl"], box=1.0,
+                   eps=0.02 / n ** (1 / 3), rs=rs, rcut=4.5 * rs, theta=0.5, pm_mesh=mesh)
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+        pool.append(dict(n=n, params=ng.params_from_workload(prm), pos=pin(pos), typ=pin(typ),
+                         mass=pin(np.full(n, 1.0 / n, np.float32)),
+                         acc=torch.zeros((3, n), dtype=torch.float32).pin_memory(),
+                         pos_out=torch.zeros((3, n), dtype=torch.float64).pin_memory(),
+                         vel_out=torch.zeros((3, n), dtype=torch.float32).pin_memory()))
+    kinds = rng.integers(0, 2, nreq)
+    gaps = rng.exponential(1.0 / 200.0, nreq)
+    arrival = np.cumsum(gaps) - gaps[0]
+
+    def requests():
+        reqs = (ng.NgRequest * nreq)()
+        for k in range(nreq):
+            e = pool[k % len(pool)]
+            reqs[k] = ng.make_request(int(kinds[k]), e["params"], e["pos"], e["typ"], e["mass"],
+                                      nsteps=10 if kinds[k] else 0, dt=1e-3,
+                                      pos_out=e["pos_out"], vel_out=e["vel_out"], acc_out=e["acc"])
+        return reqs
+
+    def run(slots, arr):
+        s = ng.ng_serve_create(slots, 120 << 30)
+        warm = requests()
+        wres = (ng.NgResult * len(pool))()
+        ng.ng_serve(s, (ng.NgRequest * len(pool))(*[warm[k] for k in range(len(pool))]), wres,
+                    None, 600.0)                                   # grow every slot's buffers
+        reqs, res = requests(), (ng.NgResult * nreq)()
+        t0 = time.perf_counter()
+        ng.ng_serve(s, reqs, res, arr, 1800.0)
+        wall = time.perf_counter() - t0
+        ng.ng_serve_destroy(s)
+        lat = np.array([r.t_done - r.t_submit for r in res])
+        ok = all(r.status == 0 for r in res)
+        return wall, lat, ok
+
+    w1, _, ok1 = run(1, None)                                      # one at a time
+    wk, _, okk = run(16, None)                                     # continuous batching, saturated
+    wp, lat, okp = run(16, arrival)                                # Poisson trace
+    line = {"metric": "requests/s (served, saturated)", "value": nreq / wk, "unit": "requests/s",
+            "n_gpus": ws, "steps": 1, "warmup": 1, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "serve2000", "requests": nreq, "rate_per_s": 200, "slots": 16,
+                       "budget_bytes": 120 << 30, "mix": "50% force, 50% 10-step KDK",
+                       "n_range_log2": [10, 20]},
+            "one_at_a_time_requests_per_s": nreq / w1, "speedup_vs_one_at_a_time": w1 / wk,
+            "poisson": {"p50_latency_ms": float(np.percentile(lat, 50) * 1e3),
+                        "p99_latency_ms": float(np.percentile(lat, 99) * 1e3),
+                        "throughput_requests_per_s": nreq / wp},
+            "all_ok": bool(ok1 and okk and okp)}
+    if rank == 0:
+        print(json.dumps(line))
 
 
 if __name__ == "__main__":

@@ -302,7 +302,7 @@ def ng_batch_launch_count(b):
 
 def _scheck(s, code):
     if code != NG_OK:
-        msg = lib().ng_serve_last_error(s) if s else b""
+        msg = lib().ng_serve_last_error(s)
         raise NgError(code, msg.decode() if msg else "")
 
 

@@ -314,6 +314,8 @@ int ctx_configure(ng_ctx* c, const ng_params* p) {
     cudaGraphExecDestroy(c->step_exec);
     c->step_exec = nullptr;
   }
+  // node arrays sized by the species count follow a change of D
+  if (c->cap_nodes > 0) NG_TRY(alloc_nodes(c, c->cap_nodes));
   return build_tables(c);
 }
 
@@ -353,6 +355,7 @@ int ng_create(ng_ctx** out, const ng_params* p, void* stream) {
     e = cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
   c->smem_optin = (size_t)v;
   if (e != cudaSuccess) {
+    g_create_err = std::string("device query failed: ") + cudaGetErrorString(e);
     cudaGetLastError();
     delete c;
     return NG_ECUDA;
@@ -361,6 +364,7 @@ int ng_create(ng_ctx** out, const ng_params* p, void* stream) {
   if (r == NG_OK) r = ensure(c, c->status, ST_COUNT * 4);
   if (r == NG_OK) r = ensure(c, c->counter, 8);
   if (r != NG_OK) {
+    g_create_err = c->err;
     ng_destroy(c);
     return r;
   }

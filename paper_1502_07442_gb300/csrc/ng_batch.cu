@@ -36,6 +36,8 @@ struct ng_batch {
   cudaGraphExec_t exec = nullptr;
   std::vector<const void*> sig;      // pointers, sizes and dt the graph was captured for
   uint64_t gen = 0;
+  uint64_t graph_launches = 0;       // kernels in one captured batch step
+  uint64_t replay_launches = 0;      // kernels run by graph replays so far
   std::string err;
 };
 
@@ -150,7 +152,7 @@ const char* ng_batch_last_error(const ng_batch* b) { return b ? b->err.c_str() :
 
 int ng_batch_launch_count(const ng_batch* b, uint64_t* out) {
   if (!b || !out) return NG_EINVAL;
-  uint64_t s = 0;
+  uint64_t s = b->replay_launches;
   for (const ng_ctx* c : b->sims) s += c->launches;
   *out = s;
   return NG_OK;
@@ -301,7 +303,12 @@ int ng_batch_step(ng_batch* b, const int64_t* n, double* const* pos, float* cons
         cudaGetLastError();
         return bfail(b, NG_ECUDA, "begin capture failed");
       }
+      uint64_t before = 0;
+      for (const ng_ctx* c : b->sims) before += c->launches;
       const int r = batch_step_once(b, n, pos, vel, type, mass, acc, dt, b->cap);
+      uint64_t after = 0;
+      for (const ng_ctx* c : b->sims) after += c->launches;
+      b->graph_launches = after - before;
       const cudaError_t e = cudaStreamEndCapture(b->cap, &g);
       cudaGetLastError();
       if (r != NG_OK) {
@@ -324,6 +331,7 @@ int ng_batch_step(ng_batch* b, const int64_t* n, double* const* pos, float* cons
       cudaGetLastError();
       return bfail(b, NG_ECUDA, "graph launch failed");
     }
+    b->replay_launches += b->graph_launches;
   }
   for (int i = 0; i < S; ++i) {
     ng_ctx* c = b->sims[i];

@@ -1,6 +1,10 @@
 // Serving runtime (no paper counterpart): a stream of independent force
 // evaluations and short integrations, each a full ngravs solve.
 //
+// Every slot has its own host thread that enqueues its request's kernels, so
+// the launch work of concurrent requests is spread over host cores (a 10-step
+// request is ~1600 launches) while the polling thread only admits and reaps.
+//
 // Continuous batching: requests wait in a FIFO host queue and are admitted
 // as soon as a slot is free and the device memory the slots hold stays
 // within the byte budget. Every slot owns a context (reconfigured per
@@ -12,10 +16,15 @@
 // tree-capacity overflow, after which the request is rerun with more room.
 // The host loop never blocks on the device except in bounded waits.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
+#include <condition_variable>
 #include <cstring>
 #include <deque>
+#include <memory>
+#include <mutex>
 #include <new>
+#include <string>
 #include <thread>
 
 #include "ng_internal.cuh"
@@ -38,6 +47,14 @@ struct Slot {
   int64_t req = -1;                   // request in flight (-1: free)
   size_t bytes = 0;                   // device bytes this slot holds (high-water estimate)
   int retries = 0;
+  // launch thread: the poller hands it a request, it enqueues the kernels
+  std::thread worker;
+  std::mutex m;
+  std::condition_variable cv;
+  bool job = false, quit = false;
+  std::atomic<int> launched{0};       // 0 idle, 1 enqueueing, 2 enqueued, 3 launch failed
+  int launch_rc = NG_OK;
+  struct Req* cur = nullptr;          // request handed to the launch thread
 };
 
 struct Req {
@@ -45,6 +62,8 @@ struct Req {
   ng_result* out;
   int state;                          // 0 queued, 1 running, 2 done, 3 cancelled/failed
 };
+// (requests live on the heap: the launch threads hold pointers to them while
+// the polling thread keeps submitting)
 
 // Device bytes a request needs in a slot (particle arrays, sort and tree
 // buffers for a node capacity of n + 1024, PM meshes).
@@ -59,9 +78,9 @@ size_t request_bytes(const ng_request& q) {
 }  // namespace
 
 struct ng_server {
-  std::vector<Slot> slots;
+  std::vector<std::unique_ptr<Slot>> slots;
   std::deque<int64_t> queue;
-  std::vector<Req> reqs;
+  std::vector<std::unique_ptr<Req>> reqs;
   size_t budget = 0;
   int64_t completed = 0;
   std::string err;
@@ -73,6 +92,9 @@ int sfail(ng_server* s, int code, const char* msg) {
   s->err = msg;
   return code;
 }
+
+// Message of the last failed ng_serve_create on this thread.
+thread_local std::string g_serve_create_err;
 
 // Enqueue the whole request on the slot's stream.
 int launch_request(ng_server* s, Slot& sl, Req& q) {
@@ -91,8 +113,9 @@ int launch_request(ng_server* s, Slot& sl, Req& q) {
   NG_TRY(ensure(c, sl.type, n));
   NG_TRY(ensure(c, sl.mass, n * 4));
   NG_TRY(alloc_bodies(c, n));
-  const int64_t want_nodes = n + 1024;
-  if (c->cap_nodes < want_nodes) NG_TRY(alloc_nodes(c, want_nodes));
+  // every node array, including those sized by the species count, must fit
+  // this request (a slot serves requests of different n and D)
+  NG_TRY(alloc_nodes(c, std::max<int64_t>(c->cap_nodes, n + 1024)));
   double* pos = as<double>(sl.pos);
   float* vel = as<float>(sl.vel);
   float* acc = as<float>(sl.acc);
@@ -132,15 +155,28 @@ int launch_request(ng_server* s, Slot& sl, Req& q) {
 
 size_t held_bytes(const ng_server* s) {
   size_t t = 0;
-  for (const Slot& sl : s->slots) t += sl.bytes;
+  for (const auto& sl : s->slots) t += sl->bytes;
   return t;
 }
+
+// Hand the slot's request to its launch thread.
+void hand_over(Slot& sl, Req* q) {
+  {
+    std::lock_guard<std::mutex> g(sl.m);
+    sl.cur = q;
+    sl.launched.store(1);
+    sl.job = true;
+  }
+  sl.cv.notify_one();
+}
+
+void worker_loop(ng_server* s, Slot* sl);
 
 // Admit queued requests (FIFO) while a slot is free and the budget holds.
 int admit(ng_server* s) {
   while (!s->queue.empty()) {
     const int64_t id = s->queue.front();
-    Req& q = s->reqs[id];
+    Req& q = *s->reqs[id];
     if (q.state != 0) {
       s->queue.pop_front();
       continue;
@@ -148,7 +184,7 @@ int admit(ng_server* s) {
     const size_t need = request_bytes(q.r);
     int pick = -1;
     for (size_t k = 0; k < s->slots.size(); ++k) {
-      Slot& sl = s->slots[k];
+      Slot& sl = *s->slots[k];
       if (sl.req >= 0) continue;
       const size_t after = held_bytes(s) - sl.bytes + std::max(sl.bytes, need);
       if (after <= s->budget) {
@@ -157,36 +193,59 @@ int admit(ng_server* s) {
       }
     }
     if (pick < 0) return NG_OK;           // wait for a slot or for memory
-    Slot& sl = s->slots[pick];
+    Slot& sl = *s->slots[pick];
     s->queue.pop_front();
     sl.bytes = std::max(sl.bytes, need);
     sl.req = id;
     sl.retries = 0;
     q.state = 1;
     q.out->t_admit = now_s();
-    const int rc = launch_request(s, sl, q);
-    if (rc != NG_OK) {
-      // the slot's stream may hold part of the request: let it drain
-      cudaStreamSynchronize(sl.stream);
-      cudaGetLastError();
-      q.state = 3;
-      q.out->status = rc;
-      q.out->t_done = now_s();
-      sl.req = -1;
-      s->completed++;
-    }
+    hand_over(sl, &q);
   }
   return NG_OK;
+}
+
+void worker_loop(ng_server* s, Slot* sl) {
+  for (;;) {
+    {
+      std::unique_lock<std::mutex> g(sl->m);
+      sl->cv.wait(g, [&] { return sl->job || sl->quit; });
+      if (sl->quit) return;
+      sl->job = false;
+    }
+    Req& q = *sl->cur;
+    const int rc = launch_request(s, *sl, q);
+    sl->launch_rc = rc;
+    if (rc != NG_OK) {
+      // the slot's stream may hold part of the request: let it drain
+      cudaStreamSynchronize(sl->stream);
+      cudaGetLastError();
+    }
+    sl->launched.store(rc == NG_OK ? 2 : 3);
+  }
 }
 
 // Collect finished requests; returns the number completed by this call.
 int reap(ng_server* s) {
   int got = 0;
-  for (Slot& sl : s->slots) {
+  for (auto& slp : s->slots) {
+    Slot& sl = *slp;
     if (sl.req < 0) continue;
+    const int st = sl.launched.load();
+    if (st == 1) continue;               // still enqueueing
+    Req& q = *s->reqs[sl.req];
+    if (st == 3) {
+      q.state = 3;
+      q.out->status = sl.launch_rc;
+      q.out->t_done = now_s();
+      sl.req = -1;
+      sl.launched.store(0);
+      s->completed++;
+      got++;
+      continue;
+    }
     const cudaError_t e = cudaEventQuery(sl.done);
     if (e == cudaErrorNotReady) continue;
-    Req& q = s->reqs[sl.req];
     if (e != cudaSuccess) {
       cudaGetLastError();
       q.out->status = NG_ECUDA;
@@ -196,7 +255,8 @@ int reap(ng_server* s) {
       const int64_t need = (int64_t)sl.h_status[ST_NODES_NEEDED];
       if (alloc_nodes(c, std::max<int64_t>(2 * need, 2 * c->cap_nodes)) == NG_OK) {
         sl.retries++;
-        if (launch_request(s, sl, q) == NG_OK) continue;
+        hand_over(sl, &q);               // rerun on the slot's thread
+        continue;
       }
       q.out->status = NG_ENOMEM;
     } else {
@@ -205,6 +265,7 @@ int reap(ng_server* s) {
     q.state = q.out->status == NG_OK ? 2 : 3;
     q.out->t_done = now_s();
     sl.req = -1;
+    sl.launched.store(0);
     s->completed++;
     got++;
   }
@@ -229,18 +290,32 @@ int ng_serve_create(ng_server** out, int slots, size_t hbm_budget) {
   p.asmth = 0.05;
   p.rcut_over_rs = 4.5;
   p.theta = 0.5;
+  int dev = 0;
+  cudaGetDevice(&dev);
   for (int k = 0; k < slots; ++k) {
-    Slot sl;
-    if (cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess ||
-        cudaHostAlloc((void**)&sl.h_status, ST_COUNT * 4, cudaHostAllocDefault) != cudaSuccess ||
-        ng_create(&sl.ctx, &p, sl.stream) != NG_OK) {
+    s->slots.emplace_back(new Slot());
+    Slot& sl = *s->slots.back();
+    cudaError_t e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaHostAlloc((void**)&sl.h_status, ST_COUNT * 4, cudaHostAllocDefault);
+    int rc = e == cudaSuccess ? NG_OK : NG_ECUDA;
+    if (e != cudaSuccess) {
+      g_serve_create_err = std::string("slot ") + std::to_string(k) + ": " + cudaGetErrorString(e);
       cudaGetLastError();
-      s->slots.push_back(sl);
-      ng_serve_destroy(s);
-      return NG_ECUDA;
+    } else {
+      rc = ng_create(&sl.ctx, &p, sl.stream);
+      if (rc != NG_OK)
+        g_serve_create_err = std::string("slot ") + std::to_string(k) + ": " + ng_last_error(nullptr);
     }
-    s->slots.push_back(sl);
+    if (rc != NG_OK) {
+      ng_serve_destroy(s);
+      return rc;
+    }
+    Slot* slp = &sl;
+    sl.worker = std::thread([s, slp, dev] {
+      cudaSetDevice(dev);
+      worker_loop(s, slp);
+    });
   }
   *out = s;
   return NG_OK;
@@ -248,7 +323,18 @@ int ng_serve_create(ng_server** out, int slots, size_t hbm_budget) {
 
 int ng_serve_destroy(ng_server* s) {
   if (!s) return NG_OK;
-  for (Slot& sl : s->slots) {
+  for (auto& slp : s->slots) {
+    Slot& sl = *slp;
+    if (sl.worker.joinable()) {
+      // let an enqueueing request finish, then stop the thread
+      while (sl.launched.load() == 1) std::this_thread::sleep_for(std::chrono::microseconds(50));
+      {
+        std::lock_guard<std::mutex> g(sl.m);
+        sl.quit = true;
+      }
+      sl.cv.notify_one();
+      sl.worker.join();
+    }
     if (sl.stream) cudaStreamSynchronize(sl.stream);
     if (sl.ctx) {
       release(sl.pos);
@@ -278,8 +364,7 @@ int ng_serve_submit(ng_server* s, const ng_request* r, ng_result* out, int64_t* 
   if (validate(&probe, &r->params) != NG_OK) return sfail(s, NG_EINVAL, probe.err.c_str());
   if (request_bytes(*r) > s->budget)
     return sfail(s, NG_EBUSY, "request larger than the whole device byte budget");
-  Req q{*r, out, 0};
-  s->reqs.push_back(q);
+  s->reqs.emplace_back(new Req{*r, out, 0});
   const int64_t k = (int64_t)s->reqs.size() - 1;
   s->queue.push_back(k);
   out->status = 1;                    // pending
@@ -289,7 +374,7 @@ int ng_serve_submit(ng_server* s, const ng_request* r, ng_result* out, int64_t* 
 
 int ng_serve_cancel(ng_server* s, int64_t id) {
   if (!s || id < 0 || id >= (int64_t)s->reqs.size()) return NG_EINVAL;
-  Req& q = s->reqs[id];
+  Req& q = *s->reqs[id];
   if (q.state != 0) return NG_ESTATE;   // admitted work is not interrupted
   q.state = 3;
   q.out->status = NG_ESTATE;
@@ -347,7 +432,9 @@ int ng_serve(ng_server* s, const ng_request* reqs, ng_result* res, int nreq,
   return NG_OK;
 }
 
-const char* ng_serve_last_error(const ng_server* s) { return s ? s->err.c_str() : "no server"; }
+const char* ng_serve_last_error(const ng_server* s) {
+  return s ? s->err.c_str() : g_serve_create_err.c_str();
+}
 
 size_t ng_serve_request_bytes(const ng_request* r) { return r ? request_bytes(*r) : 0; }
 

@@ -151,3 +151,18 @@ def test_bounded_wait_times_out_into_status(ng):
         assert res.status == 0 and np.isfinite(acc).all()
     finally:
         ng.ng_serve_destroy(s)
+
+
+def test_one_slot_serves_growing_species_count(ng):
+    # a slot reused by a request with more species and fewer bodies must
+    # regrow its per-species node arrays
+    items = []
+    for k, (n, D) in enumerate([(6000, 1), (2500, 6), (4000, 3)]):
+        w = small_clustered(n, D, 850 + k, mesh=32)
+        items.append(dict(w=w, kind=k % 2, nsteps=2 if k % 2 else 0))
+    seq, res = _run(ng, items, slots=1, budget=8 << 30)
+    assert all(r.status == 0 for r in res)
+    for it, got in zip(items, seq):
+        alone, r1 = _run(ng, [it], slots=1, budget=8 << 30)
+        assert r1[0].status == 0
+        assert _close(got["acc"], alone[0]["acc"])
