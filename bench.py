@@ -54,6 +54,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-tune", action="store_true", help="skip the leaf/group autotuner")
+    ap.add_argument("--leaf", type=int, default=None,
+                    help="leaf size (with --cell: fixed walk configuration, no autotuning)")
+    ap.add_argument("--cell", type=int, default=None, help="group cell size (with --leaf)")
     return ap.parse_args()
 
 
@@ -201,7 +204,10 @@ def main():
     acc = torch.zeros((3, n), dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
     tuned = None
-    if not args.no_tune:
+    if args.leaf is not None and args.cell is not None:
+        w["params"] = dict(w["params"], leaf_size=args.leaf, group_cell=args.cell)
+        tuned = {"leaf_size": args.leaf, "group_cell": args.cell, "fixed": True}
+    elif not args.no_tune:
         from paper_1502_07442_gb300 import autotune
         best, trials = autotune.tune(w["params"], pos, typ, mass, stream=stream)
         w["params"] = dict(w["params"], leaf_size=best["leaf_size"], group_cell=best["group_cell"])

@@ -18,8 +18,9 @@
 // Inner loop per (body, record): q = |d|^2 + eps^2, inv = rsqrt(q); the
 // table index is rint(q * inv) read from the float bits of q*inv + 2^23; the
 // table holds one linear segment {c0, c1} per index, zero past the cut-off;
-// the force is m * (c0 + t c1) * inv^3 * d, accumulated per active species
-// (the coupling G[s][t] is applied once per body at the end).
+// the force is m * (c0 + t c1) * inv^3 * d, summed over one species list;
+// each list's sum is scaled by the coupling G[s][t] of the body's species s
+// and the list's species t and added to one accumulator per body.
 #include "ng_internal.cuh"
 
 namespace ng {
@@ -123,10 +124,10 @@ __global__ void __launch_bounds__(walk_warps(D) * 32, 1) k_walk(WalkLaunch L) {
     const float yr = (wrap_unit(lg.y - oy) + bd.y) * s_tab;
     const float zr = (wrap_unit(lg.z - oz) + bd.z) * s_tab;
 
-    float ax[D], ay[D], az[D];
+    float ax = 0.f, ay = 0.f, az = 0.f;
     int lc[D];                      // records per species list (same in every lane)
 #pragma unroll
-    for (int t = 0; t < D; ++t) { ax[t] = ay[t] = az[t] = 0.f; lc[t] = 0; }
+    for (int t = 0; t < D; ++t) lc[t] = 0;
 
     if (lane == 0) ws->stack[0] = 0;
     int size = 1;
@@ -167,15 +168,12 @@ __global__ void __launch_bounds__(walk_warps(D) * 32, 1) k_walk(WalkLaunch L) {
             sz = fmaf(f, dz, sz);
           }
           __syncwarp();
+          const float G = DESC(G[s][t]);
+          ax = fmaf(G, sx, ax);
+          ay = fmaf(G, sy, ay);
+          az = fmaf(G, sz, az);
 #pragma unroll
-          for (int q = 0; q < D; ++q) {
-            if (q == t) {
-              ax[q] += sx;
-              ay[q] += sy;
-              az[q] += sz;
-              lc[q] = 0;
-            }
-          }
+          for (int q = 0; q < D; ++q) lc[q] = (q == t) ? 0 : lc[q];
           nint += (unsigned long long)cnt * (unsigned long long)nact;
         }
       }
@@ -305,14 +303,7 @@ __global__ void __launch_bounds__(walk_warps(D) * 32, 1) k_walk(WalkLaunch L) {
       continue;
     }
     if (active) {
-      float fx = 0.f, fy = 0.f, fz = 0.f;
-#pragma unroll
-      for (int t = 0; t < D; ++t) {
-        const float G = DESC(G[s][t]);
-        fx = fmaf(G, ax[t], fx);
-        fy = fmaf(G, ay[t], fy);
-        fz = fmaf(G, az[t], fz);
-      }
+      float fx = ax, fy = ay, fz = az;
       const uint32_t i = DESC(perm)[p];
       float* acc = DESC(acc);
       const int64_t nb = DESC(n);
