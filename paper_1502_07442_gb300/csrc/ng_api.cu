@@ -499,8 +499,12 @@ int ng_step(ng_ctx* c, int64_t n, double* pos, float* vel, const uint8_t* type,
     NG_CUDA(c, cudaGetLastError());
     done = 1;
     if (c->cap_nodes < c->nnodes + c->nnodes / 4 + 1024) {
+      // headroom for the replayed steps, whose trees cannot regrow; the
+      // regrow drops the node arrays, so the tree of the current positions
+      // is built again for tree queries made after this call
       NG_CUDA(c, cudaStreamSynchronize(c->stream));
       NG_TRY(alloc_nodes(c, c->nnodes + c->nnodes / 4 + 1024));
+      NG_TRY(build_checked(c, n, pos, type, mass));
     }
     NG_CUDA(c, cudaStreamSynchronize(c->stream));
     if (c->step_exec) {

@@ -44,7 +44,7 @@ struct DevBuf {
 // Walk tuning constants.
 constexpr int kListCap = 64;            // records per species list per warp
 constexpr int kStackCap = 384;          // node stack entries per warp
-constexpr int kStackReserve = 7 * kMaxLevel + 8;   // kept free for depth-first descent
+constexpr int kStackReserve = 7 * kMaxLevel + 8 + 32;   // depth-first descent + push-backs
 constexpr int kWalkMaxWarps = 32;
 // Warps per walk block by species count: as many as the per-warp lists and a
 // 64 KB law table leave room for in 227 KB of shared memory; the register

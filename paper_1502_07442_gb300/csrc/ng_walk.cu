@@ -209,13 +209,21 @@ __global__ void __launch_bounds__(walk_warps(D) * 32, 1) k_walk(WalkLaunch L) {
         continue;
       }
 
-      // ---- pop up to 32 nodes while the pushes (<= 8 per node) leave
-      // kStackReserve free slots; otherwise pop one (depth-first). Depth-first
-      // growth is at most 7 slots per level below the popped node, so the
-      // stack never exceeds (kStackCap - kStackReserve) + 7 * kMaxLevel + 7.
-      const int room = (kStackCap - kStackReserve - size) / 7;
+      // ---- pop the top min(32, size) nodes. Their children may use `avail`
+      // slots of the breadth area (kStackCap - kStackReserve); an opened
+      // node whose children do not fit is pushed back and popped again
+      // later (lane 0 always fits: avail >= 8). When fewer than 8 slots are
+      // left, pop one node (depth-first) whose children go into the reserve.
+      // A breadth round leaves at most (kStackCap - kStackReserve) + 31
+      // entries, and depth-first descent adds at most 7 per level below
+      // that, so the stack stays below kStackCap - 7.
       if (size + 7 > kStackCap || visits > nnodes) { overflow = true; break; }
-      const int k = max(1, min(min(32, size), room));
+      int k = min(32, size);
+      int avail = (kStackCap - kStackReserve) - (size - k);
+      if (avail < 8) {
+        k = 1;
+        avail = kStackCap - (size - 1);
+      }
       visits += k;
       const int node = lane < k ? ws->stack[size - k + lane] : -1;
       size -= k;
@@ -228,6 +236,11 @@ __global__ void __launch_bounds__(walk_warps(D) * 32, 1) k_walk(WalkLaunch L) {
         const float4 ge = DESC(geo)[node];
         const float4 cm = DESC(com)[node];
         lk = DESC(link)[node];
+        // the species monopoles are read only if the node is accepted;
+        // start moving them into L1 now
+        const char* mp = reinterpret_cast<const char*>(DESC(mono) + (size_t)node * D);
+        asm volatile("prefetch.global.L1 [%0];" ::"l"(mp));
+        asm volatile("prefetch.global.L1 [%0];" ::"l"(mp + D * 16 - 1));
         dcx = wrap_unit(ge.x - ox);
         dcy = wrap_unit(ge.y - oy);
         dcz = wrap_unit(ge.z - oz);
@@ -259,7 +272,8 @@ __global__ void __launch_bounds__(walk_warps(D) * 32, 1) k_walk(WalkLaunch L) {
           lc[t] += __popc(b);
         }
       }
-      // rejected internal nodes: push children
+      // rejected internal nodes: push children, in lane order while they
+      // fit in `avail`; the remaining opened nodes are pushed back
       {
         const int nch = cls == 3 ? lk.y : 0;
         int incl = nch;
@@ -268,10 +282,17 @@ __global__ void __launch_bounds__(walk_warps(D) * 32, 1) k_walk(WalkLaunch L) {
           const int t = __shfl_up_sync(0xffffffffu, incl, o);
           if (lane >= o) incl += t;
         }
-        const int total = __shfl_sync(0xffffffffu, incl, 31);
-        const int base = size + incl - nch;
-        for (int cc = 0; cc < nch; ++cc) ws->stack[base + cc] = lk.x + cc;
-        size += total;
+        const bool fit = incl <= avail;
+        const uint32_t back = __ballot_sync(0xffffffffu, cls == 3 && !fit);
+        const int used = (int)__reduce_max_sync(0xffffffffu, fit ? (unsigned)incl : 0u);
+        if (fit) {
+          const int base = size + incl - nch;
+          for (int cc = 0; cc < nch; ++cc) ws->stack[base + cc] = lk.x + cc;
+        } else if (cls == 3) {
+          ws->stack[size + used + __popc(back & lt)] = node;
+        }
+        size += used + __popc(back);
+        visits -= __popc(back);
       }
       // rejected leaves: queue their bodies (drained 32 per iteration above)
       {
@@ -288,6 +309,10 @@ __global__ void __launch_bounds__(walk_warps(D) * 32, 1) k_walk(WalkLaunch L) {
           qdone = 0;
           nl = __popc(lm);
           if (cls == 2) {
+            // the queued bodies are read in the next chunks; start moving
+            // their records into L1 now
+            const char* bp = reinterpret_cast<const char*>(DESC(body) + lk.z);
+            for (int o = 0; o < lk.w * 16; o += 128) asm volatile("prefetch.global.L1 [%0];" ::"l"(bp + o));
             const int pos = __popc(lm & lt);
             ws->leafc[pos] = make_float4(dcx, dcy, dcz, 0.f);
             ws->leafb[pos] = make_int2(lk.z, lk.w);

@@ -100,3 +100,34 @@ def test_interaction_counts_bit_exact(ng, name, w, theta):
     assert np.array_equal(got, c_ref)
     assert total == int(c_ref.sum())
     sim.close()
+
+
+def test_tree_queries_after_single_steps(ng):
+    """ng_step with nsteps = 1 takes the eager path and may then regrow the
+    node arrays for the replayed steps; the tree left in the context must
+    still be the tree of the current positions (this case triggers the
+    regrow: 2551 nodes in the initial 4096-node capacity)."""
+    import torch
+    w = small_clustered(20000, 3, 91, leaf=32)
+    prm = w["params"]
+    pos, typ, mass = device_arrays(w)
+    n = typ.numel()
+    vel = torch.zeros((3, n), dtype=torch.float32, device=pos.device)
+    acc = torch.empty((3, n), dtype=torch.float32, device=pos.device)
+    sim = ng.Simulation(ng_params(prm))
+    ng.ng_step(sim.ctx, pos, vel, typ, mass, acc, False, 1, 1e-3)
+    ng.ng_step(sim.ctx, pos, vel, typ, mass, acc, True, 1, 1e-3)
+    counts = torch.empty(n, dtype=torch.int64, device=pos.device)
+    total = ng.ng_count_interactions(sim.ctx, counts)
+    tree = ng.ng_tree_export(sim.ctx, prm["D"])
+    fresh = ng.Simulation(ng_params(prm))
+    ng.ng_build_tree(fresh.ctx, pos, typ, mass)
+    counts_f = torch.empty(n, dtype=torch.int64, device=pos.device)
+    total_f = ng.ng_count_interactions(fresh.ctx, counts_f)
+    tree_f = ng.ng_tree_export(fresh.ctx, prm["D"])
+    assert total == total_f
+    assert torch.equal(counts, counts_f)
+    for k in ("level", "prefix", "first", "count", "nchild", "child_first", "cnt"):
+        assert np.array_equal(tree[k], tree_f[k]), k
+    sim.close()
+    fresh.close()
