@@ -336,8 +336,17 @@ def bench_batch(args, ws, rank, local):
                  typ=torch.from_numpy(sp["type"]).to(dev), mass=torch.from_numpy(sp["mass"]).to(dev))
         x["acc"] = torch.zeros((3, sp["type"].size), dtype=torch.float32, device=dev)
         state.append(x)
-        p = ng.params_from_workload(sp["params"])
-        params.append(p)
+    # walk leaf size and group cell: tuned on the largest simulation, used by all
+    big = max(range(len(specs)), key=lambda i: specs[i]["type"].size)
+    tuned = {"leaf_size": 8, "group_cell": 32, "tuned_on_n": int(specs[big]["type"].size)}
+    if not args.no_tune:
+        from paper_1502_07442_gb300 import autotune
+        best, trials = autotune.tune(specs[big]["params"], state[big]["pos"], state[big]["typ"],
+                                     state[big]["mass"])
+        tuned.update(leaf_size=best["leaf_size"], group_cell=best["group_cell"], trials=len(trials))
+    for sp in specs:
+        params.append(ng.params_from_workload(sp["params"], leaf_size=tuned["leaf_size"],
+                                              group_cell=tuned["group_cell"]))
     b = ng.ng_batch_create(params)
     L = lambda k: [x[k] for x in state]
     ng.ng_batch_step(b, L("pos"), L("vel"), L("typ"), L("mass"), L("acc"), False, args.warmup, 1e-3)
@@ -365,7 +374,8 @@ def bench_batch(args, ws, rank, local):
                        "n_range": [int(min(x["typ"].numel() for x in state)),
                                    int(max(x["typ"].numel() for x in state))],
                        "pm_mesh": 64, "walk_launches_per_step": ng.ng_batch_walk_launches(b),
-                       "step": "one graph: per-simulation sort/tree/PM on 8 streams, one walk per D class"},
+                       "step": "one graph: per-simulation sort/tree/PM on 8 streams, one walk per D class",
+                       "autotune": tuned},
             "particles_per_s": nbodies * args.steps / (ms / 1e3), "clocks": clk.summary(),
             "gpu_launches": int(ng.ng_batch_launch_count(b) - l0)}
     ng.ng_batch_destroy(b)
@@ -426,10 +436,14 @@ def bench_serve(args, ws, rank, local):
         t0 = time.perf_counter()
         ng.ng_serve(s, reqs, res, arr, 1800.0)
         wall = time.perf_counter() - t0
+        first_err = ng.lib().ng_serve_last_error(s)
         ng.ng_serve_destroy(s)
         lat = np.array([r.t_done - r.t_submit for r in res])
-        ok = all(r.status == 0 for r in res)
-        return wall, lat, ok
+        bad = [(k, r.status) for k, r in enumerate(res) if r.status != 0]
+        if bad:
+            print(f"serve: {len(bad)} of {nreq} requests failed; first {bad[:5]}; "
+                  f"{(first_err or b'').decode()}", file=sys.stderr, flush=True)
+        return wall, lat, not bad
 
     def plain():
         # one request at a time through the plain calls, as a caller without
@@ -451,8 +465,11 @@ def bench_serve(args, ws, rank, local):
             acc = torch.empty((3, n), dtype=torch.float32, device=dev)
             try:
                 ng.ng_step(sim.ctx, pos, vel, typ, mass, acc, False, 10 if kinds[k] else 0, 1e-3)
-            except ng.NgError:
+            except ng.NgError as err:
+                print(f"plain request {k} (n={n}, kind={int(kinds[k])}) failed: {err}",
+                      file=sys.stderr, flush=True)
                 ok = False
+                break
             e["acc"].copy_(acc, non_blocking=True)
             if kinds[k]:
                 e["pos_out"].copy_(pos, non_blocking=True)
@@ -461,10 +478,25 @@ def bench_serve(args, ws, rank, local):
             sim.close()
         return time.perf_counter() - t0, ok
 
-    wpl, okpl = plain()                                            # plain calls, one at a time
-    w1, _, ok1 = run(1, None)                                      # serving loop, one slot
-    wk, _, okk = run(16, None)                                     # continuous batching, saturated
-    wp, lat, okp = run(16, arrival)                                # Poisson trace
+    def leg(name, fn, *a):
+        # a failed leg reports where it failed and ends the process at once
+        # (no unwinding through CUDA buffers of a context that has faulted)
+        t = time.perf_counter()
+        print(f"serve leg {name}: start", file=sys.stderr, flush=True)
+        try:
+            r = fn(*a)
+        except Exception:
+            import traceback
+            traceback.print_exc()
+            sys.stderr.flush()
+            os._exit(3)
+        print(f"serve leg {name}: {time.perf_counter() - t:.1f} s", file=sys.stderr, flush=True)
+        return r
+
+    wpl, okpl = leg("plain", plain)                                # plain calls, one at a time
+    w1, _, ok1 = leg("one-slot", run, 1, None)                     # serving loop, one slot
+    wk, _, okk = leg("saturated", run, 16, None)                   # continuous batching, saturated
+    wp, lat, okp = leg("poisson", run, 16, arrival)                # Poisson trace
     line = {"metric": "requests/s (served, saturated)", "value": nreq / wk, "unit": "requests/s",
             "n_gpus": ws, "steps": 1, "warmup": 1, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",

@@ -73,8 +73,8 @@ double short_law_factor(int law, double a, double l, double rs, double rho) {
 }
 
 // One table per distinct law; segment k (k < ncut) is the chord of T over
-// [(k - 1/2) dr, (k + 1/2) dr] (segment 0 over [0, dr/2]); the walk reads
-// c0 + t c1 with t = rho/dr - k; entry ncut is zero (beyond the cut-off,
+// [(k - 1/2) dr, (k + 1/2) dr] (segment 0 over [0, dr/2]), c0 + t c1 with
+// t = rho/dr - k, stored as {c0 - k c1, c1}; entry ncut is zero (beyond the cut-off,
 // which sits at rho = (ncut - 1/2) dr = r_cut). The table depends on the
 // law, r_s and r_cut only, not on the softening.
 int build_tables(ng_ctx* c) {
@@ -117,7 +117,8 @@ int build_tables(ng_ctx* c) {
     t[1] = (float)(2.0 * (T(0.5 * dr) - T(0.0)));
     for (int k = 1; k < ncut; ++k) {
       const double lo = T((k - 0.5) * dr), hi = T((k + 0.5) * dr);
-      t[2 * k] = (float)(0.5 * (lo + hi));
+      // stored shifted: the walk evaluates (c0 - k c1) + (rho / dr) c1
+      t[2 * k] = (float)(0.5 * (lo + hi) - k * (hi - lo));
       t[2 * k + 1] = (float)(hi - lo);
     }
     t[2 * ncut] = 0.f;
@@ -125,8 +126,18 @@ int build_tables(ng_ctx* c) {
   }
   c->h_tab = h;
   NG_TRY(ensure(c, c->d_tab, h.size() * sizeof(float)));
-  // stream-ordered upload from the context's own host copy (it outlives the copy)
-  NG_CUDA(c, cudaMemcpyAsync(c->d_tab.p, c->h_tab.data(), h.size() * sizeof(float),
+  // upload through the context's pinned staging copy: wait until the stream
+  // has consumed the previous contents, then copy without a pageable stall
+  NG_CUDA(c, cudaStreamSynchronize(c->stream));
+  if (c->h_tab_pinned_bytes < h.size() * sizeof(float)) {
+    if (c->h_tab_pinned) cudaFreeHost(c->h_tab_pinned);
+    c->h_tab_pinned = nullptr;
+    c->h_tab_pinned_bytes = 0;
+    NG_CUDA(c, cudaHostAlloc(&c->h_tab_pinned, h.size() * sizeof(float), cudaHostAllocDefault));
+    c->h_tab_pinned_bytes = h.size() * sizeof(float);
+  }
+  std::memcpy(c->h_tab_pinned, h.data(), h.size() * sizeof(float));
+  NG_CUDA(c, cudaMemcpyAsync(c->d_tab.p, c->h_tab_pinned, h.size() * sizeof(float),
                              cudaMemcpyHostToDevice, c->stream));
   return NG_OK;
 }
@@ -374,11 +385,16 @@ int ng_create(ng_ctx** out, const ng_params* p, void* stream) {
 
 int ng_destroy(ng_ctx* c) {
   if (!c) return NG_OK;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  if (c->h_tab_pinned) cudaFreeHost(c->h_tab_pinned);
   if (c->step_exec) cudaGraphExecDestroy(c->step_exec);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
-  for (const auto& pl : c->plans) {
-    cufftDestroy(pl.r2c);
-    cufftDestroy(pl.c2r);
+  {
+    std::lock_guard<std::mutex> lock(g_fft_plan_lock);
+    for (const auto& pl : c->plans) {
+      cufftDestroy(pl.r2c);
+      cufftDestroy(pl.c2r);
+    }
   }
   DevBuf* bufs[] = {&c->d_tab, &c->keys_a, &c->keys_b, &c->vals_a, &c->vals_b, &c->blockhist,
                     &c->skeys, &c->perm, &c->spos, &c->smass, &c->stype, &c->body, &c->bleaf,

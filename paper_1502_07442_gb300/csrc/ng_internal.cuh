@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <mutex>
 #include <vector>
 
 #include "../../include/ngravs.h"
@@ -109,6 +110,8 @@ struct ng_ctx {
   double dr_phys = 0;                 // table spacing (physical length)
   ng::DevBuf d_tab;
   std::vector<float> h_tab;           // host copy (tables of a batch are matched on it)
+  void* h_tab_pinned = nullptr;       // pinned staging copy of the table upload
+  size_t h_tab_pinned_bytes = 0;
 
   // particles of the last build
   int64_t n = 0;
@@ -124,7 +127,6 @@ struct ng_ctx {
   ng::DevBuf groups;
   ng::DevBuf status;     // uint32[ST_COUNT]
   ng::DevBuf walk_desc, walk_prefix;
-  ng::WalkDesc h_walk_desc{};
   ng::DevBuf counter;    // unsigned long long
   ng::DevBuf acc_tmp;    // float[3][n] scratch for summing short + long
 
@@ -193,6 +195,7 @@ int launch_walk_descs(ng_ctx* c, cudaStream_t stream, const WalkDesc* d_descs, i
                       uint32_t* d_prefix, uint32_t* d_work, unsigned long long* counter);
 int launch_count(ng_ctx* c, int64_t* counts);  // per-particle walk counts
 int pm_force(ng_ctx* c, float* acc, bool accumulate);
+extern std::mutex g_fft_plan_lock;   // see pm_setup
 int type_order(ng_ctx* c);
 
 // Host short-range law tables (double precision closed forms).

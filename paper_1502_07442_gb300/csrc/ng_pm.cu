@@ -13,6 +13,8 @@
 // unnormalised inverse transform.
 #include <cmath>
 
+#include <mutex>
+
 #include "ng_internal.cuh"
 
 namespace ng {
@@ -151,6 +153,11 @@ __global__ void k_pm_interp(int64_t n, const double* __restrict__ spos,
   }
 }
 
+// cuFFT plan creation and destruction are serialised across host threads
+// (serving slots create plans concurrently); executing different plans from
+// different threads needs no lock.
+std::mutex g_fft_plan_lock;
+
 static int pm_setup(ng_ctx* c) {
   const int N = c->p.pm_mesh, D = c->p.D;
   const size_t N3 = (size_t)N * N * N;
@@ -166,6 +173,7 @@ static int pm_setup(ng_ctx* c) {
     }
   int dims[3] = {N, N, N};
   ng_ctx::Plan pl{N, D, 0, 0};
+  std::lock_guard<std::mutex> lock(g_fft_plan_lock);
   if (cufftPlanMany(&pl.r2c, 3, dims, nullptr, 1, (int)N3, nullptr, 1, (int)modes,
                     CUFFT_R2C, D) != CUFFT_SUCCESS ||
       cufftPlanMany(&pl.c2r, 3, dims, nullptr, 1, (int)modes, nullptr, 1, (int)N3,

@@ -237,6 +237,7 @@ int reap(ng_server* s) {
     if (st == 3) {
       q.state = 3;
       q.out->status = sl.launch_rc;
+      if (s->err.empty()) s->err = "request " + std::to_string(sl.req) + ": " + sl.ctx->err;
       q.out->t_done = now_s();
       sl.req = -1;
       sl.launched.store(0);
@@ -249,6 +250,7 @@ int reap(ng_server* s) {
     if (e != cudaSuccess) {
       cudaGetLastError();
       q.out->status = NG_ECUDA;
+      sl.ctx->err = std::string("completion event: ") + cudaGetErrorString(e);
     } else if ((sl.h_status[ST_FLAGS] & SF_NODE_OVERFLOW) && sl.retries < 4) {
       // rerun with room for the node count the build reported
       ng_ctx* c = sl.ctx;
@@ -263,6 +265,8 @@ int reap(ng_server* s) {
       q.out->status = sl.h_status[ST_FLAGS] ? check_flags(sl.ctx, sl.h_status[ST_FLAGS]) : NG_OK;
     }
     q.state = q.out->status == NG_OK ? 2 : 3;
+    if (q.out->status != NG_OK && s->err.empty())
+      s->err = "request " + std::to_string(sl.req) + ": " + sl.ctx->err;
     q.out->t_done = now_s();
     sl.req = -1;
     sl.launched.store(0);

@@ -16,9 +16,10 @@
 // exact in FP32 and no FP64 enters the inner loop.
 //
 // Inner loop per (body, record): q = |d|^2 + eps^2, inv = rsqrt(q); the
-// table index is rint(q * inv) read from the float bits of q*inv + 2^23; the
-// table holds one linear segment {c0, c1} per index, zero past the cut-off;
-// the force is m * (c0 + t c1) * inv^3 * d, summed over one species list;
+// table index k = rint(rho), rho = q * inv, is read from the float bits of
+// q*inv + 2^23; the table holds one linear segment per index, stored as
+// {c0 - k c1, c1} so that its value is (c0 - k c1) + rho c1 (zero past the
+// cut-off); the force is m * value * inv^3 * d, summed over one species list;
 // each list's sum is scaled by the coupling G[s][t] of the body's species s
 // and the list's species t and added to one accumulator per body.
 #include "ng_internal.cuh"
@@ -39,6 +40,13 @@ constexpr float kMagic = 8388608.0f;   // 2^23
 constexpr int kMagicBits = 0x4B000000;
 
 __device__ __forceinline__ float wrap_unit(float d) { return d - rintf(d); }
+
+// 8-byte shared-memory load from a 32-bit shared address
+__device__ __forceinline__ float2 lds_f2(uint32_t addr) {
+  float2 v;
+  asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(addr));
+  return v;
+}
 
 // Each warp copies its item's descriptor (one per simulation) from device
 // memory into shared memory and reads the fields from there.
@@ -145,7 +153,11 @@ __global__ void __launch_bounds__(walk_warps(D) * 32, 1) k_walk(WalkLaunch L) {
 #pragma unroll
         for (int q = 0; q < D; ++q) cnt = (q == t) ? lc[q] : cnt;
         if (cnt > kListCap - 32 || (drain && cnt > 0)) {
-          const float2* __restrict__ T = tab + (int)DESC(tabid[s][t]) * L.tab_entries;
+          // shared address of segment k is tb + 8 * (float bits of k + 2^23), mod 2^32,
+          // so the index needs no subtraction
+          const uint32_t tb =
+              (uint32_t)__cvta_generic_to_shared(tab + (int)DESC(tabid[s][t]) * L.tab_entries) -
+              ((uint32_t)kMagicBits << 3);
           const float4* __restrict__ list = ws->list[t];
           float sx = 0.f, sy = 0.f, sz = 0.f;
           __syncwarp();
@@ -157,10 +169,9 @@ __global__ void __launch_bounds__(walk_warps(D) * 32, 1) k_walk(WalkLaunch L) {
             const float inv = rsqrtf(qq);
             const float fi = fmaf(qq, inv, kMagic);
             const int bits = min(__float_as_int(fi), clampbits);
-            const float r0 = __int_as_float(bits) - kMagic;
-            const float tt = fmaf(qq, inv, -r0);
-            const float2 e = T[bits - kMagicBits];
-            const float gg = fmaf(tt, e.y, e.x);
+            const float rho = qq * inv;
+            const float2 e = lds_f2(tb + ((uint32_t)bits << 3));
+            const float gg = fmaf(rho, e.y, e.x);
             const float inv2 = inv * inv;
             const float f = (r.w * gg) * (inv2 * inv);
             sx = fmaf(f, dx, sx);
@@ -403,8 +414,10 @@ static int launch_walk_d(ng_ctx* c, cudaStream_t stream, const WalkLaunch& L) {
   const size_t smem = walk_smem<D>(L.nlaws, L.tab_entries, nwarps);
   if (smem > c->smem_optin)
     return fail(c, NG_ENOMEM, "walk needs %zu B shared memory (max %zu)", smem, c->smem_optin);
+  // the attribute is a per-function ceiling shared by every thread that
+  // launches the walk: always raise it to the device maximum, never lower it
   NG_CUDA(c, cudaFuncSetAttribute(k_walk<D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)smem));
+                                  (int)c->smem_optin));
   int per_sm = 0;
   NG_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walk<D>, nwarps * 32,
                                                            smem));
@@ -471,13 +484,21 @@ int launch_walk_descs(ng_ctx* c, cudaStream_t stream, const WalkDesc* d_descs, i
   return dispatch_walk(c, stream, L);
 }
 
+// The descriptor travels as a kernel argument (captured by value, also in
+// graphs) and is stored to device memory by one thread: no host buffer has
+// to outlive the launch and no pageable copy stalls the stream.
+__global__ void k_put_desc(const WalkDesc d, WalkDesc* out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) *out = d;
+}
+
 int launch_walk(ng_ctx* c, float* acc, bool accumulate, bool count) {
   NG_TRY(ensure(c, c->walk_desc, sizeof(WalkDesc)));
   NG_TRY(ensure(c, c->walk_prefix, 4 * sizeof(uint32_t)));
-  // the host copy lives in the context, so a captured copy stays valid
-  fill_walk_desc(c, acc, accumulate, &c->h_walk_desc);
-  NG_CUDA(c, cudaMemcpyAsync(c->walk_desc.p, &c->h_walk_desc, sizeof(WalkDesc),
-                             cudaMemcpyHostToDevice, c->stream));
+  WalkDesc d;
+  fill_walk_desc(c, acc, accumulate, &d);
+  k_put_desc<<<1, 32, 0, c->stream>>>(d, as<WalkDesc>(c->walk_desc));
+  c->launches += 1;
+  NG_CUDA(c, cudaGetLastError());
   uint32_t* pre = as<uint32_t>(c->walk_prefix);
   return launch_walk_descs(c, c->stream, as<WalkDesc>(c->walk_desc), 1, pre, pre + 2,
                            count ? as<unsigned long long>(c->counter) : nullptr);
