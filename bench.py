@@ -9,8 +9,10 @@ CUDA graph through ng_step.
 metric: particle-node interactions per second, where the interactions are
 those of the per-particle Barnes-Hut walk (ng_count_interactions, the
 algorithm's unit of work: one (accepted node, species with mass) term or
-one body of an opened leaf), counted on the positions at the start and at
-the end of the timed region and averaged.
+one body of an opened leaf) on the canonical tree with leaf size 8, counted
+on the positions at the start and at the end of the timed region and
+averaged. The timed walk may run on a tree with another leaf size (the
+autotuner's choice); the count does not follow it.
 
 roofline: the dominant kernel is the walk, bound by the FP32 pipe; achieved
 = 23 flop x per-particle-walk interactions / average walk duration (CUDA
@@ -40,6 +42,34 @@ sys.path.insert(0, ROOT)
 
 FLOP_PER_INTERACTION = 23
 DEFAULT_WORKLOAD = "clustered16m_d4_yukawa"
+# The unit of work is counted on the canonical tree with this leaf size (the
+# library's default), whatever leaf size the timed walk runs with: the count
+# of the per-particle walk grows with the leaf size, the work to be done does not.
+REF_LEAF = 8
+
+
+def walk_traffic(workload, n_override, leaf, cell):
+    """DRAM bytes (read + write) of one walk launch, from the ncu capture recorded in
+    profiles/ for this workload and walk configuration; None unless that capture was
+    taken of the walk and tree sources as they are now (the SHA-256 of ng_walk.cu
+    followed by ng_tree.cu is recorded beside it)."""
+    import hashlib
+    import re
+    if workload != DEFAULT_WORKLOAD or n_override is not None:
+        return None
+    try:
+        text = open(os.path.join(ROOT, "profiles", "k_walk_clustered16m_d4_yukawa_dram.md")).read()
+        csrc = os.path.join(ROOT, "paper_1502_07442_gb300", "csrc")
+        src = b"".join(open(os.path.join(csrc, f), "rb").read() for f in ("ng_walk.cu", "ng_tree.cu"))
+    except OSError:
+        return None
+    sha = hashlib.sha256(src).hexdigest()
+    for line in text.splitlines():
+        m = re.search(r"traffic: leaf=(\d+) cell=(\d+) read=(\d+) write=(\d+) "
+                      r"source_sha256=([0-9a-f]{64})", line)
+        if m and int(m[1]) == leaf and int(m[2]) == cell and m[5] == sha:
+            return int(m[3]) + int(m[4])
+    return None
 
 
 def parse():
@@ -125,7 +155,7 @@ def cpu_leg(w, seconds, tag):
     sys.path.insert(0, os.path.join(ROOT, "tests"))
     prm = w["params"]
     op = oracle.make_params(prm["D"], prm["G"], box=prm["box"], eps=prm["eps"], rs=prm["rs"],
-                            rcut=prm["rcut"], theta=prm["theta"], leaf_size=prm["leaf_size"],
+                            rcut=prm["rcut"], theta=prm["theta"], leaf_size=REF_LEAF,
                             pm_mesh=prm["pm_mesh"], law=prm["law"], ya=prm["ya"], yl=prm["yl"])
     cores = oracle.set_threads(0)
     n = w["pos"].shape[1]
@@ -223,7 +253,14 @@ def main():
 
     # warm-up: the first call computes the initial force and captures the step graph
     ng.ng_step(sim.ctx, pos, vel, typ, mass, acc, False, args.warmup, dt)
-    count0 = ng.ng_count_interactions(sim.ctx)
+    ref = ng.Simulation(ng.params_from_workload(dict(w["params"], leaf_size=REF_LEAF)), stream)
+
+    def algorithmic():
+        # per-particle walk count on the reference tree of the current positions
+        ng.ng_build_tree(ref.ctx, pos, typ, mass)
+        return ng.ng_count_interactions(ref.ctx)
+
+    count0 = algorithmic()
     l0 = ng.ng_launch_count(sim.ctx)
     barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -235,7 +272,9 @@ def main():
     ms = e0.elapsed_time(e1)
     launches = ng.ng_launch_count(sim.ctx) - l0
     clocks = clk.summary()
-    count1 = ng.ng_count_interactions(sim.ctx)
+    count1 = algorithmic()
+    count_tuned_leaf = ng.ng_count_interactions(sim.ctx)
+    ref.close()
     count = 0.5 * (count0 + count1)
     if ws > 1:
         t = torch.tensor([ms], device=dev)
@@ -259,7 +298,9 @@ def main():
     achieved = FLOP_PER_INTERACTION * count1 / (walk / 1e3) / 1e12
     med = clocks.get("sm_mhz") or 2070.0
     roofline = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 2),
-                "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None,
+                "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
+                "traffic": walk_traffic(args.workload, args.n, int(w["params"]["leaf_size"]),
+                                        int(w["params"].get("group_cell", 0) or 32)),
                 "kernel": "k_walk", "walk_ms": round(walk, 3),
                 "peak_at_median_clock": round(nsm * 128 * 2 * med * 1e6 / 1e12, 2),
                 "frac_at_median_clock": round(achieved / (nsm * 128 * 2 * med * 1e6 / 1e12), 4),
@@ -310,7 +351,11 @@ def main():
                 "warmup": args.warmup, "ms_per_step": ms / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32", "data": "synthetic", "config": workload_config(w, args),
-                "interactions_per_step": count, "particles_per_s": n * args.steps * ws / (ms / 1e3),
+                "interactions_per_step": count,
+                "count_basis": f"per-particle walk (theta {w['params']['theta']}) on the canonical "
+                               f"tree with leaf size {REF_LEAF}",
+                "interactions_per_step_at_walk_leaf": int(count_tuned_leaf),
+                "particles_per_s": n * args.steps * ws / (ms / 1e3),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
                 "gpu_launches": int(launches), "autotune": tuned}
         print(json.dumps(line))
@@ -351,8 +396,8 @@ def bench_batch(args, ws, rank, local):
     L = lambda k: [x[k] for x in state]
     ng.ng_batch_step(b, L("pos"), L("vel"), L("typ"), L("mass"), L("acc"), False, args.warmup, 1e-3)
     # algorithmic interactions per simulation at the start of the timed region
-    for x, p in zip(state, params):
-        s = ng.Simulation(p)
+    for x, sp in zip(state, specs):
+        s = ng.Simulation(ng.params_from_workload(sp["params"], leaf_size=REF_LEAF))
         ng.ng_build_tree(s.ctx, x["pos"], x["typ"], x["mass"])
         counts.append(ng.ng_count_interactions(s.ctx))
         s.close()

@@ -125,6 +125,7 @@ struct ng_ctx {
   ng::DevBuf n_level, n_prefix, n_first, n_count, n_child, n_nchild, n_tmp, n_off;
   ng::DevBuf n_m64, n_cnt, n_geo, n_com, n_link, n_mono;
   ng::DevBuf groups;
+  ng::DevBuf gsize, grank;          // group size at its first body, rank of each group start
   ng::DevBuf status;     // uint32[ST_COUNT]
   ng::DevBuf walk_desc, walk_prefix;
   ng::DevBuf counter;    // unsigned long long
@@ -180,6 +181,7 @@ inline T* as(const DevBuf& b) { return static_cast<T*>(b.p); }
 // Device-wide exclusive scan of uint32 values; len read from *d_len when
 // d_len != nullptr (then len is an upper bound), total written to *d_total
 // when non-null. Needs ctx->scan_part scratch.
+int scan_u32_flags(ng_ctx* c, const uint32_t* in, uint32_t* out, int64_t len, uint32_t* d_total);
 int scan_u32(ng_ctx* c, const uint32_t* in, uint32_t* out, int64_t len,
              const uint32_t* d_len, uint32_t* d_total);
 

@@ -48,13 +48,13 @@ __device__ __forceinline__ int64_t scan_len(int64_t bound, const uint32_t* d_len
 
 __global__ void __launch_bounds__(kScanThreads)
 k_scan_partial(const uint32_t* __restrict__ in, int64_t bound, const uint32_t* d_len,
-               uint32_t* part) {
+               uint32_t* part, int as_flags) {
   const int64_t len = scan_len(bound, d_len);
   const int64_t chunk = (len + gridDim.x - 1) / gridDim.x;
   const int64_t b0 = (int64_t)blockIdx.x * chunk;
   const int64_t b1 = b0 + chunk < len ? b0 + chunk : len;
   uint32_t s = 0;
-  for (int64_t i = b0 + threadIdx.x; i < b1; i += blockDim.x) s += in[i];
+  for (int64_t i = b0 + threadIdx.x; i < b1; i += blockDim.x) s += as_flags ? (in[i] != 0u) : in[i];
 #pragma unroll
   for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   __shared__ uint32_t ws[32];
@@ -70,7 +70,7 @@ k_scan_partial(const uint32_t* __restrict__ in, int64_t bound, const uint32_t* d
 
 __global__ void __launch_bounds__(kScanThreads)
 k_scan_final(const uint32_t* in, uint32_t* out, int64_t bound, const uint32_t* d_len,
-             const uint32_t* __restrict__ part, uint32_t* d_total) {
+             const uint32_t* __restrict__ part, uint32_t* d_total, int as_flags) {
   __shared__ uint32_t warp_tot[32];
   __shared__ uint32_t tile_total;
   __shared__ uint32_t off;
@@ -89,7 +89,8 @@ k_scan_final(const uint32_t* in, uint32_t* out, int64_t bound, const uint32_t* d
   uint32_t carry = off;
   for (int64_t base = b0; base < b1; base += kScanThreads) {
     const int64_t i = base + threadIdx.x;
-    const uint32_t v = i < b1 ? in[i] : 0u;
+    uint32_t v = i < b1 ? in[i] : 0u;
+    if (as_flags) v = v != 0u;
     const uint32_t inc = block_inclusive_scan<kScanThreads>(v, warp_tot, &tile_total);
     if (i < b1) out[i] = carry + inc - v;
     __syncthreads();
@@ -103,8 +104,20 @@ int scan_u32(ng_ctx* c, const uint32_t* in, uint32_t* out, int64_t len, const ui
              uint32_t* d_total) {
   NG_TRY(ensure(c, c->scan_part, kScanBlocks * sizeof(uint32_t)));
   uint32_t* part = as<uint32_t>(c->scan_part);
-  k_scan_partial<<<kScanBlocks, kScanThreads, 0, c->stream>>>(in, len, d_len, part);
-  k_scan_final<<<kScanBlocks, kScanThreads, 0, c->stream>>>(in, out, len, d_len, part, d_total);
+  k_scan_partial<<<kScanBlocks, kScanThreads, 0, c->stream>>>(in, len, d_len, part, 0);
+  k_scan_final<<<kScanBlocks, kScanThreads, 0, c->stream>>>(in, out, len, d_len, part, d_total, 0);
+  c->launches += 2;
+  NG_CUDA(c, cudaGetLastError());
+  return NG_OK;
+}
+
+// Exclusive scan of the flags (in[i] != 0): out[i] = number of non-zero
+// entries before i; *d_total = number of non-zero entries.
+int scan_u32_flags(ng_ctx* c, const uint32_t* in, uint32_t* out, int64_t len, uint32_t* d_total) {
+  NG_TRY(ensure(c, c->scan_part, kScanBlocks * sizeof(uint32_t)));
+  uint32_t* part = as<uint32_t>(c->scan_part);
+  k_scan_partial<<<kScanBlocks, kScanThreads, 0, c->stream>>>(in, len, nullptr, part, 1);
+  k_scan_final<<<kScanBlocks, kScanThreads, 0, c->stream>>>(in, out, len, nullptr, part, d_total, 1);
   c->launches += 2;
   NG_CUDA(c, cudaGetLastError());
   return NG_OK;

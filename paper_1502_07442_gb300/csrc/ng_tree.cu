@@ -330,20 +330,20 @@ int reduce_monopoles(ng_ctx* c) {
 // Walk groups: runs of consecutive sibling cells holding <= S bodies each
 // (and <= S together) whose parent holds more than S, each run cut into
 // ceil(c / G) contiguous chunks of balanced size; leaves with more than S
-// bodies are cut the same way. Every body lands in exactly one group.
+// bodies are cut the same way. Every body lands in exactly one group, so a
+// group is named by its first body: gsize[first] = body count (zero
+// elsewhere). A flag scan then numbers the groups in body (Morton) order,
+// so that warps taking consecutive groups walk neighbouring regions and
+// share the nodes they fetch in L2.
 __global__ void k_groups(uint32_t* status, int64_t cap, int G, int S,
                          const uint32_t* __restrict__ first,
                          const uint32_t* __restrict__ count, const uint8_t* __restrict__ nchild,
-                         const uint32_t* __restrict__ child, int2* groups, int64_t gcap) {
+                         const uint32_t* __restrict__ child, uint32_t* gsize) {
   if (status[ST_FLAGS] & SF_NODE_OVERFLOW) return;
   Levels lv = levels_of(status);
   uint32_t total = lv.start[kMaxLevel + 1];
   if (total > cap) total = (uint32_t)cap;
-  auto emit = [&](uint32_t f, uint32_t c) {
-    const uint32_t g = atomicAdd(&status[ST_NGROUPS], 1u);
-    if (g < gcap) groups[g] = make_int2((int)f, (int)c);
-    else atomicOr(&status[ST_FLAGS], (uint32_t)SF_GROUP_OVERFLOW);
-  };
+  auto emit = [&](uint32_t f, uint32_t c) { gsize[f] = c; };
   auto emit_chunks = [&](uint32_t f, uint32_t c) {
     const uint32_t k = (c + G - 1) / G, base = c / k, rem = c % k;
     for (uint32_t j = 0, o = 0; j < k; ++j) {
@@ -380,14 +380,33 @@ __global__ void k_groups(uint32_t* status, int64_t cap, int G, int S,
   }
 }
 
+// groups[rank[b]] = (b, gsize[b]) for every group start b.
+__global__ void k_group_compact(int64_t n, const uint32_t* __restrict__ gsize,
+                                const uint32_t* __restrict__ rank, int2* __restrict__ groups) {
+  for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < n;
+       b += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t s = gsize[b];
+    if (s) groups[rank[b]] = make_int2((int)b, (int)s);
+  }
+}
+
 int build_groups(ng_ctx* c) {
-  NG_TRY(ensure(c, c->groups, (size_t)c->n * sizeof(int2)));
-  c->launches += 1;
+  const int64_t n = c->n;
+  NG_TRY(ensure(c, c->groups, (size_t)n * sizeof(int2)));
+  NG_TRY(ensure(c, c->gsize, (size_t)n * sizeof(uint32_t)));
+  NG_TRY(ensure(c, c->grank, (size_t)n * sizeof(uint32_t)));
+  uint32_t* gsize = as<uint32_t>(c->gsize);
+  uint32_t* grank = as<uint32_t>(c->grank);
+  NG_CUDA(c, cudaMemsetAsync(gsize, 0, (size_t)n * sizeof(uint32_t), c->stream));
+  c->launches += 2;   // groups, compaction (the flag scan counts itself)
   k_groups<<<device_grid(c, 4), 256, 0, c->stream>>>(
       as<uint32_t>(c->status), c->cap_nodes, c->p.group_size, c->p.group_cell,
       as<uint32_t>(c->n_first),
-      as<uint32_t>(c->n_count), as<uint8_t>(c->n_nchild), as<uint32_t>(c->n_child),
-      as<int2>(c->groups), c->n);
+      as<uint32_t>(c->n_count), as<uint8_t>(c->n_nchild), as<uint32_t>(c->n_child), gsize);
+  NG_CUDA(c, cudaGetLastError());
+  NG_TRY(scan_u32_flags(c, gsize, grank, n, as<uint32_t>(c->status) + ST_NGROUPS));
+  k_group_compact<<<device_grid(c, 8), 256, 0, c->stream>>>(n, gsize, grank,
+                                                          as<int2>(c->groups));
   NG_CUDA(c, cudaGetLastError());
   return NG_OK;
 }

@@ -10,8 +10,10 @@
 //           its D species monopoles go to D per-species record lists;
 //   leaf    a rejected leaf: its bodies go to the list of their species;
 //   open    a rejected internal node: its children are pushed.
-// When a list may overflow, all lists are evaluated: every lane interacts its
-// body with every record. Records and bodies are float4 {x, y, z, m} in
+// A record (monopole or body) that lies r_cut or more from the box is not
+// appended: it would contribute exactly zero to every body of the group.
+// A list that may overflow is evaluated: every lane interacts its body with
+// every record. Records and bodies are float4 {x, y, z, m} in
 // table units relative to a dyadic group origin, so node-centre offsets are
 // exact in FP32 and no FP64 enters the inner loop.
 //
@@ -40,6 +42,16 @@ constexpr float kMagic = 8388608.0f;   // 2^23
 constexpr int kMagicBits = 0x4B000000;
 
 __device__ __forceinline__ float wrap_unit(float d) { return d - rintf(d); }
+
+// A record at p (box units, relative to the group origin) can reach some body
+// of the group only if it lies within r_cut of the group box (half extents g
+// around the origin); records beyond contribute exactly zero for every body.
+__device__ __forceinline__ bool near_box(float px, float py, float pz, float gx, float gy,
+                                         float gz, float r2) {
+  const float ex = fmaxf(0.f, fabsf(px) - gx), ey = fmaxf(0.f, fabsf(py) - gy),
+              ez = fmaxf(0.f, fabsf(pz) - gz);
+  return fmaf(ex, ex, fmaf(ey, ey, ez * ez)) < r2;
+}
 
 // 8-byte shared-memory load from a 32-bit shared address
 __device__ __forceinline__ float2 lds_f2(uint32_t addr) {
@@ -89,6 +101,7 @@ __global__ void __launch_bounds__(walk_warps(D) * 32, 1) k_walk(WalkLaunch L) {
     __syncwarp();
     const uint32_t nnodes = DESC(status)[ST_LEVELS + kMaxLevel + 1];
     const float rc2 = DESC(rcut_box) * DESC(rcut_box);
+    const float rc2_keep = rc2 * 1.0001f;   // margin for FP32 rounding of the offsets
     const float s_tab = DESC(s_tab);
     const float eps2 = DESC(eps2_tab);
     const int2 gr = DESC(groups)[g - L.gprefix[lo_s]];
@@ -147,12 +160,18 @@ __global__ void __launch_bounds__(walk_warps(D) * 32, 1) k_walk(WalkLaunch L) {
       // ---- the single evaluation site: lists that could overflow on the
       // next round of (<= 32 per species) appends, or everything at the end
       const bool drain = size == 0 && qdone >= qtotal;
+      uint32_t fmask = 0;   // lists to evaluate now (the same in every lane)
+#pragma unroll
+      for (int q = 0; q < D; ++q)
+        if (lc[q] > kListCap - 32 || (drain && lc[q] > 0)) fmask |= 1u << q;
 #pragma unroll 1
-      for (int t = 0; t < D; ++t) {
+      while (fmask) {
+        const int t = __ffs(fmask) - 1;
+        fmask &= fmask - 1;
         int cnt = 0;
 #pragma unroll
         for (int q = 0; q < D; ++q) cnt = (q == t) ? lc[q] : cnt;
-        if (cnt > kListCap - 32 || (drain && cnt > 0)) {
+        {
           // shared address of segment k is tb + 8 * (float bits of k + 2^23), mod 2^32,
           // so the index needs no subtraction
           const uint32_t tb =
@@ -206,8 +225,9 @@ __global__ void __launch_bounds__(walk_warps(D) * 32, 1) k_walk(WalkLaunch L) {
           const int b = ws->leafb[lo].x + (f - ws->leafo[lo]);
           const float4 lc4 = ws->leafc[lo];
           const float4 bb = DESC(body)[b];
-          bt = DESC(btype)[b];
-          rec = make_float4((lc4.x + bb.x) * s_tab, (lc4.y + bb.y) * s_tab, (lc4.z + bb.z) * s_tab, bb.w);
+          const float px = lc4.x + bb.x, py = lc4.y + bb.y, pz = lc4.z + bb.z;
+          bt = near_box(px, py, pz, gx, gy, gz, rc2_keep) ? (int)DESC(btype)[b] : -1;
+          rec = make_float4(px * s_tab, py * s_tab, pz * s_tab, bb.w);
         }
 #pragma unroll
         for (int t = 0; t < D; ++t) {
@@ -275,11 +295,12 @@ __global__ void __launch_bounds__(walk_warps(D) * 32, 1) k_walk(WalkLaunch L) {
         for (int t = 0; t < D; ++t) {
           float4 mo = make_float4(0.f, 0.f, 0.f, 0.f);
           if (cls == 1) mo = DESC(mono)[(size_t)node * D + t];
-          const bool has = mo.w > 0.f;
+          const float px = dcx + mo.x, py = dcy + mo.y, pz = dcz + mo.z;
+          const bool has = mo.w > 0.f && near_box(px, py, pz, gx, gy, gz, rc2_keep);
           const uint32_t b = __ballot_sync(0xffffffffu, has);
           if (has)
             ws->list[t][lc[t] + __popc(b & lt)] =
-                make_float4((dcx + mo.x) * s_tab, (dcy + mo.y) * s_tab, (dcz + mo.z) * s_tab, mo.w);
+                make_float4(px * s_tab, py * s_tab, pz * s_tab, mo.w);
           lc[t] += __popc(b);
         }
       }
