@@ -160,14 +160,14 @@ __global__ void k_drift(int64_t m, double* __restrict__ pos, const float* __rest
 }
 
 int launch_kick(ng_ctx* c, int64_t n, float* vel, const float* acc, double h) {
-  k_kick<<<device_grid(c, 8), 256, 0, c->stream>>>(3 * n, vel, acc, (float)h);
+  k_kick<<<work_grid(c, 3 * n, 8), 256, 0, c->stream>>>(3 * n, vel, acc, (float)h);
   c->launches += 1;
   NG_CUDA(c, cudaGetLastError());
   return NG_OK;
 }
 
 int launch_drift(ng_ctx* c, int64_t n, double* pos, const float* vel, double dt) {
-  k_drift<<<device_grid(c, 8), 256, 0, c->stream>>>(3 * n, pos, vel, dt, c->L, 1.0 / c->L,
+  k_drift<<<work_grid(c, 3 * n, 8), 256, 0, c->stream>>>(3 * n, pos, vel, dt, c->L, 1.0 / c->L,
                                                     box_is_pow2(c->L));
   c->launches += 1;
   NG_CUDA(c, cudaGetLastError());
@@ -262,6 +262,8 @@ int build_checked(ng_ctx* c, int64_t n, const double* pos, const uint8_t* type,
     NG_TRY(type_order(c));
     NG_TRY(read_status(c, st));
     NG_TRY(check_flags(c, st[ST_FLAGS]));
+    c->ngroups = st[ST_NGROUPS];
+    c->ngroups_n = n;
     c->built = true;
     return NG_OK;
   }
@@ -471,7 +473,7 @@ int ng_pm_force(ng_ctx* c, float* acc_out) {
 
 static int step_once(ng_ctx* c, int64_t n, double* pos, float* vel, const uint8_t* type,
                      const float* mass, float* acc, double dt) {
-  const int grid = device_grid(c, 8);
+  const int grid = work_grid(c, 3 * n, 8);
   c->launches += 3;   // kick, drift, kick
   k_kick<<<grid, 256, 0, c->stream>>>(3 * n, vel, acc, (float)(0.5 * dt));
   k_drift<<<grid, 256, 0, c->stream>>>(3 * n, pos, vel, dt, c->L, 1.0 / c->L, box_is_pow2(c->L));
@@ -504,7 +506,7 @@ int ng_step(ng_ctx* c, int64_t n, double* pos, float* vel, const uint8_t* type,
   int done = 0;
   if (!reuse) {
     // one eager step sizes every buffer, then the step is captured
-    const int grid = device_grid(c, 8);
+    const int grid = work_grid(c, 3 * n, 8);
     k_kick<<<grid, 256, 0, c->stream>>>(3 * n, vel, acc, (float)(0.5 * dt));
     k_drift<<<grid, 256, 0, c->stream>>>(3 * n, pos, vel, dt, c->L, 1.0 / c->L, box_is_pow2(c->L));
     c->launches += 3;

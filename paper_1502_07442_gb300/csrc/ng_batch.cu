@@ -205,8 +205,10 @@ int batch_step_once(ng_batch* b, const int64_t* n, double* const* pos, float* co
                         origin) != cudaSuccess)
       r = fail(rep, NG_ECUDA, "descriptor copy failed");
     uint32_t* pre = as<uint32_t>(k.pre);
+    int64_t groups = 0;
+    for (int m : k.members) groups += walk_groups_hint(b->sims[m]);
     if (r == NG_OK)
-      r = launch_walk_descs(rep, origin, as<WalkDesc>(k.d), nd, pre, pre + nd + 1, nullptr);
+      r = launch_walk_descs(rep, origin, as<WalkDesc>(k.d), nd, pre, pre + nd + 1, nullptr, groups);
     rep->stream = keep;
     if (r != NG_OK) return from_sim(b, k.members[0], r);
   }

@@ -122,6 +122,7 @@ struct ng_ctx {
 
   // tree
   int64_t cap_nodes = 0, nnodes = 0;
+  int64_t ngroups = 0, ngroups_n = -1;   // walk groups of the last checked build, for n = ngroups_n
   ng::DevBuf n_level, n_prefix, n_first, n_count, n_child, n_nchild, n_tmp, n_off;
   ng::DevBuf n_m64, n_cnt, n_geo, n_com, n_link, n_mono;
   ng::DevBuf groups;
@@ -193,8 +194,10 @@ int reduce_monopoles(ng_ctx* c);              // needs octree
 int build_groups(ng_ctx* c);                  // needs octree
 int launch_walk(ng_ctx* c, float* acc, bool accumulate, bool count);
 void fill_walk_desc(ng_ctx* c, float* acc, bool accumulate, WalkDesc* d);
+int64_t walk_groups_hint(const ng_ctx* c);
 int launch_walk_descs(ng_ctx* c, cudaStream_t stream, const WalkDesc* d_descs, int ndesc,
-                      uint32_t* d_prefix, uint32_t* d_work, unsigned long long* counter);
+                      uint32_t* d_prefix, uint32_t* d_work, unsigned long long* counter,
+                      int64_t groups);
 int launch_count(ng_ctx* c, int64_t* counts);  // per-particle walk counts
 int pm_force(ng_ctx* c, float* acc, bool accumulate);
 extern std::mutex g_fft_plan_lock;   // see pm_setup
@@ -205,6 +208,11 @@ int build_tables(ng_ctx* c);
 double short_law_factor(int law, double a, double l, double rs, double rho);
 
 int device_grid(ng_ctx* c, int per_sm);
+// Blocks of 256 threads for a grid-stride kernel over `items` items: enough
+// to cover them, at most per_sm blocks per SM, at least one.
+int work_grid(ng_ctx* c, int64_t items, int per_sm);
+// Upper bound on the nodes of tree level l: 8^l and the body count.
+int64_t level_bound(int l, int64_t n);
 
 // Pipeline pieces shared by the single-simulation calls and the batch
 // runtime (ng_api.cu).

@@ -194,7 +194,8 @@ int pm_force(ng_ctx* c, float* acc, bool accumulate) {
   const size_t N3 = (size_t)N * N * N;
   const double L = c->L;
   NG_CUDA(c, cudaMemsetAsync(c->rho.p, 0, (size_t)D * N3 * sizeof(float), c->stream));
-  const int grid = device_grid(c, 8);
+  const int grid = work_grid(c, c->n, 8);
+  const int kgrid = work_grid(c, (int64_t)N * N * (N / 2 + 1), 8);
   c->launches += 3;   // deposit, k-space, interpolation (cuFFT kernels are the library's)
   k_cic_deposit<<<grid, 256, 0, c->stream>>>(c->n, as<uint32_t>(c->tperm), as<double>(c->spos),
                                             as<float>(c->smass), as<uint8_t>(c->stype), N,
@@ -220,12 +221,12 @@ int pm_force(ng_ctx* c, float* acc, bool accumulate) {
   const float rs2 = (float)(c->rs * c->rs);
   cufftComplex* mk = as<cufftComplex>(c->rhok);
   switch (D) {
-    case 1: k_kspace<1><<<grid, 256, 0, c->stream>>>(mk, N, kf, rs2, pref, law); break;
-    case 2: k_kspace<2><<<grid, 256, 0, c->stream>>>(mk, N, kf, rs2, pref, law); break;
-    case 3: k_kspace<3><<<grid, 256, 0, c->stream>>>(mk, N, kf, rs2, pref, law); break;
-    case 4: k_kspace<4><<<grid, 256, 0, c->stream>>>(mk, N, kf, rs2, pref, law); break;
-    case 5: k_kspace<5><<<grid, 256, 0, c->stream>>>(mk, N, kf, rs2, pref, law); break;
-    default: k_kspace<6><<<grid, 256, 0, c->stream>>>(mk, N, kf, rs2, pref, law); break;
+    case 1: k_kspace<1><<<kgrid, 256, 0, c->stream>>>(mk, N, kf, rs2, pref, law); break;
+    case 2: k_kspace<2><<<kgrid, 256, 0, c->stream>>>(mk, N, kf, rs2, pref, law); break;
+    case 3: k_kspace<3><<<kgrid, 256, 0, c->stream>>>(mk, N, kf, rs2, pref, law); break;
+    case 4: k_kspace<4><<<kgrid, 256, 0, c->stream>>>(mk, N, kf, rs2, pref, law); break;
+    case 5: k_kspace<5><<<kgrid, 256, 0, c->stream>>>(mk, N, kf, rs2, pref, law); break;
+    default: k_kspace<6><<<kgrid, 256, 0, c->stream>>>(mk, N, kf, rs2, pref, law); break;
   }
   NG_CUDA(c, cudaGetLastError());
   if (cufftExecC2R(c->plan_c2r, mk, as<cufftReal>(c->phi)) != CUFFT_SUCCESS)

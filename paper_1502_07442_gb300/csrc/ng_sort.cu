@@ -100,12 +100,19 @@ k_scan_final(const uint32_t* in, uint32_t* out, int64_t bound, const uint32_t* d
   if (d_total && blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) *d_total = carry;
 }
 
+static int scan_blocks(int64_t len) {
+  return (int)std::max<int64_t>(
+      1, std::min<int64_t>(kScanBlocks, (len + 4 * kScanThreads - 1) / (4 * kScanThreads)));
+}
+
 int scan_u32(ng_ctx* c, const uint32_t* in, uint32_t* out, int64_t len, const uint32_t* d_len,
              uint32_t* d_total) {
   NG_TRY(ensure(c, c->scan_part, kScanBlocks * sizeof(uint32_t)));
   uint32_t* part = as<uint32_t>(c->scan_part);
-  k_scan_partial<<<kScanBlocks, kScanThreads, 0, c->stream>>>(in, len, d_len, part, 0);
-  k_scan_final<<<kScanBlocks, kScanThreads, 0, c->stream>>>(in, out, len, d_len, part, d_total, 0);
+  // blocks for at most 4 tiles each; both kernels split the range by gridDim
+  const int blocks = scan_blocks(len);
+  k_scan_partial<<<blocks, kScanThreads, 0, c->stream>>>(in, len, d_len, part, 0);
+  k_scan_final<<<blocks, kScanThreads, 0, c->stream>>>(in, out, len, d_len, part, d_total, 0);
   c->launches += 2;
   NG_CUDA(c, cudaGetLastError());
   return NG_OK;
@@ -116,8 +123,9 @@ int scan_u32(ng_ctx* c, const uint32_t* in, uint32_t* out, int64_t len, const ui
 int scan_u32_flags(ng_ctx* c, const uint32_t* in, uint32_t* out, int64_t len, uint32_t* d_total) {
   NG_TRY(ensure(c, c->scan_part, kScanBlocks * sizeof(uint32_t)));
   uint32_t* part = as<uint32_t>(c->scan_part);
-  k_scan_partial<<<kScanBlocks, kScanThreads, 0, c->stream>>>(in, len, nullptr, part, 1);
-  k_scan_final<<<kScanBlocks, kScanThreads, 0, c->stream>>>(in, out, len, nullptr, part, d_total, 1);
+  const int blocks = scan_blocks(len);
+  k_scan_partial<<<blocks, kScanThreads, 0, c->stream>>>(in, len, nullptr, part, 1);
+  k_scan_final<<<blocks, kScanThreads, 0, c->stream>>>(in, out, len, nullptr, part, d_total, 1);
   c->launches += 2;
   NG_CUDA(c, cudaGetLastError());
   return NG_OK;
@@ -285,6 +293,16 @@ __global__ void k_iota(int64_t n, uint32_t* out) {
 
 int device_grid(ng_ctx* c, int per_sm) { return c->nsm * per_sm; }
 
+int work_grid(ng_ctx* c, int64_t items, int per_sm) {
+  const int64_t need = (items + 255) / 256;
+  const int64_t most = (int64_t)c->nsm * per_sm;
+  return (int)std::max<int64_t>(1, std::min(need, most));
+}
+
+int64_t level_bound(int l, int64_t n) {
+  return l >= 21 ? n : std::min<int64_t>(n, (int64_t)1 << (3 * l));
+}
+
 bool box_is_pow2(double L) {
   int e = 0;
   return std::frexp(L, &e) == 0.5;
@@ -303,7 +321,7 @@ int sort_bodies(ng_ctx* c, int64_t n, const double* pos, const uint8_t* type, co
   NG_TRY(ensure(c, c->tperm, n * 4));
   uint64_t *ka = as<uint64_t>(c->keys_a), *kb = as<uint64_t>(c->keys_b);
   uint32_t *va = as<uint32_t>(c->vals_a), *vb = as<uint32_t>(c->vals_b);
-  const int grid = device_grid(c, 8);
+  const int grid = work_grid(c, n, 8);
   const bool pow2 = box_is_pow2(c->L);
   k_keys<<<grid, 256, 0, c->stream>>>(n, pos, type, c->L, 1.0 / c->L, pow2, ka, va);
   c->launches += 2;   // keys + gather
@@ -325,7 +343,7 @@ int sort_bodies(ng_ctx* c, int64_t n, const double* pos, const uint8_t* type, co
 // keys. tperm[j] = sorted index of the j-th body in type-major order.
 int type_order(ng_ctx* c) {
   const int64_t n = c->n;
-  const int grid = device_grid(c, 8);
+  const int grid = work_grid(c, n, 8);
   uint64_t *ka = as<uint64_t>(c->keys_a), *kb = as<uint64_t>(c->keys_b);
   uint32_t* vb = as<uint32_t>(c->vals_b);
   k_iota<<<grid, 256, 0, c->stream>>>(n, vb);

@@ -140,13 +140,15 @@ int build_octree(ng_ctx* c) {
   const int leaf = c->p.leaf_size;
   k_tree_init<<<1, 32, 0, c->stream>>>(st, n, level, prefix, first, count);
   c->launches += 1 + (kMaxLevel + 1) + kMaxLevel;   // init, counts, emits (scans count themselves)
-  const int grid = device_grid(c, 4);
   for (int l = 0; l <= kMaxLevel; ++l) {
+    // grids sized by the most nodes level l can hold (kernels stride over the actual count)
+    const int64_t bound = std::min<int64_t>(cap, level_bound(l, c->n));
+    const int grid = work_grid(c, bound, 4);
     k_tree_count<<<grid, 256, 0, c->stream>>>(l, st, cap, leaf, keys, first, count, nchild, tmp);
     if (l == kMaxLevel) break;
     // children per level: exclusive scan of the per-node child counts
     uint32_t* lvcount = st + ST_LEVELS + kMaxLevel + 2;
-    NG_TRY(scan_u32(c, tmp, tmp, cap, lvcount + l, lvcount + l + 1));
+    NG_TRY(scan_u32(c, tmp, tmp, bound, lvcount + l, lvcount + l + 1));
     k_tree_emit<<<grid, 256, 0, c->stream>>>(l, st, cap, keys, level, prefix, first, count,
                                              nchild, child, tmp);
   }
@@ -309,9 +311,9 @@ int reduce_monopoles(ng_ctx* c) {
   a.n = c->n;
   a.cap = c->cap_nodes;
   a.invL = 1.0 / c->L;
-  const int grid = device_grid(c, 8);
   c->launches += kMaxLevel + 1;
   for (int l = kMaxLevel; l >= 0; --l) {
+    const int grid = work_grid(c, std::min<int64_t>(c->cap_nodes, level_bound(l, c->n)), 8);
     switch (c->p.D) {
       case 1: k_monopoles<1><<<grid, 256, 0, c->stream>>>(l, a); break;
       case 2: k_monopoles<2><<<grid, 256, 0, c->stream>>>(l, a); break;
@@ -399,13 +401,13 @@ int build_groups(ng_ctx* c) {
   uint32_t* grank = as<uint32_t>(c->grank);
   NG_CUDA(c, cudaMemsetAsync(gsize, 0, (size_t)n * sizeof(uint32_t), c->stream));
   c->launches += 2;   // groups, compaction (the flag scan counts itself)
-  k_groups<<<device_grid(c, 4), 256, 0, c->stream>>>(
+  k_groups<<<work_grid(c, std::min<int64_t>(c->cap_nodes, 2 * n + 64), 4), 256, 0, c->stream>>>(
       as<uint32_t>(c->status), c->cap_nodes, c->p.group_size, c->p.group_cell,
       as<uint32_t>(c->n_first),
       as<uint32_t>(c->n_count), as<uint8_t>(c->n_nchild), as<uint32_t>(c->n_child), gsize);
   NG_CUDA(c, cudaGetLastError());
   NG_TRY(scan_u32_flags(c, gsize, grank, n, as<uint32_t>(c->status) + ST_NGROUPS));
-  k_group_compact<<<device_grid(c, 8), 256, 0, c->stream>>>(n, gsize, grank,
+  k_group_compact<<<work_grid(c, n, 8), 256, 0, c->stream>>>(n, gsize, grank,
                                                           as<int2>(c->groups));
   NG_CUDA(c, cudaGetLastError());
   return NG_OK;

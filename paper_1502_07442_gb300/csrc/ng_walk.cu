@@ -429,7 +429,7 @@ static size_t walk_smem(int nlaws, int entries, int nwarps) {
 }
 
 template <int D>
-static int launch_walk_d(ng_ctx* c, cudaStream_t stream, const WalkLaunch& L) {
+static int launch_walk_d(ng_ctx* c, cudaStream_t stream, const WalkLaunch& L, int64_t groups) {
   int nwarps = walk_warps(D);
   while (nwarps > 1 && walk_smem<D>(L.nlaws, L.tab_entries, nwarps) > c->smem_optin) --nwarps;
   const size_t smem = walk_smem<D>(L.nlaws, L.tab_entries, nwarps);
@@ -443,7 +443,11 @@ static int launch_walk_d(ng_ctx* c, cudaStream_t stream, const WalkLaunch& L) {
   NG_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walk<D>, nwarps * 32,
                                                            smem));
   if (per_sm < 1) per_sm = 1;
-  k_walk<D><<<c->nsm * per_sm, nwarps * 32, smem, stream>>>(L);
+  // persistent warps take groups from a counter: no more blocks than the
+  // expected groups need, so small problems leave SMs to concurrent work
+  const int64_t want = (std::max<int64_t>(groups, 1) + nwarps - 1) / nwarps;
+  const int grid = (int)std::min<int64_t>((int64_t)c->nsm * per_sm, want);
+  k_walk<D><<<grid, nwarps * 32, smem, stream>>>(L);
   c->launches += 1;
   NG_CUDA(c, cudaGetLastError());
   return NG_OK;
@@ -476,19 +480,26 @@ void fill_walk_desc(ng_ctx* c, float* acc, bool accumulate, WalkDesc* d) {
     }
 }
 
-static int dispatch_walk(ng_ctx* c, cudaStream_t stream, const WalkLaunch& L) {
+static int dispatch_walk(ng_ctx* c, cudaStream_t stream, const WalkLaunch& L, int64_t groups) {
   switch (c->p.D) {
-    case 1: return launch_walk_d<1>(c, stream, L);
-    case 2: return launch_walk_d<2>(c, stream, L);
-    case 3: return launch_walk_d<3>(c, stream, L);
-    case 4: return launch_walk_d<4>(c, stream, L);
-    case 5: return launch_walk_d<5>(c, stream, L);
-    default: return launch_walk_d<6>(c, stream, L);
+    case 1: return launch_walk_d<1>(c, stream, L, groups);
+    case 2: return launch_walk_d<2>(c, stream, L, groups);
+    case 3: return launch_walk_d<3>(c, stream, L, groups);
+    case 4: return launch_walk_d<4>(c, stream, L, groups);
+    case 5: return launch_walk_d<5>(c, stream, L, groups);
+    default: return launch_walk_d<6>(c, stream, L, groups);
   }
 }
 
+int64_t walk_groups_hint(const ng_ctx* c) {
+  // the group count of the last checked build of this size, else a guess
+  // from the body count (grids only size the launch, every group is walked)
+  return c->ngroups_n == c->n && c->ngroups > 0 ? c->ngroups : (c->n + 15) / 16;
+}
+
 int launch_walk_descs(ng_ctx* c, cudaStream_t stream, const WalkDesc* d_descs, int ndesc,
-                      uint32_t* d_prefix, uint32_t* d_work, unsigned long long* counter) {
+                      uint32_t* d_prefix, uint32_t* d_work, unsigned long long* counter,
+                      int64_t groups) {
   k_walk_prep<<<1, 1024, 0, stream>>>(d_descs, ndesc, d_prefix, d_work);
   c->launches += 1;
   NG_CUDA(c, cudaGetLastError());
@@ -502,7 +513,7 @@ int launch_walk_descs(ng_ctx* c, cudaStream_t stream, const WalkDesc* d_descs, i
   L.ncut = c->ncut;
   L.nlaws = c->nlaws;
   L.counter = counter;
-  return dispatch_walk(c, stream, L);
+  return dispatch_walk(c, stream, L, groups);
 }
 
 // The descriptor travels as a kernel argument (captured by value, also in
@@ -522,7 +533,8 @@ int launch_walk(ng_ctx* c, float* acc, bool accumulate, bool count) {
   NG_CUDA(c, cudaGetLastError());
   uint32_t* pre = as<uint32_t>(c->walk_prefix);
   return launch_walk_descs(c, c->stream, as<WalkDesc>(c->walk_desc), 1, pre, pre + 2,
-                           count ? as<unsigned long long>(c->counter) : nullptr);
+                           count ? as<unsigned long long>(c->counter) : nullptr,
+                           walk_groups_hint(c));
 }
 
 // ------------------------------------------------ per-particle count walk
