@@ -49,6 +49,30 @@ __device__ __forceinline__ uint32_t octant_bound(const uint64_t* __restrict__ ke
   return lo;
 }
 
+// Both kernels give each node of level lvl a team of 8 lanes: lane o finds
+// where octant o of the node's (sorted) body range starts, all 8 binary
+// searches at once, so a level with few large nodes (the top of the tree)
+// waits for one search, not eight in a row. Teams of a warp loop together
+// (every lane runs the same iterations, so the team shuffles are safe).
+struct OctTeam {
+  uint32_t start, end;   // octant `sub` of the node: bodies [start, end)
+  bool nonempty;
+  uint32_t bits;         // non-empty octants of the node, bit o for octant o
+};
+
+__device__ __forceinline__ OctTeam octant_team(const uint64_t* __restrict__ keys, bool split,
+                                               uint32_t f, uint32_t c, int shift, int sub,
+                                               int lane) {
+  OctTeam t;
+  t.start = (split && sub > 0) ? octant_bound(keys, f, f + c, shift, (uint32_t)sub) : f;
+  const uint32_t nxt = __shfl_down_sync(0xffffffffu, t.start, 1, 8);
+  t.end = sub == 7 ? f + c : nxt;
+  t.nonempty = split && t.end > t.start;
+  const uint32_t m = __ballot_sync(0xffffffffu, t.nonempty);
+  t.bits = (m >> (lane & 24)) & 0xffu;
+  return t;
+}
+
 __global__ void k_tree_count(int lvl, uint32_t* status, int64_t cap, int leaf_size,
                              const uint64_t* __restrict__ keys, const uint32_t* __restrict__ first,
                              const uint32_t* __restrict__ count, uint8_t* nchild,
@@ -57,21 +81,23 @@ __global__ void k_tree_count(int lvl, uint32_t* status, int64_t cap, int leaf_si
   const uint32_t s = lv.start[lvl];
   uint32_t e = lv.start[lvl + 1];
   if (e > cap) e = (uint32_t)cap;
+  const int nodes = e > s ? (int)(e - s) : 0;
   const int shift = 3 * (kMaxLevel - (lvl + 1));
-  for (uint32_t k = s + blockIdx.x * blockDim.x + threadIdx.x; k < e;
-       k += gridDim.x * blockDim.x) {
-    const uint32_t f = first[k], c = count[k];
-    uint32_t nch = 0;
-    if ((int)c > leaf_size && lvl < kMaxLevel) {
-      uint32_t prev = f;
-      for (uint32_t o = 1; o <= 8; ++o) {
-        const uint32_t b = o < 8 ? octant_bound(keys, prev, f + c, shift, o) : f + c;
-        nch += b > prev;
-        prev = b;
-      }
+  const int lane = threadIdx.x & 31, sub = lane & 7;
+  const int64_t team = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 3;
+  const int64_t teams = ((int64_t)gridDim.x * blockDim.x) >> 3;   // a multiple of 4
+  for (int64_t base = team & ~(int64_t)3; base < nodes; base += teams) {
+    const int64_t j = base + (team & 3);
+    const bool valid = j < nodes;
+    const uint32_t k = s + (uint32_t)j;
+    const uint32_t f = valid ? first[k] : 0u, c = valid ? count[k] : 0u;
+    const bool split = valid && (int)c > leaf_size && lvl < kMaxLevel;
+    const OctTeam t = octant_team(keys, split, f, c, shift, sub, lane);
+    if (valid && sub == 0) {
+      const uint32_t nch = (uint32_t)__popc(t.bits);
+      nchild[k] = (uint8_t)nch;
+      tmp[k - s] = nch;
     }
-    nchild[k] = (uint8_t)nch;
-    tmp[k - s] = nch;
   }
 }
 
@@ -95,32 +121,33 @@ __global__ void k_tree_emit(int lvl, uint32_t* status, int64_t cap,
       if (end > (uint64_t)cap) status[ST_FLAGS] |= (uint32_t)SF_NODE_OVERFLOW;
     }
   }
+  const int nodes = e > s ? (int)(e - s) : 0;
   const int shift = 3 * (kMaxLevel - (lvl + 1));
-  for (uint32_t k = s + blockIdx.x * blockDim.x + threadIdx.x; k < e;
-       k += gridDim.x * blockDim.x) {
-    const uint32_t nch = nchild[k];
-    if (nch == 0) {
-      child[k] = 0xffffffffu;
+  const int lane = threadIdx.x & 31, sub = lane & 7;
+  const int64_t team = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 3;
+  const int64_t teams = ((int64_t)gridDim.x * blockDim.x) >> 3;
+  for (int64_t base = team & ~(int64_t)3; base < nodes; base += teams) {
+    const int64_t j = base + (team & 3);
+    const bool valid = j < nodes;
+    const uint32_t k = s + (uint32_t)j;
+    const uint32_t nch = valid ? nchild[k] : 0u;
+    const bool split = nch > 0;
+    const uint32_t f = split ? first[k] : 0u, c = split ? count[k] : 0u;
+    const OctTeam t = octant_team(keys, split, f, c, shift, sub, lane);
+    if (!split) {
+      if (valid && sub == 0) child[k] = 0xffffffffu;
       continue;
     }
     const uint32_t c0 = next0 + off[k - s];
-    child[k] = c0;
-    const uint32_t f = first[k], c = count[k];
-    const uint64_t pre = prefix[k];
-    uint32_t prev = f, j = 0;
-    for (uint32_t o = 1; o <= 8; ++o) {
-      const uint32_t b = o < 8 ? octant_bound(keys, prev, f + c, shift, o) : f + c;
-      if (b > prev) {
-        const uint64_t id = (uint64_t)c0 + j;
-        if (id < (uint64_t)cap) {
-          level[id] = (uint8_t)(lvl + 1);
-          prefix[id] = (pre << 3) | (uint64_t)(o - 1);
-          first[id] = prev;
-          count[id] = b - prev;
-        }
-        ++j;
+    if (sub == 0) child[k] = c0;
+    if (t.nonempty) {
+      const uint64_t id = (uint64_t)c0 + (uint32_t)__popc(t.bits & ((1u << sub) - 1u));
+      if (id < (uint64_t)cap) {
+        level[id] = (uint8_t)(lvl + 1);
+        prefix[id] = (prefix[k] << 3) | (uint64_t)sub;
+        first[id] = t.start;
+        count[id] = t.end - t.start;
       }
-      prev = b;
     }
   }
 }
@@ -143,7 +170,7 @@ int build_octree(ng_ctx* c) {
   for (int l = 0; l <= kMaxLevel; ++l) {
     // grids sized by the most nodes level l can hold (kernels stride over the actual count)
     const int64_t bound = std::min<int64_t>(cap, level_bound(l, c->n));
-    const int grid = work_grid(c, bound, 4);
+    const int grid = work_grid(c, 8 * bound, 4);   // 8 lanes per node
     k_tree_count<<<grid, 256, 0, c->stream>>>(l, st, cap, leaf, keys, first, count, nchild, tmp);
     if (l == kMaxLevel) break;
     // children per level: exclusive scan of the per-node child counts
@@ -197,18 +224,28 @@ struct MonoArgs {
   uint32_t* bleaf;         // [sorted body] leaf index
   uint32_t* status;
   int64_t n, cap;
-  double invL;
+  double invL, L;
 };
 
 // One thread per node of level lvl (FP64 is ~1/64 of the FP32 rate here, so
 // every FP64 operation counts): a leaf adds each body to its own species
-// (4 FP64 operations per body) and writes the body records; an internal node
-// adds its <= 8 children. The FP32 walk records need no FP64 division: the
+// (4 FP64 operations per body, in shared-memory slots chosen by the species)
+// and writes the body records (offset from the leaf centre, subtracted in
+// FP64 in physical units, scaled to box units in FP32); an internal node adds
+// its <= 8 children. The FP32 walk records need no FP64 division: the
 // mass-weighted offset sum(m x) - M c is formed with one FP64 FMA and divided
 // by M in FP32.
+constexpr int kMonoThreads = 128;
+
 template <int D>
-__global__ void __launch_bounds__(256) k_monopoles(int lvl, MonoArgs a) {
+__global__ void __launch_bounds__(kMonoThreads) k_monopoles(int lvl, MonoArgs a) {
+  // per-thread leaf sums per species {m, m x, m y, m z} (physical units),
+  // addressed by the body's species: no FP64 instruction is spent on the
+  // species a body does not have (predicated per-species sums would issue D
+  // times as many, and FP64 issues at 1/64 of the FP32 rate here)
+  __shared__ double lacc[D][4][kMonoThreads];
   if (a.status[ST_FLAGS] & SF_NODE_OVERFLOW) return;   // truncated tree: do not read it
+  const int tid = threadIdx.x;
   Levels lv = levels_of(a.status);
   const uint32_t s = lv.start[lvl];
   uint32_t e = lv.start[lvl + 1];
@@ -224,25 +261,35 @@ __global__ void __launch_bounds__(256) k_monopoles(int lvl, MonoArgs a) {
     const uint32_t nch = a.nchild[k];
     const uint32_t f = a.first[k], c = a.count[k];
     if (nch == 0) {
+#pragma unroll
+      for (int q = 0; q < D; ++q)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) lacc[q][j][tid] = 0.0;
+      // leaf centre in physical units; body records are offsets from it in box units
+      const double cxL = cen[0] * a.L, cyL = cen[1] * a.L, czL = cen[2] * a.L;
+      const float invLf = (float)a.invL;
       for (uint32_t b = f; b < f + c; ++b) {
-        const double x = a.spos[b] * a.invL, y = a.spos[a.n + b] * a.invL,
-                     z = a.spos[2 * a.n + b] * a.invL;
+        const double xp = a.spos[b], yp = a.spos[a.n + b], zp = a.spos[2 * a.n + b];
         const float m = a.smass[b];
         const int t = a.stype[b];
-        a.body[b] = make_float4((float)(x - cen[0]), (float)(y - cen[1]), (float)(z - cen[2]), m);
+        a.body[b] = make_float4((float)(xp - cxL) * invLf, (float)(yp - cyL) * invLf,
+                                (float)(zp - czL) * invLf, m);
         a.bleaf[b] = k;
         const double md = (double)m;
-        // species slot chosen by an unrolled compare (no dynamic register index)
+        lacc[t][0][tid] += md;
+        lacc[t][1][tid] = fma(md, xp, lacc[t][1][tid]);
+        lacc[t][2][tid] = fma(md, yp, lacc[t][2][tid]);
+        lacc[t][3][tid] = fma(md, zp, lacc[t][3][tid]);
 #pragma unroll
-        for (int q = 0; q < D; ++q) {
-          if (t == q) {
-            sm[q] += md;
-            sx[q] = fma(md, x, sx[q]);
-            sy[q] = fma(md, y, sy[q]);
-            sz[q] = fma(md, z, sz[q]);
-            sc[q] += 1u;
-          }
-        }
+        for (int q = 0; q < D; ++q) sc[q] += t == q ? 1u : 0u;
+      }
+      // to box units (exact when the box is a power of two)
+#pragma unroll
+      for (int q = 0; q < D; ++q) {
+        sm[q] = lacc[q][0][tid];
+        sx[q] = lacc[q][1][tid] * a.invL;
+        sy[q] = lacc[q][2][tid] * a.invL;
+        sz[q] = lacc[q][3][tid] * a.invL;
       }
     } else {
       const uint32_t c0 = a.child[k];
@@ -311,16 +358,19 @@ int reduce_monopoles(ng_ctx* c) {
   a.n = c->n;
   a.cap = c->cap_nodes;
   a.invL = 1.0 / c->L;
+  a.L = c->L;
   c->launches += kMaxLevel + 1;
   for (int l = kMaxLevel; l >= 0; --l) {
-    const int grid = work_grid(c, std::min<int64_t>(c->cap_nodes, level_bound(l, c->n)), 8);
+    const int64_t nodes = std::min<int64_t>(c->cap_nodes, level_bound(l, c->n));
+    const int grid = (int)std::max<int64_t>(
+        1, std::min<int64_t>((int64_t)c->nsm * 16, (nodes + kMonoThreads - 1) / kMonoThreads));
     switch (c->p.D) {
-      case 1: k_monopoles<1><<<grid, 256, 0, c->stream>>>(l, a); break;
-      case 2: k_monopoles<2><<<grid, 256, 0, c->stream>>>(l, a); break;
-      case 3: k_monopoles<3><<<grid, 256, 0, c->stream>>>(l, a); break;
-      case 4: k_monopoles<4><<<grid, 256, 0, c->stream>>>(l, a); break;
-      case 5: k_monopoles<5><<<grid, 256, 0, c->stream>>>(l, a); break;
-      default: k_monopoles<6><<<grid, 256, 0, c->stream>>>(l, a); break;
+      case 1: k_monopoles<1><<<grid, kMonoThreads, 0, c->stream>>>(l, a); break;
+      case 2: k_monopoles<2><<<grid, kMonoThreads, 0, c->stream>>>(l, a); break;
+      case 3: k_monopoles<3><<<grid, kMonoThreads, 0, c->stream>>>(l, a); break;
+      case 4: k_monopoles<4><<<grid, kMonoThreads, 0, c->stream>>>(l, a); break;
+      case 5: k_monopoles<5><<<grid, kMonoThreads, 0, c->stream>>>(l, a); break;
+      default: k_monopoles<6><<<grid, kMonoThreads, 0, c->stream>>>(l, a); break;
     }
   }
   NG_CUDA(c, cudaGetLastError());
