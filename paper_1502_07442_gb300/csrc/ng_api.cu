@@ -155,7 +155,9 @@ __global__ void k_drift(int64_t m, double* __restrict__ pos, const float* __rest
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
        i += (int64_t)gridDim.x * blockDim.x) {
     const double x = fma((double)vel[i], dt, pos[i]);
-    pos[i] = x - L * floor(pow2 ? x * invL : x / L);
+    // in a power-of-two box, x in [+0, L) wraps to itself (decided on the bits)
+    const long long b = __double_as_longlong(x);
+    pos[i] = pow2 && b >= 0 && b < __double_as_longlong(L) ? x : x - L * floor(pow2 ? x * invL : x / L);
   }
 }
 

@@ -141,12 +141,37 @@ __device__ __forceinline__ double div_box(double x, double L, double invL, bool 
 
 // Periodic wrap x - L floor(x / L) with each operation rounded separately
 // (no fused multiply-add), so that the host reference rounds identically.
+// FP64 issues at 1/64 of the FP32 rate here, so for a power-of-two box the
+// common case is decided on the bits: a non-negative double orders like its
+// bit pattern, and for x in [+0, L) x / L is exact and below 1, so the wrap
+// returns x itself.
 __device__ __forceinline__ double wrap_box(double x, double L, double invL, bool pow2) {
+  if (pow2) {
+    const long long b = __double_as_longlong(x);
+    if (b >= 0 && b < __double_as_longlong(L)) return x;
+  }
   const double f = floor(div_box(x, L, invL, pow2));
   return __dsub_rn(x, __dmul_rn(L, f));
 }
 
-__device__ __forceinline__ uint64_t quantise20(double w, double L, double invL, bool pow2) {
+// floor(w / L * 2^20) clamped to [0, 2^20 - 1]. For a box L = 2^ebox the
+// scaled value is w * 2^(20 - ebox) exactly, and its integer part is read
+// from the exponent and mantissa bits (the same number the FP64 formula
+// gives, without FP64 instructions).
+__device__ __forceinline__ uint64_t quantise20(double w, double L, double invL, bool pow2,
+                                               int ebox) {
+  if (pow2) {
+    const long long b = __double_as_longlong(w);
+    const int e = (int)((b >> 52) & 0x7ff);
+    if (b <= 0) return 0;                        // +0, -0 and negative w
+    if (e != 0x7ff) {                            // finite w > 0
+      const int sh = e - 1023 + 20 - ebox;      // w * 2^(20 - ebox) = 1.m * 2^sh
+      if (sh < 0) return 0;
+      if (sh >= 20) return 1048575;
+      const uint64_t m = ((uint64_t)b & ((1ull << 52) - 1)) | (1ull << 52);
+      return m >> (52 - sh);
+    }
+  }
   double q = floor(__dmul_rn(div_box(w, L, invL, pow2), 1048576.0));
   q = q < 0.0 ? 0.0 : q;
   q = q > 1048575.0 ? 1048575.0 : q;
@@ -165,13 +190,13 @@ __device__ __forceinline__ uint64_t spread3(uint64_t v) {
 }
 
 __global__ void k_keys(int64_t n, const double* __restrict__ pos, const uint8_t* __restrict__ type,
-                       double L, double invL, bool pow2, uint64_t* __restrict__ keys,
+                       double L, double invL, bool pow2, int ebox, uint64_t* __restrict__ keys,
                        uint32_t* __restrict__ idx) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const uint64_t qx = quantise20(wrap_box(pos[i], L, invL, pow2), L, invL, pow2);
-    const uint64_t qy = quantise20(wrap_box(pos[n + i], L, invL, pow2), L, invL, pow2);
-    const uint64_t qz = quantise20(wrap_box(pos[2 * n + i], L, invL, pow2), L, invL, pow2);
+    const uint64_t qx = quantise20(wrap_box(pos[i], L, invL, pow2), L, invL, pow2, ebox);
+    const uint64_t qy = quantise20(wrap_box(pos[n + i], L, invL, pow2), L, invL, pow2, ebox);
+    const uint64_t qz = quantise20(wrap_box(pos[2 * n + i], L, invL, pow2), L, invL, pow2, ebox);
     const uint64_t m = (spread3(qx) << 2) | (spread3(qy) << 1) | spread3(qz);
     keys[i] = (m << 3) | (uint64_t)(type[i] & 7);
     idx[i] = (uint32_t)i;
@@ -323,7 +348,8 @@ int sort_bodies(ng_ctx* c, int64_t n, const double* pos, const uint8_t* type, co
   uint32_t *va = as<uint32_t>(c->vals_a), *vb = as<uint32_t>(c->vals_b);
   const int grid = work_grid(c, n, 8);
   const bool pow2 = box_is_pow2(c->L);
-  k_keys<<<grid, 256, 0, c->stream>>>(n, pos, type, c->L, 1.0 / c->L, pow2, ka, va);
+  k_keys<<<grid, 256, 0, c->stream>>>(n, pos, type, c->L, 1.0 / c->L, pow2,
+                                      pow2 ? std::ilogb(c->L) : 0, ka, va);
   c->launches += 2;   // keys + gather
   NG_CUDA(c, cudaGetLastError());
   // 8 passes of 8 bits: the result returns to (ka, va)
