@@ -1,0 +1,125 @@
+"""GPU parity at the benchmark's full sizes and walk configuration.
+
+The clustered workloads of N = 2^21 (D = 2, Newtonian, PM 128^3) and
+N = 2^24 (D = 4, Yukawa, PM 256^3) are built and walked by the CUDA path
+with the leaf size and group cell the autotuner picks on them (leaf 32,
+group cell 256). Outputs the oracle produces for every body are compared in
+full: Morton+type keys, the sort permutation and the canonical octree
+(bit-exact), the FP64 monopoles (summation-order bound). Outputs the oracle
+computes one target at a time are compared on a seeded sample of bodies:
+per-particle interaction counts on the leaf-8 tree the benchmark counts its
+unit of work on (bit-exact), and short-range forces (99th percentile of the
+error against the FP64 direct sum no worse than 1.1x the oracle walk's on
+the same tree). The long-range PM force is compared at 2^21 for every body
+(the oracle's FP64 FFT at 256^3 x 4 species would dominate the suite).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from common import device_arrays, ng_params, oracle_params
+from metrics import rel_err
+from paper_1502_07442_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+WALK = dict(leaf_size=32, group_cell=256)
+REF_LEAF = 8
+CASES = ["clustered2m_d2_newton", "clustered16m_d4_yukawa"]
+
+
+@pytest.fixture(scope="module")
+def ng():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1502_07442_gb300 import binding, build
+    build.build()
+    return binding
+
+
+@pytest.fixture(scope="module", params=CASES)
+def case(request):
+    return request.param, inputs.workload(request.param)
+
+
+def test_fullsize_keys_permutation_tree(ng, case):
+    import torch
+    name, w = case
+    prm = dict(w["params"], **WALK)
+    pos, typ, mass = device_arrays(w)
+    n = typ.numel()
+    sim = ng.Simulation(ng_params(prm))
+    keys = torch.empty(n, dtype=torch.int64, device=pos.device)
+    perm = torch.empty(n, dtype=torch.int32, device=pos.device)
+    ng.ng_build_tree(sim.ctx, pos, typ, mass, keys, perm)
+    torch.cuda.synchronize()
+    k_ref = oracle.keys(w["pos"], w["type"])
+    p_ref = oracle.sort_perm(k_ref)
+    assert np.array_equal(perm.cpu().numpy().view(np.uint32), p_ref)
+    assert np.array_equal(keys.cpu().numpy().view(np.uint64), k_ref[p_ref])
+    del keys, perm
+    T = ng.ng_tree_export(sim.ctx, prm["D"])
+    sim.close()
+    R = oracle.tree(oracle_params(prm), w["pos"], w["type"], w["mass"])
+    for f in ("level", "prefix", "first", "count", "nchild", "child_first", "cnt"):
+        assert np.array_equal(T[f], R[f].astype(T[f].dtype)), f
+    np.testing.assert_allclose(T["mass"], R["mass"], rtol=1e-12, atol=0)
+    dcom = np.abs(T["com"] - R["com"]).max(axis=2)
+    bound = 2.0 ** -53 * 4 * (R["cnt"].astype(np.float64) + 2)
+    assert np.all(dcom <= bound)
+
+
+def test_fullsize_sampled_counts_and_forces(ng, case):
+    import torch
+    name, w = case
+    n = w["pos"].shape[1]
+    rng = np.random.Generator(np.random.PCG64(20260))
+    sample = np.sort(rng.choice(n, size=2000, replace=False))
+    pos, typ, mass = device_arrays(w)
+
+    # unit of work: per-particle counts on the reference tree, bit-exact
+    prm8 = dict(w["params"], leaf_size=REF_LEAF)
+    ref = ng.Simulation(ng_params(prm8))
+    ng.ng_build_tree(ref.ctx, pos, typ, mass)
+    counts = torch.empty(n, dtype=torch.int64, device=pos.device)
+    ng.ng_count_interactions(ref.ctx, counts)
+    got_counts = counts.cpu().numpy()[sample]
+    ref.close()
+    _, c_ref = oracle.tree_walk(oracle_params(prm8), w["pos"], w["type"], w["mass"], tgt=sample)
+    assert np.array_equal(got_counts, c_ref)
+
+    # short-range force of the benchmark's walk configuration
+    prm = dict(w["params"], **WALK)
+    sim = ng.Simulation(ng_params(prm))
+    ng.ng_build_tree(sim.ctx, pos, typ, mass)
+    acc = torch.empty((3, n), dtype=torch.float32, device=pos.device)
+    ng.ng_tree_force(sim.ctx, acc)
+    torch.cuda.synchronize()
+    got = acc.cpu().numpy()[:, sample].astype(np.float64)
+    sim.close()
+    op = oracle_params(prm)
+    direct = oracle.direct(op, w["pos"], w["type"], w["mass"], tgt=sample)
+    tree, _ = oracle.tree_walk(op, w["pos"], w["type"], w["mass"], tgt=sample)
+    e_gpu, _ = rel_err(got, direct)
+    e_cpu, _ = rel_err(tree, direct)
+    assert np.percentile(e_gpu, 99) <= 1.1 * np.percentile(e_cpu, 99), (
+        np.percentile(e_gpu, 99), np.percentile(e_cpu, 99))
+
+
+def test_fullsize_pm_2m(ng):
+    import torch
+    w = inputs.workload("clustered2m_d2_newton")
+    prm = dict(w["params"], **WALK)
+    pos, typ, mass = device_arrays(w)
+    sim = ng.Simulation(ng_params(prm))
+    ng.ng_build_tree(sim.ctx, pos, typ, mass)
+    acc = torch.empty((3, typ.numel()), dtype=torch.float32, device=pos.device)
+    ng.ng_pm_force(sim.ctx, acc)
+    torch.cuda.synchronize()
+    got = acc.cpu().numpy().astype(np.float64)
+    sim.close()
+    ref = oracle.pm(oracle_params(prm), w["pos"], w["type"], w["mass"])
+    rms = np.sqrt(np.mean(np.sum(ref ** 2, axis=0)))
+    err = np.linalg.norm(got - ref, axis=0) / rms
+    assert err.max() <= 2e-4, (err.max(), err.mean())
