@@ -44,6 +44,9 @@ class OrParams(ctypes.Structure):
         ("law", (ctypes.c_int32 * 6) * 6),
         ("ya", (ctypes.c_double * 6) * 6),
         ("yl", (ctypes.c_double * 6) * 6),
+        ("opening", ctypes.c_int32),
+        ("pad1", ctypes.c_int32),
+        ("alpha", ctypes.c_double),
     ]
 
 
@@ -83,6 +86,7 @@ def lib():
         L.or_direct_mag.argtypes = [P, i64, vp, vp, vp, i64, vp, vp, vp]
         L.or_tree_walk.argtypes = [P, i64, vp, vp, vp, i64, vp, vp, vp]
         L.or_tree_walk_timed.argtypes = [P, i64, vp, vp, vp, i64, vp, vp, vp, vp]
+        L.or_tree_walk_aold.argtypes = [P, i64, vp, vp, vp, vp, i64, vp, vp, vp]
         L.or_fft1d.argtypes = [i64, vp, vp, ctypes.c_int]
         L.or_fft3d.argtypes = [i64, vp, vp, ctypes.c_int]
         L.or_pm.argtypes = [P, i64, vp, vp, vp, vp]
@@ -104,9 +108,12 @@ def set_threads(n: int = 0) -> int:
 
 
 def make_params(D, G, *, box=1.0, eps, rs, rcut, theta=0.5, leaf_size=8, pm_mesh=0,
-                law=None, ya=None, yl=None) -> OrParams:
-    """Build the oracle's parameter block from plain numbers / nested lists."""
+                law=None, ya=None, yl=None, opening=0, alpha=0.005) -> OrParams:
+    """Build the oracle's parameter block from plain numbers / nested lists.
+    opening 0: geometric criterion (theta); 1: relative criterion (alpha, with
+    the previous acceleration magnitudes given to tree_walk)."""
     p = OrParams()
+    p.opening, p.alpha = int(opening), float(alpha)
     p.D, p.leaf_size, p.pm_mesh = int(D), int(leaf_size), int(pm_mesh)
     p.box, p.eps, p.rs, p.rcut, p.theta = float(box), float(eps), float(rs), float(rcut), float(theta)
     G = np.asarray(G, dtype=np.float64)
@@ -207,8 +214,10 @@ def direct_mag(p: OrParams, pos, typ, mass, tgt=None):
     return acc, mag
 
 
-def tree_walk(p: OrParams, pos, typ, mass, tgt=None):
-    """Per-particle tree walk; returns (acc [3][len(tgt)], counts [len(tgt)])."""
+def tree_walk(p: OrParams, pos, typ, mass, tgt=None, aold=None):
+    """Per-particle tree walk; returns (acc [3][len(tgt)], counts [len(tgt)]).
+    aold (float32 [n], original order): previous acceleration magnitudes for
+    the relative criterion (p.opening == 1); without it the walk is geometric."""
     pos = _soa(pos)
     typ = np.ascontiguousarray(typ, np.uint8)
     mass = np.ascontiguousarray(mass, np.float32)
@@ -216,8 +225,14 @@ def tree_walk(p: OrParams, pos, typ, mass, tgt=None):
     t = _targets(n, tgt)
     acc = np.zeros((3, t.size))
     cnt = np.zeros(t.size, np.int64)
-    lib().or_tree_walk(ctypes.byref(p), n, _p(pos), _p(typ), _p(mass), t.size, _p(t),
-                       _p(acc), _p(cnt))
+    if aold is None:
+        lib().or_tree_walk(ctypes.byref(p), n, _p(pos), _p(typ), _p(mass), t.size, _p(t),
+                           _p(acc), _p(cnt))
+    else:
+        a = np.ascontiguousarray(aold, np.float32)
+        assert a.shape == (n,)
+        lib().or_tree_walk_aold(ctypes.byref(p), n, _p(pos), _p(typ), _p(mass), _p(a), t.size,
+                                _p(t), _p(acc), _p(cnt))
     return acc, cnt
 
 

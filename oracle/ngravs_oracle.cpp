@@ -73,6 +73,9 @@ typedef struct {
   int32_t law[6][6];    /* 0 = Newtonian, 1 = Newtonian + Yukawa (C = 1) */
   double ya[6][6];      /* Yukawa strength alpha */
   double yl[6][6];      /* Yukawa range lambda */
+  int32_t opening;      /* 0 geometric (theta), 1 relative (alpha, previous |a|) */
+  int32_t pad1;
+  double alpha;         /* relative criterion tolerance */
 } or_params;
 
 enum { OR_NEWTON = 0, OR_YUKAWA = 1 };
@@ -445,14 +448,14 @@ static double wall_seconds() {
 #endif
 }
 
-void or_tree_walk_timed(const or_params* p, int64_t n, const double* pos,
-                        const uint8_t* type, const float* mass, int64_t ntgt,
-                        const int64_t* tgt, double* acc, int64_t* counts, double* times);
+static void tree_walk(const or_params* p, int64_t n, const double* pos, const uint8_t* type,
+                      const float* mass, const float* aold, int64_t ntgt, const int64_t* tgt,
+                      double* acc, int64_t* counts, double* times);
 
 void or_tree_walk(const or_params* p, int64_t n, const double* pos,
                   const uint8_t* type, const float* mass, int64_t ntgt,
                   const int64_t* tgt, double* acc, int64_t* counts) {
-  or_tree_walk_timed(p, n, pos, type, mass, ntgt, tgt, acc, counts, nullptr);
+  tree_walk(p, n, pos, type, mass, nullptr, ntgt, tgt, acc, counts, nullptr);
 }
 
 /* The same walk; times (optional, 2 doubles) receives the wall seconds of the
@@ -460,6 +463,27 @@ void or_tree_walk(const or_params* p, int64_t n, const double* pos,
 void or_tree_walk_timed(const or_params* p, int64_t n, const double* pos,
                         const uint8_t* type, const float* mass, int64_t ntgt,
                         const int64_t* tgt, double* acc, int64_t* counts, double* times) {
+  tree_walk(p, n, pos, type, mass, nullptr, ntgt, tgt, acc, counts, times);
+}
+
+/* The walk with the relative opening criterion when p->opening == 1:
+ * aold[i] is the magnitude of body i's previous acceleration (original
+ * order). Sec. 2.2: ngravs keeps GADGET-2's Newtonian relative criterion in
+ * its single vectorised walk. A node of side l, total mass M and all-species
+ * centre of mass at distance r is accepted iff the target lies outside the
+ * cube of side 1.2 l about the node centre and G_max M l^2 <= alpha |a_old|
+ * r^4, G_max the largest coupling (the Newtonian estimate bounds every
+ * species' term). Without aold the geometric criterion is used, as for the
+ * first force of a run. */
+void or_tree_walk_aold(const or_params* p, int64_t n, const double* pos, const uint8_t* type,
+                       const float* mass, const float* aold, int64_t ntgt, const int64_t* tgt,
+                       double* acc, int64_t* counts) {
+  tree_walk(p, n, pos, type, mass, aold, ntgt, tgt, acc, counts, nullptr);
+}
+
+static void tree_walk(const or_params* p, int64_t n, const double* pos, const uint8_t* type,
+                      const float* mass, const float* aold, int64_t ntgt, const int64_t* tgt,
+                      double* acc, int64_t* counts, double* times) {
   const double t0 = wall_seconds();
   std::vector<uint64_t> skeys;
   std::vector<uint32_t> perm;
@@ -475,9 +499,14 @@ void or_tree_walk_timed(const or_params* p, int64_t n, const double* pos,
   const double L = p->box;
   const int D = p->D;
   const double rc2 = p->rcut * p->rcut;
+  const bool relative = p->opening == 1 && aold != nullptr;
+  double gmax = 0.0;
+  for (int i = 0; i < D; ++i)
+    for (int j = 0; j < D; ++j) gmax = std::max(gmax, p->G[i][j]);
 #pragma omp parallel for schedule(dynamic, 16)
   for (int64_t q = 0; q < ntgt; ++q) {
     const int64_t i = tgt[q];
+    const double a_old = relative ? (double)aold[i] : 0.0;
     const int64_t si = rank[i];
     const int s = type[i];
     double x[3];
@@ -508,7 +537,19 @@ void or_tree_walk_timed(const or_params* p, int64_t n, const double* pos,
           const double v = min_image(T.comtot[k * 3 + e] - x[e], L);
           dd2 += v * v;
         }
-        if (side < p->theta * std::sqrt(dd2)) {
+        bool accept;
+        if (relative) {
+          const double lim = 0.6 * side;
+          bool near = true;
+          for (int e = 0; e < 3; ++e)
+            if (!(std::fabs(dc[e]) < lim)) near = false;
+          const double lhs = (gmax * T.mtot[k]) * (side * side);
+          const double rhs = (p->alpha * a_old) * (dd2 * dd2);
+          accept = !near && lhs <= rhs;
+        } else {
+          accept = side < p->theta * std::sqrt(dd2);
+        }
+        if (accept) {
           for (int t = 0; t < D; ++t) {
             const double M = T.mass[k * D + t];
             if (!(M > 0.0)) continue;
