@@ -50,6 +50,7 @@ enum {
 };
 
 enum { NG_NEWTON = 0, NG_YUKAWA = 1 };
+enum { NG_OPEN_GEOMETRIC = 0, NG_OPEN_RELATIVE = 1 };
 
 /*
  * Parameters of one simulation (Sec. 2, Eq. (map); Sec. 2.4.1).
@@ -67,6 +68,16 @@ enum { NG_NEWTON = 0, NG_YUKAWA = 1 };
  *  theta          opening angle: a node of side l is used as D monopoles when
  *                 l < theta * d (d from the target group to the node's centre
  *                 of mass); theta = 0 opens every node (direct summation).
+ *  opening        NG_OPEN_GEOMETRIC (theta) or NG_OPEN_RELATIVE: the Newtonian
+ *                 relative criterion GADGET-2 uses and ngravs keeps (Sec. 2.2):
+ *                 a node of side l, total mass M and centre of mass at
+ *                 distance r is used when the target lies outside the cube of
+ *                 side 1.2 l about the node centre and
+ *                 G_max M l^2 <= alpha |a_old| r^4, G_max = max G[i][j] and
+ *                 |a_old| the magnitude of the target's previous acceleration
+ *                 (see ng_set_acc_old). Until a context holds |a_old| for its
+ *                 bodies, the geometric criterion with theta is used.
+ *  alpha          relative criterion tolerance (> 0 when opening is relative).
  *  leaf_size      maximum bodies per tree leaf (1..64, 0 = 8).
  *  group_size     particles per walk group (32 or 64, 0 = 32).
  *  table_size     short-range table entries per law (0 = automatic).
@@ -90,6 +101,9 @@ typedef struct {
   double asmth;
   double rcut_over_rs;
   double theta;
+  int32_t opening;
+  int32_t reserved1;   /* must be 0 */
+  double alpha;
 } ng_params;
 
 typedef struct ng_ctx ng_ctx;
@@ -132,8 +146,21 @@ int ng_build_tree(ng_ctx* ctx, int64_t n, const double* pos, const uint8_t* type
 int ng_tree_force(ng_ctx* ctx, float* acc_out, uint64_t* interactions_out);
 
 /*
- * Per-particle walk interaction count (Sec. 2.2, geometric criterion with
- * angle theta per target particle, double precision decisions): the number
+ * Previous accelerations for the relative opening criterion (Sec. 2.2): the
+ * context keeps |a| of acc_old (device float[3][n], caller order; |a| formed
+ * in FP32 as sqrt((x*x + y*y) + z*z), each operation rounded on its own).
+ * With opening == NG_OPEN_RELATIVE every force evaluation of this context
+ * on n bodies then uses these magnitudes, and afterwards replaces them with
+ * the magnitudes of the acceleration it computed (the short-range part for
+ * ng_tree_force, the total for ng_step and batches), as GADGET-2 does from
+ * step to step. Served requests are independent and start without them.
+ * NG_EINVAL for a NULL pointer or n outside [1, 2^31).
+ */
+int ng_set_acc_old(ng_ctx* ctx, int64_t n, const float* acc_old);
+
+/*
+ * Per-particle walk interaction count (Sec. 2.2, the context's opening
+ * criterion per target particle, double precision decisions): the number
  * of (accepted node, species with mass > 0) terms plus bodies of opened
  * leaves, the target excluded, summed over all bodies. This is the
  * algorithm's unit of work for throughput reports; it evaluates no force.

@@ -37,10 +37,12 @@ class NgParams(ctypes.Structure):
         ("G", _M6d), ("law", _M6i), ("yuk_a", _M6d), ("yuk_l", _M6d),
         ("eps", ctypes.c_double), ("box", ctypes.c_double), ("asmth", ctypes.c_double),
         ("rcut_over_rs", ctypes.c_double), ("theta", ctypes.c_double),
+        ("opening", ctypes.c_int32), ("reserved1", ctypes.c_int32), ("alpha", ctypes.c_double),
     ]
 
 
 NG_REQ_FORCE, NG_REQ_STEPS = 0, 1
+NG_OPEN_GEOMETRIC, NG_OPEN_RELATIVE = 0, 1
 
 
 class NgRequest(ctypes.Structure):
@@ -85,6 +87,7 @@ def lib():
         L.ng_build_tree.argtypes = [vp, i64, vp, vp, vp, vp, vp]
         L.ng_tree_force.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_uint64)]
         L.ng_count_interactions.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_uint64)]
+        L.ng_set_acc_old.argtypes = [vp, i64, vp]
         L.ng_pm_force.argtypes = [vp, vp]
         L.ng_step.argtypes = [vp, i64, vp, vp, vp, vp, vp, i32, i32, d]
         L.ng_tree_export.argtypes = [vp, ctypes.POINTER(i64)] + [vp] * 9
@@ -122,7 +125,7 @@ def lib():
                   "ng_batch_step", "ng_batch_size", "ng_batch_walk_launches",
                   "ng_batch_launch_count", "ng_serve_create", "ng_serve_destroy",
                   "ng_serve_submit", "ng_serve_cancel", "ng_serve_poll", "ng_serve_pending",
-                  "ng_serve_wait", "ng_serve"):
+                  "ng_serve_wait", "ng_serve", "ng_set_acc_old"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -137,7 +140,7 @@ def exported_symbols():
             "ng_batch_launch_count", "ng_batch_last_error", "ng_serve_create",
             "ng_serve_destroy", "ng_serve_submit", "ng_serve_cancel", "ng_serve_poll",
             "ng_serve_pending", "ng_serve_wait", "ng_serve", "ng_serve_last_error",
-            "ng_serve_request_bytes", "ng_sort_keys_noalloc"]
+            "ng_serve_request_bytes", "ng_sort_keys_noalloc", "ng_set_acc_old"]
 
 
 def _check(ctx, code):
@@ -148,13 +151,14 @@ def _check(ctx, code):
 
 def make_params(D, G, *, eps, box=1.0, pm_mesh=0, asmth=1.25, rcut_over_rs=4.5, theta=0.5,
                 leaf_size=8, group_size=32, table_size=0, law=None, yuk_a=None, yuk_l=None,
-                group_cell=0):
+                group_cell=0, opening=0, alpha=0.0):
     p = NgParams()
     p.D, p.pm_mesh, p.leaf_size, p.group_size, p.table_size = (int(D), int(pm_mesh), int(leaf_size),
                                                                int(group_size), int(table_size))
     p.eps, p.box, p.asmth, p.rcut_over_rs, p.theta = (float(eps), float(box), float(asmth),
                                                       float(rcut_over_rs), float(theta))
     p.group_cell = int(group_cell)
+    p.opening, p.reserved1, p.alpha = int(opening), 0, float(alpha)
     G = np.asarray(G, np.float64)
     law = np.zeros((D, D), np.int32) if law is None else np.asarray(law, np.int32)
     ya = np.zeros((D, D)) if yuk_a is None else np.asarray(yuk_a, np.float64)
@@ -179,7 +183,8 @@ def params_from_workload(w: dict, **over) -> NgParams:
     return make_params(q["D"], q["G"], eps=q["eps"], box=box, pm_mesh=mesh, asmth=asmth,
                        rcut_over_rs=float(q["rcut"]) / rs, theta=q["theta"],
                        leaf_size=q.get("leaf_size", 8), law=q["law"], yuk_a=q["ya"], yuk_l=q["yl"],
-                       table_size=q.get("table_size", 0), group_cell=q.get("group_cell", 0))
+                       table_size=q.get("table_size", 0), group_cell=q.get("group_cell", 0),
+                       opening=q.get("opening", 0), alpha=q.get("alpha", 0.0))
 
 
 def _ptr(t):
@@ -210,6 +215,12 @@ def ng_build_tree(ctx, pos, typ, mass, keys_out=None, perm_out=None):
     n = typ.numel()
     _check(ctx, lib().ng_build_tree(ctx, n, _ptr(pos), _ptr(typ), _ptr(mass), _ptr(keys_out),
                                     _ptr(perm_out)))
+
+
+def ng_set_acc_old(ctx, acc_old):
+    """|a_old| for the relative criterion from a device float32[3][n] tensor."""
+    n = acc_old.shape[-1]
+    _check(ctx, lib().ng_set_acc_old(ctx, int(n), _ptr(acc_old)))
 
 
 def ng_tree_force(ctx, acc_out, count=False):

@@ -176,6 +176,42 @@ int launch_drift(ng_ctx* c, int64_t n, double* pos, const float* vel, double dt)
   return NG_OK;
 }
 
+// ------------------------------------------- relative opening criterion
+
+double coupling_max(const ng_ctx* c) {
+  double g = 0.0;
+  for (int i = 0; i < c->p.D; ++i)
+    for (int j = 0; j < c->p.D; ++j) g = std::max(g, c->p.G[i][j]);
+  return g > 0.0 ? g : 1.0;
+}
+
+bool relative_active(const ng_ctx* c) {
+  return c->p.opening == NG_OPEN_RELATIVE && c->n > 0 && c->aold_n == c->n;
+}
+
+// |a| per body in FP32, each operation rounded on its own: sqrt((x x + y y) + z z)
+__global__ void k_amag(int64_t n, const float* __restrict__ acc, float* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const float x = acc[i], y = acc[n + i], z = acc[2 * n + i];
+    out[i] = __fsqrt_rn(__fadd_rn(__fadd_rn(__fmul_rn(x, x), __fmul_rn(y, y)), __fmul_rn(z, z)));
+  }
+}
+
+static int set_aold(ng_ctx* c, int64_t n, const float* acc) {
+  NG_TRY(ensure(c, c->aold, (size_t)n * sizeof(float)));
+  k_amag<<<work_grid(c, n, 8), 256, 0, c->stream>>>(n, acc, as<float>(c->aold));
+  c->launches += 1;
+  NG_CUDA(c, cudaGetLastError());
+  c->aold_n = n;
+  return NG_OK;
+}
+
+int update_aold(ng_ctx* c, const float* acc) {
+  if (c->p.opening != NG_OPEN_RELATIVE) return NG_OK;
+  return set_aold(c, c->n, acc);
+}
+
 // ------------------------------------------------------------ pipeline
 
 static size_t node_bytes(int D) {
@@ -280,6 +316,7 @@ int force_stages(ng_ctx* c, float* acc) {
   } else {
     NG_TRY(launch_walk(c, acc, false, false));
   }
+  NG_TRY(update_aold(c, acc));
   return NG_OK;
 }
 
@@ -293,6 +330,11 @@ int validate(ng_ctx* c, const ng_params* p) {
   if (!(p->asmth > 0)) return fail(c, NG_EINVAL, "asmth must be > 0");
   if (!(p->rcut_over_rs > 0)) return fail(c, NG_EINVAL, "rcut_over_rs must be > 0");
   if (!(p->theta >= 0) || p->theta > 2.0) return fail(c, NG_EINVAL, "theta must be in [0, 2]");
+  if (p->opening != NG_OPEN_GEOMETRIC && p->opening != NG_OPEN_RELATIVE)
+    return fail(c, NG_EINVAL, "opening must be NG_OPEN_GEOMETRIC or NG_OPEN_RELATIVE");
+  if (p->reserved1 != 0) return fail(c, NG_EINVAL, "reserved1 must be 0");
+  if (p->opening == NG_OPEN_RELATIVE && (!(p->alpha > 0) || !std::isfinite(p->alpha)))
+    return fail(c, NG_EINVAL, "alpha must be > 0 for the relative criterion");
   if (p->pm_mesh != 0 && (!is_pow2(p->pm_mesh) || p->pm_mesh < 8 || p->pm_mesh > 1024))
     return fail(c, NG_EINVAL, "pm_mesh must be 0 or a power of two in [8, 1024]");
   if (p->leaf_size < 0 || p->leaf_size > 64) return fail(c, NG_EINVAL, "leaf_size must be 0..64");
@@ -405,7 +447,7 @@ int ng_destroy(ng_ctx* c) {
                     &c->tperm, &c->scan_part, &c->n_level, &c->n_prefix, &c->n_first,
                     &c->n_count, &c->n_child, &c->n_nchild, &c->n_tmp, &c->n_off, &c->n_m64,
                     &c->n_cnt, &c->n_geo, &c->n_com, &c->n_link, &c->n_mono, &c->groups, &c->gsize, &c->grank,
-                    &c->status, &c->counter, &c->acc_tmp, &c->rho, &c->rhok, &c->phi,
+                    &c->status, &c->counter, &c->acc_tmp, &c->aold, &c->rho, &c->rhok, &c->phi,
                     &c->walk_desc, &c->walk_prefix};
   for (DevBuf* b : bufs) release(*b);
   delete c;
@@ -442,6 +484,7 @@ int ng_tree_force(ng_ctx* c, float* acc_out, uint64_t* interactions_out) {
   if (interactions_out)
     NG_CUDA(c, cudaMemsetAsync(c->counter.p, 0, 8, c->stream));
   NG_TRY(launch_walk(c, acc_out, false, interactions_out != nullptr));
+  NG_TRY(update_aold(c, acc_out));
   if (interactions_out) {
     unsigned long long v = 0;
     NG_CUDA(c, cudaMemcpyAsync(&v, c->counter.p, 8, cudaMemcpyDeviceToHost, c->stream));
@@ -451,6 +494,13 @@ int ng_tree_force(ng_ctx* c, float* acc_out, uint64_t* interactions_out) {
     *interactions_out = v;
   }
   return NG_OK;
+}
+
+int ng_set_acc_old(ng_ctx* c, int64_t n, const float* acc_old) {
+  if (!c) return NG_EINVAL;
+  if (n < 1 || n >= (int64_t)1 << 31) return fail(c, NG_EINVAL, "n outside [1, 2^31)");
+  if (!acc_old) return fail(c, NG_EINVAL, "acc_old is NULL");
+  return set_aold(c, n, acc_old);
 }
 
 int ng_count_interactions(ng_ctx* c, int64_t* counts_out, uint64_t* total_out) {

@@ -216,7 +216,8 @@ int batch_step_once(ng_batch* b, const int64_t* n, double* const* pos, float* co
     ng_ctx* c = b->sims[i];
     cudaStream_t keep = c->stream;
     c->stream = origin;
-    const int r = launch_kick(c, n[i], vel[i], acc[i], 0.5 * dt);
+    int r = update_aold(c, acc[i]);
+    if (r == NG_OK) r = launch_kick(c, n[i], vel[i], acc[i], 0.5 * dt);
     c->stream = keep;
     if (r != NG_OK) return from_sim(b, i, r);
   }

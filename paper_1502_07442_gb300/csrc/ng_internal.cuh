@@ -74,6 +74,8 @@ struct __align__(16) WalkDesc {
   float out_scale;          // converts accumulated table-unit sums to acceleration
   int8_t tabid[kMaxD][kMaxD];
   float G[kMaxD][kMaxD];
+  const float* aold;        // relative criterion: |a_old| per caller index (nullptr: geometric)
+  float rel_scale;          // alpha L^2 / G_max (box units)
 };
 
 // Kernel parameters of one walk launch over one or more simulations that
@@ -130,6 +132,8 @@ struct ng_ctx {
   ng::DevBuf status;     // uint32[ST_COUNT]
   ng::DevBuf walk_desc, walk_prefix;
   ng::DevBuf counter;    // unsigned long long
+  ng::DevBuf aold;       // float[n] |previous acceleration| per body (caller order)
+  int64_t aold_n = -1;   // bodies aold holds (-1: none)
   ng::DevBuf acc_tmp;    // float[3][n] scratch for summing short + long
 
   // PM: cuFFT plans cached per (mesh, species count); a context reused for
@@ -199,6 +203,11 @@ int launch_walk_descs(ng_ctx* c, cudaStream_t stream, const WalkDesc* d_descs, i
                       uint32_t* d_prefix, uint32_t* d_work, unsigned long long* counter,
                       int64_t groups);
 int launch_count(ng_ctx* c, int64_t* counts);  // per-particle walk counts
+// Relative opening criterion: active when the context asks for it and holds
+// |a_old| for its current bodies; G_max of the law table; |acc| -> aold.
+bool relative_active(const ng_ctx* c);
+double coupling_max(const ng_ctx* c);
+int update_aold(ng_ctx* c, const float* acc);
 int pm_force(ng_ctx* c, float* acc, bool accumulate);
 extern std::mutex g_fft_plan_lock;   // see pm_setup
 int type_order(ng_ctx* c);

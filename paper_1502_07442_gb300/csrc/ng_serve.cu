@@ -130,6 +130,7 @@ int launch_request(ng_server* s, Slot& sl, Req& q) {
   }
   NG_CUDA(c, cudaMemsetAsync(c->status.p, 0, ST_COUNT * 4, sl.stream));
   c->n = n;
+  c->aold_n = -1;  // requests are independent: no previous acceleration
   // force at the input positions
   NG_TRY(sort_bodies(c, n, pos, type, mass));
   NG_TRY(tree_stages(c));

@@ -138,6 +138,16 @@ __global__ void __launch_bounds__(walk_warps(D) * 32, 1) k_walk(WalkLaunch L) {
       gy = 0.5f * (hi[1] - lo[1]) + pad;
       gz = 0.5f * (hi[2] - lo[2]) + pad;
     }
+    // relative criterion: the group accepts a node only when every body of it
+    // would, so it uses the smallest |a_old| of the group
+    const bool rel = DESC(aold) != nullptr;
+    float thr = 0.f;
+    if (rel) {
+      float a = active ? DESC(aold)[DESC(perm)[p]] : 3.0e38f;
+#pragma unroll
+      for (int o = 16; o; o >>= 1) a = fminf(a, __shfl_xor_sync(0xffffffffu, a, o));
+      thr = DESC(rel_scale) * a;
+    }
     // the body's own position is formed exactly as its record in the lists
     // (leaf centre offset + body offset, then scaled), so the self term has
     // d = 0 exactly and contributes nothing
@@ -285,7 +295,18 @@ __global__ void __launch_bounds__(walk_warps(D) * 32, 1) k_walk(WalkLaunch L) {
           const float ez = fmaxf(0.f, fabsf(dcz + cm.z) - gz);
           const float dd2 = ex * ex + ey * ey + ez * ez;
           const float side = 2.f * ge.w;
-          if (d2min > 0.f && side * side < DESC(theta2) * dd2) cls = 1;
+          bool take;
+          if (rel) {
+            // the box lies outside the cube of side 1.2 l about the node centre,
+            // and G_max M l^2 <= alpha |a_old| d^4 at the box's closest point
+            const float lim = 0.6f * side;
+            const bool outside = fabsf(dcx) - gx >= lim || fabsf(dcy) - gy >= lim ||
+                                 fabsf(dcz) - gz >= lim;
+            take = outside && cm.w * (side * side) <= thr * (dd2 * dd2);
+          } else {
+            take = d2min > 0.f && side * side < DESC(theta2) * dd2;
+          }
+          if (take) cls = 1;
           else cls = lk.y == 0 ? 2 : 3;
         }
       }
@@ -478,6 +499,8 @@ void fill_walk_desc(ng_ctx* c, float* acc, bool accumulate, WalkDesc* d) {
       d->tabid[i][j] = c->tabid[i][j];
       d->G[i][j] = (float)c->p.G[i][j];
     }
+  d->aold = relative_active(c) ? as<float>(c->aold) : nullptr;
+  d->rel_scale = (float)(c->p.alpha * c->L * c->L / coupling_max(c));
 }
 
 static int dispatch_walk(ng_ctx* c, cudaStream_t stream, const WalkLaunch& L, int64_t groups) {
@@ -558,6 +581,9 @@ struct CountArgs {
   int64_t* out;            // [caller index] or nullptr
   unsigned long long* total;
   uint32_t* status;
+  const float* aold;       // relative criterion: |a_old| per caller index
+  double alphaL2, gmax;    // alpha L^2 (box units), largest coupling
+  int relative;
 };
 
 __device__ __forceinline__ uint32_t compact3c(uint64_t v) {
@@ -599,11 +625,12 @@ __global__ void __launch_bounds__(128) k_count(CountArgs a) {
                            ((double)compact3c(pre >> 1) + 0.5) * side,
                            ((double)compact3c(pre) + 0.5) * side};
       const double half = __dmul_rn(0.5, side);
-      double g2 = 0.0;
+      double g2 = 0.0, dcs[3];
       bool inside = true;
 #pragma unroll
       for (int e = 0; e < 3; ++e) {
         const double dc = min_image_d(__dsub_rn(c[e], x[e]));
+        dcs[e] = dc;
         double gap = __dsub_rn(fabs(dc), half);
         gap = gap > 0.0 ? gap : 0.0;
         g2 = __dadd_rn(g2, __dmul_rn(gap, gap));
@@ -629,7 +656,23 @@ __global__ void __launch_bounds__(128) k_count(CountArgs a) {
           const double v = min_image_d(__dsub_rn(com[e], x[e]));
           dd2 = __dadd_rn(dd2, __dmul_rn(v, v));
         }
-        if (side < __dmul_rn(a.theta, sqrt(dd2))) {
+        bool accept;
+        if (a.relative) {
+          // outside the cube of side 1.2 l about the centre, and
+          // G_max M l^2 <= alpha |a_old| r^4 (box units: alpha L^2)
+          const double lim = __dmul_rn(0.6, side);
+          bool near = true;
+#pragma unroll
+          for (int e = 0; e < 3; ++e)
+            if (!(fabs(dcs[e]) < lim)) near = false;
+          const double lhs = __dmul_rn(__dmul_rn(a.gmax, mt), __dmul_rn(side, side));
+          const double rhs = __dmul_rn(__dmul_rn(a.alphaL2, (double)a.aold[a.perm[k]]),
+                                       __dmul_rn(dd2, dd2));
+          accept = !near && lhs <= rhs;
+        } else {
+          accept = side < __dmul_rn(a.theta, sqrt(dd2));
+        }
+        if (accept) {
           cnt += nspec;
           continue;
         }
@@ -670,6 +713,10 @@ int launch_count(ng_ctx* c, int64_t* counts) {
   const double rc = c->rcut / c->L;
   a.rcut2 = rc * rc;
   a.theta = c->p.theta;
+  a.relative = relative_active(c) ? 1 : 0;
+  a.aold = as<float>(c->aold);
+  a.alphaL2 = c->p.alpha * c->L * c->L;
+  a.gmax = coupling_max(c);
   a.out = counts;
   a.total = as<unsigned long long>(c->counter);
   a.status = as<uint32_t>(c->status);

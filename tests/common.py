@@ -12,7 +12,8 @@ def oracle_params(prm, **over):
     q.update(over)
     return oracle.make_params(q["D"], q["G"], box=q["box"], eps=q["eps"], rs=q["rs"],
                               rcut=q["rcut"], theta=q["theta"], leaf_size=q.get("leaf_size", 8),
-                              pm_mesh=q["pm_mesh"], law=q["law"], ya=q["ya"], yl=q["yl"])
+                              pm_mesh=q["pm_mesh"], law=q["law"], ya=q["ya"], yl=q["yl"],
+                              opening=q.get("opening", 0), alpha=q.get("alpha", 0.005))
 
 
 def ng_params(prm, **over):
