@@ -25,6 +25,7 @@ _lib = None
 
 NEWTON = 0
 YUKAWA = 1
+YUKAWA_PURE = 2
 
 
 class OrParams(ctypes.Structure):

@@ -16,7 +16,9 @@
  * in the design doc):
  *  - Sec. 2, Eq. (map): f_ij with i the passive and j the active species;
  *    G is stored [passive][active].
- *  - Eq. (yukawa) with C = 1: phi_ij(r) = -G_ij M (1 + a_ij exp(-r/l_ij)) / r.
+ *  - Eq. (yukawa) with C = 1: phi_ij(r) = -G_ij M (1 + a_ij exp(-r/l_ij)) / r;
+ *    and with C = 0 (Sec. 3.2, the pure Yukawa interaction of the transition
+ *    test): phi_ij(r) = -G_ij M a_ij exp(-r/l_ij) / r.
  *  - Sec. 2.4.1: Gaussian split exp(-k^2 r_s^2) in k-space, erfc(r / 2 r_s)
  *    in real space; r_s = a_smth L / N_m (the printed "2 pi a_smth / L" is
  *    not a length and is read as garbled).
@@ -78,7 +80,7 @@ typedef struct {
   double alpha;         /* relative criterion tolerance */
 } or_params;
 
-enum { OR_NEWTON = 0, OR_YUKAWA = 1 };
+enum { OR_NEWTON = 0, OR_YUKAWA = 1, OR_YUKAWA_PURE = 2 };
 
 /* ------------------------------------------------------------------ laws */
 
@@ -105,11 +107,12 @@ static double exp_erfc(double x, double y) {
  * Fourier kernel 4 pi a exp(-(k^2 + mu^2) r_s^2) / (k^2 + mu^2) leaves the
  * real-space potential  -a S(r)/r  with
  *   S(r) = 1/2 [ e^{-mu r} erfc(u - mu r_s) + e^{mu r} erfc(u + mu r_s) ],
- * whose force factor is S - r S'.
+ * whose force factor is S - r S'. The pure Yukawa law (C = 0) has the Yukawa
+ * part alone.
  */
 double or_short_factor(int law, double a, double l, double rs, double rho) {
-  double T = newton_short(rho, rs);
-  if (law == OR_YUKAWA) {
+  double T = law == OR_YUKAWA_PURE ? 0.0 : newton_short(rho, rs);
+  if (law == OR_YUKAWA || law == OR_YUKAWA_PURE) {
     const double mu = 1.0 / l;
     const double u = rho / (2.0 * rs);
     const double em = std::exp(-mu * rho) * std::erfc(u - mu * rs);
@@ -124,17 +127,18 @@ double or_short_factor(int law, double a, double l, double rs, double rho) {
 
 /* Unsplit force factor of Eq. (yukawa): |F| r^2 / (G M m). */
 double or_full_factor(int law, double a, double l, double r) {
-  double F = 1.0;
-  if (law == OR_YUKAWA) F += a * (1.0 + r / l) * std::exp(-r / l);
+  double F = law == OR_YUKAWA_PURE ? 0.0 : 1.0;
+  if (law == OR_YUKAWA || law == OR_YUKAWA_PURE) F += a * (1.0 + r / l) * std::exp(-r / l);
   return F;
 }
 
 /* Long-range k-space kernel without the -4 pi G factor and the CIC window:
- * [1/k^2 + a exp(-mu^2 r_s^2)/(k^2 + mu^2)] exp(-k^2 r_s^2); 0 at k = 0. */
+ * [C/k^2 + a exp(-mu^2 r_s^2)/(k^2 + mu^2)] exp(-k^2 r_s^2), C = 0 for the
+ * pure Yukawa law, else 1; 0 at k = 0. */
 double or_long_kernel(int law, double a, double l, double rs, double k2) {
   if (k2 <= 0.0) return 0.0;
-  double K = 1.0 / k2;
-  if (law == OR_YUKAWA) {
+  double K = law == OR_YUKAWA_PURE ? 0.0 : 1.0 / k2;
+  if (law == OR_YUKAWA || law == OR_YUKAWA_PURE) {
     const double mu = 1.0 / l;
     K += a * std::exp(-mu * mu * rs * rs) / (k2 + mu * mu);
   }

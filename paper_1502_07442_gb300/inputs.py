@@ -55,6 +55,20 @@ def clustered(n: int, rng: np.random.Generator, nspheres: int = 512, a: float = 
     return np.ascontiguousarray(pos[:, perm])
 
 
+def source_shells(ntest: int, rng: np.random.Generator, rmin: float, rmax: float,
+                  box: float = 1.0) -> np.ndarray:
+    """One source at a uniform random place followed by ntest test positions
+    at separations log-uniform in [rmin, rmax] (number density falling as
+    1/r^3, so every logarithmic shell holds about as many) in isotropic
+    directions, wrapped into the box. Returns [3][ntest + 1]."""
+    src = rng.random(3) * box
+    r = np.exp(rng.uniform(np.log(rmin), np.log(rmax), ntest))
+    v = rng.standard_normal((ntest, 3))
+    v /= np.linalg.norm(v, axis=1)[:, None]
+    pos = np.mod(src[None, :] + r[:, None] * v, box)
+    return np.ascontiguousarray(np.concatenate([src[None, :], pos]).T)
+
+
 def species_blocks(n: int, D: int, rng: np.random.Generator) -> np.ndarray:
     """Species labels with n/D bodies of each species, in random order."""
     t = np.repeat(np.arange(D, dtype=np.uint8), -(-n // D))[:n]

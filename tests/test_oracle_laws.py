@@ -116,3 +116,51 @@ def test_long_kernel_is_filtered_greens_function():
         want = _long_accel(r, rs, lambda k: ref_n(k) + ref_y(k))
         assert got == pytest.approx(want, rel=1e-10)
     assert oracle.long_kernel(oracle.YUKAWA, a, l, rs, 0.0) == 0.0
+
+
+# --- the pure Yukawa law (C = 0 in Eq. (yukawa); Sec. 3.2 transition test)
+
+@pytest.mark.parametrize("a,l", [(1.0, 0.1), (1.0, 0.02), (-0.5, 0.05)])
+@pytest.mark.parametrize("r_over_rs", [0.1, 0.7, 1.5, 3.0, 4.4])
+def test_pure_yukawa_short_equals_full_minus_long(a, l, r_over_rs):
+    rs = 0.0195
+    r = r_over_rs * rs
+    mu = 1.0 / l
+    full_y = a * (1.0 + mu * r) * math.exp(-mu * r) / r ** 2
+    long_y = _long_accel(r, rs, _yukawa_phik_k(rs, a, l))
+    short_or = oracle.short_factor(oracle.YUKAWA_PURE, a, l, rs, r) / r ** 2
+    assert short_or == pytest.approx(full_y - long_y, rel=2e-8, abs=1e-9 * abs(full_y))
+
+
+def test_pure_yukawa_limits_and_derivative():
+    a, l, rs = 0.7, 0.05, 0.01
+    # no Newtonian part: the full law is -d/dr of -a e^{-r/l}/r
+    V = lambda r: -a * math.exp(-r / l) / r
+    for r in (0.004, 0.02, 0.1):
+        h = r * 1e-5
+        dV = (V(r + h) - V(r - h)) / (2 * h)
+        assert oracle.full_factor(oracle.YUKAWA_PURE, a, l, r) / r ** 2 == pytest.approx(dV, rel=1e-8)
+    # r -> 0: the short part carries the whole law, whose factor tends to a
+    assert oracle.short_factor(oracle.YUKAWA_PURE, a, l, rs, 1e-7) == pytest.approx(a, abs=1e-9)
+    # rs -> infinity: no long-range part
+    for r in (0.01, 0.05):
+        assert oracle.short_factor(oracle.YUKAWA_PURE, a, l, 1e6, r) == pytest.approx(
+            oracle.full_factor(oracle.YUKAWA_PURE, a, l, r), rel=1e-6)
+    # Newtonian + pure Yukawa = the C = 1 law, term by term
+    for r in (0.3 * rs, 2 * rs):
+        assert (oracle.short_factor(oracle.NEWTON, 0, 1, rs, r)
+                + oracle.short_factor(oracle.YUKAWA_PURE, a, l, rs, r)) == pytest.approx(
+            oracle.short_factor(oracle.YUKAWA, a, l, rs, r), rel=1e-14)
+
+
+def test_pure_yukawa_long_kernel_has_no_newtonian_part():
+    rs, a, l = 0.01, 0.8, 0.03
+    mu = 1.0 / l
+    for k2 in (1.0, 400.0, 1e4):
+        want = a * math.exp(-mu * mu * rs * rs) / (k2 + mu * mu) * math.exp(-k2 * rs * rs)
+        assert oracle.long_kernel(oracle.YUKAWA_PURE, a, l, rs, k2) == pytest.approx(want, rel=1e-14)
+    def phik_k(k):
+        return -4 * math.pi * k * oracle.long_kernel(oracle.YUKAWA_PURE, a, l, rs, k * k) if k > 0 else 0.0
+    ref = _yukawa_phik_k(rs, a, l)
+    for r in (0.5 * rs, 2 * rs, 5 * rs):
+        assert _long_accel(r, rs, phik_k) == pytest.approx(_long_accel(r, rs, ref), rel=1e-10)
