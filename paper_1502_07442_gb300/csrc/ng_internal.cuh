@@ -50,7 +50,7 @@ constexpr int kWalkMaxWarps = 32;
 // Warps per walk block by species count: as many as the per-warp lists and a
 // 64 KB law table leave room for in 227 KB of shared memory; the register
 // budget follows (65536 / threads).
-__host__ __device__ constexpr int walk_warps(int D) { return D <= 3 ? 32 : D == 4 ? 24 : D == 5 ? 20 : 16; }
+__host__ __device__ constexpr int walk_warps(int D) { return D <= 3 ? 24 : D == 4 ? 24 : D == 5 ? 20 : 16; }
 
 // Per-simulation inputs of the walk (device memory, one per simulation).
 struct __align__(16) WalkDesc {

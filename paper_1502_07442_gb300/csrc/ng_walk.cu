@@ -31,7 +31,11 @@ namespace ng {
 template <int D>
 struct __align__(16) WarpSmem {
   WalkDesc desc;              // batched launches: the current item's simulation
-  float4 list[D][kListCap];   // records per active species, table units
+  // records per active species, table units, one float array per component
+  // (x[kListCap], y[kListCap], z[kListCap], m[kListCap]): consecutive records
+  // of one component are one 8- or 16-byte load, so the inner loop forms
+  // (record j, record j + 1) pairs for the packed FP32x2 instructions
+  float4 list[D][kListCap];
   float4 leafc[32];           // opened leaves: centre offset from the origin (box units)
   int2 leafb[32];             // opened leaves: first body, body count
   int leafo[32];              // opened leaves: exclusive prefix of body counts
@@ -51,6 +55,16 @@ __device__ __forceinline__ bool near_box(float px, float py, float pz, float gx,
   const float ex = fmaxf(0.f, fabsf(px) - gx), ey = fmaxf(0.f, fabsf(py) - gy),
               ez = fmaxf(0.f, fabsf(pz) - gz);
   return fmaf(ex, ex, fmaf(ey, ey, ez * ez)) < r2;
+}
+
+// Append one record at `slot` of a component-major list.
+__device__ __forceinline__ void put_rec(float4* list, int slot, float x, float y, float z,
+                                        float m) {
+  float* c = reinterpret_cast<float*>(list);
+  c[slot] = x;
+  c[kListCap + slot] = y;
+  c[2 * kListCap + slot] = z;
+  c[3 * kListCap + slot] = m;
 }
 
 // 8-byte shared-memory load from a 32-bit shared address
@@ -187,26 +201,47 @@ __global__ void __launch_bounds__(walk_warps(D) * 32, 1) k_walk(WalkLaunch L) {
           const uint32_t tb =
               (uint32_t)__cvta_generic_to_shared(tab + (int)DESC(tabid[s][t]) * L.tab_entries) -
               ((uint32_t)kMagicBits << 3);
-          const float4* __restrict__ list = ws->list[t];
-          float sx = 0.f, sy = 0.f, sz = 0.f;
+          float* lt4 = reinterpret_cast<float*>(ws->list[t]);
+          // pad to a multiple of 4 with massless records (zero force)
+          const int cnt4 = (cnt + 3) & ~3;
+          if (lane < cnt4 - cnt) put_rec(ws->list[t], cnt + lane, 0.f, 0.f, 0.f, 0.f);
           __syncwarp();
-#pragma unroll 4
-          for (int j = 0; j < cnt; ++j) {
-            const float4 r = list[j];
-            const float dx = r.x - xr, dy = r.y - yr, dz = r.z - zr;
-            const float qq = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
-            const float inv = rsqrtf(qq);
-            const float fi = fmaf(qq, inv, kMagic);
-            const int bits = min(__float_as_int(fi), clampbits);
-            const float rho = qq * inv;
-            const float2 e = lds_f2(tb + ((uint32_t)bits << 3));
-            const float gg = fmaf(rho, e.y, e.x);
-            const float inv2 = inv * inv;
-            const float f = (r.w * gg) * (inv2 * inv);
-            sx = fmaf(f, dx, sx);
-            sy = fmaf(f, dy, sy);
-            sz = fmaf(f, dz, sz);
+          // (record j, record j + 1) in the two halves of packed FP32x2
+          // operations; each half rounds exactly as the scalar operation
+          const float2 nx = make_float2(-xr, -xr), ny = make_float2(-yr, -yr),
+                       nz = make_float2(-zr, -zr), e2 = make_float2(eps2, eps2),
+                       mg = make_float2(kMagic, kMagic);
+          float2 sx2 = make_float2(0.f, 0.f), sy2 = sx2, sz2 = sx2;
+          auto pair = [&](float2 rx, float2 ry, float2 rz, float2 rm) {
+            const float2 dx = __fadd2_rn(rx, nx), dy = __fadd2_rn(ry, ny), dz = __fadd2_rn(rz, nz);
+            const float2 qq = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __ffma2_rn(dz, dz, e2)));
+            const float2 inv = make_float2(rsqrtf(qq.x), rsqrtf(qq.y));
+            const float2 fi = __ffma2_rn(qq, inv, mg);
+            const int b0 = min(__float_as_int(fi.x), clampbits);
+            const int b1 = min(__float_as_int(fi.y), clampbits);
+            const float2 rho = __fmul2_rn(qq, inv);
+            const float2 t0 = lds_f2(tb + ((uint32_t)b0 << 3));
+            const float2 t1 = lds_f2(tb + ((uint32_t)b1 << 3));
+            const float2 gg = make_float2(fmaf(rho.x, t0.y, t0.x), fmaf(rho.y, t1.y, t1.x));
+            const float2 inv2 = __fmul2_rn(inv, inv);
+            const float2 f = __fmul2_rn(__fmul2_rn(rm, gg), __fmul2_rn(inv2, inv));
+            sx2 = __ffma2_rn(f, dx, sx2);
+            sy2 = __ffma2_rn(f, dy, sy2);
+            sz2 = __ffma2_rn(f, dz, sz2);
+          };
+          // four records of each component per 16-byte load
+#pragma unroll 1
+          for (int j = 0; j < cnt4; j += 4) {
+            const float4 X = *reinterpret_cast<const float4*>(lt4 + j);
+            const float4 Y = *reinterpret_cast<const float4*>(lt4 + kListCap + j);
+            const float4 Z = *reinterpret_cast<const float4*>(lt4 + 2 * kListCap + j);
+            const float4 M = *reinterpret_cast<const float4*>(lt4 + 3 * kListCap + j);
+            pair(make_float2(X.x, X.y), make_float2(Y.x, Y.y), make_float2(Z.x, Z.y),
+                 make_float2(M.x, M.y));
+            pair(make_float2(X.z, X.w), make_float2(Y.z, Y.w), make_float2(Z.z, Z.w),
+                 make_float2(M.z, M.w));
           }
+          const float sx = sx2.x + sx2.y, sy = sy2.x + sy2.y, sz = sz2.x + sz2.y;
           __syncwarp();
           const float G = DESC(G[s][t]);
           ax = fmaf(G, sx, ax);
@@ -242,7 +277,7 @@ __global__ void __launch_bounds__(walk_warps(D) * 32, 1) k_walk(WalkLaunch L) {
 #pragma unroll
         for (int t = 0; t < D; ++t) {
           const uint32_t m = __ballot_sync(0xffffffffu, bt == t);
-          if (bt == t) ws->list[t][lc[t] + __popc(m & lt)] = rec;
+          if (bt == t) put_rec(ws->list[t], lc[t] + __popc(m & lt), rec.x, rec.y, rec.z, rec.w);
           lc[t] += __popc(m);
         }
         qdone += 32;
@@ -319,9 +354,7 @@ __global__ void __launch_bounds__(walk_warps(D) * 32, 1) k_walk(WalkLaunch L) {
           const float px = dcx + mo.x, py = dcy + mo.y, pz = dcz + mo.z;
           const bool has = mo.w > 0.f && near_box(px, py, pz, gx, gy, gz, rc2_keep);
           const uint32_t b = __ballot_sync(0xffffffffu, has);
-          if (has)
-            ws->list[t][lc[t] + __popc(b & lt)] =
-                make_float4(px * s_tab, py * s_tab, pz * s_tab, mo.w);
+          if (has) put_rec(ws->list[t], lc[t] + __popc(b & lt), px * s_tab, py * s_tab, pz * s_tab, mo.w);
           lc[t] += __popc(b);
         }
       }
