@@ -11,6 +11,7 @@ with gcc and marshals numpy arrays through ctypes.
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 import subprocess
 import threading
@@ -287,6 +288,38 @@ def force(p: OrParams, pos, typ, mass):
     acc = np.zeros((3, n))
     lib().or_force(ctypes.byref(p), n, _p(pos), _p(typ), _p(mass), _p(acc))
     return acc
+
+
+def law_amax(p: OrParams, box=None):
+    """A_max of Sec. 2.1.1 (the constant of Eq. (our_timestep)): the largest
+    G_ij |f_ij(r)| r^2 / M over the species pairs, the supremum over r taken
+    on a dense logarithmic grid of the full (unsplit) law from 1e-9 L to
+    1e3 L (the laws are defined for every separation)."""
+    L = p.box if box is None else box
+    r = np.geomspace(1e-9 * L, 1e3 * L, 200001)
+    A = 0.0
+    for i in range(p.D):
+        for j in range(p.D):
+            f = np.array([abs(full_factor(p.law[i][j], p.ya[i][j], p.yl[i][j], x)) for x in r[::100]])
+            k = int(np.argmax(f))
+            lo, hi = max(0, 100 * k - 100), min(r.size, 100 * k + 101)
+            fine = max(abs(full_factor(p.law[i][j], p.ya[i][j], p.yl[i][j], x)) for x in r[lo:hi])
+            A = max(A, abs(p.G[i][j]) * max(f.max(), fine))
+    return A
+
+
+def timestep(p: OrParams, acc, eta, dt_max):
+    """Synchronous step: the smallest per-particle step of Eq. (our_timestep),
+    dt_i = min(dt_max, sqrt(2 eta eps / (A_max |a_i|))), with |a_i| formed in
+    float32 as sqrt((x x + y y) + z z). Returns (dt, max |a|)."""
+    a = np.ascontiguousarray(acc, np.float32)
+    mag = np.sqrt((a[0] * a[0] + a[1] * a[1]) + a[2] * a[2]).astype(np.float32)
+    A = law_amax(p)
+    steps = [dt_max]
+    for m in mag:
+        if m > 0 and A > 0:
+            steps.append(min(dt_max, math.sqrt(2.0 * eta * p.eps / (A * float(m)))))
+    return min(steps), float(mag.max())
 
 
 def kdk(p: OrParams, pos, vel, typ, mass, nsteps, dt):
