@@ -49,14 +49,18 @@ enum {
   NG_ESTATE = -6     /* call out of order (e.g. force before build) */
 };
 
-enum { NG_NEWTON = 0, NG_YUKAWA = 1 };
+enum { NG_NEWTON = 0, NG_YUKAWA = 1, NG_YUKAWA_PURE = 2 };
 enum { NG_OPEN_GEOMETRIC = 0, NG_OPEN_RELATIVE = 1 };
 
 /*
  * Parameters of one simulation (Sec. 2, Eq. (map); Sec. 2.4.1).
  *  G[i][j]        coupling for passive species i and active species j.
  *  law[i][j]      NG_NEWTON, or NG_YUKAWA for Eq. (yukawa) with C = 1:
- *                 phi_ij(r) = -G_ij M (1 + yuk_a[i][j] exp(-r / yuk_l[i][j])) / r.
+ *                 phi_ij(r) = -G_ij M (1 + yuk_a[i][j] exp(-r / yuk_l[i][j])) / r,
+ *                 or NG_YUKAWA_PURE for C = 0 (the pure Yukawa interaction of
+ *                 Sec. 3.2): phi_ij(r) = -G_ij M yuk_a[i][j] exp(-r / yuk_l[i][j]) / r.
+ *                 Both Yukawa kinds need yuk_l > 0; their long-range k-space
+ *                 part carries the factor exp(-r_s^2 / yuk_l^2) of Sec. 3.2.
  *  eps            Plummer softening length (> 0): the radial law is
  *                 evaluated at rho = sqrt(r^2 + eps^2).
  *  box            periodic box side L.
@@ -157,6 +161,20 @@ int ng_tree_force(ng_ctx* ctx, float* acc_out, uint64_t* interactions_out);
  * NG_EINVAL for a NULL pointer or n outside [1, 2^31).
  */
 int ng_set_acc_old(ng_ctx* ctx, int64_t n, const float* acc_old);
+
+/*
+ * Synchronous time step of Sec. 2.1.1, Eq. (our_timestep):
+ *   dt = min(dt_max, sqrt(2 eta eps / (A_max |a|_max))),
+ * the smallest of the per-particle steps, with |a|_max the largest |a| of acc
+ * (device float[3][n]; |a| in FP32 as sqrt((x*x + y*y) + z*z)) and A_max the
+ * bound |f_ij(r)| r^2 <= A_max M over the context's laws: G_ij for Newtonian
+ * pairs, G_ij max(1, |1 + yuk_a|) for NG_YUKAWA, G_ij |yuk_a| for
+ * NG_YUKAWA_PURE (maximum over i, j < D). dt_max > 0 and eta > 0; dt = dt_max
+ * when every acceleration is zero. Writes the host double *dt_out and the
+ * optional *amax_out (host, |a|_max). Synchronises the stream.
+ */
+int ng_timestep(ng_ctx* ctx, int64_t n, const float* acc, double eta, double dt_max,
+                double* dt_out, float* amax_out);
 
 /*
  * Per-particle walk interaction count (Sec. 2.2, the context's opening

@@ -21,7 +21,7 @@ from . import build as _build
 
 NG_MAX_SPECIES = 6
 NG_OK, NG_EINVAL, NG_ENOMEM, NG_ECUDA, NG_ETIMEOUT, NG_EBUSY, NG_ESTATE = 0, -1, -2, -3, -4, -5, -6
-NG_NEWTON, NG_YUKAWA = 0, 1
+NG_NEWTON, NG_YUKAWA, NG_YUKAWA_PURE = 0, 1, 2
 
 _M6d = (ctypes.c_double * NG_MAX_SPECIES) * NG_MAX_SPECIES
 _M6i = (ctypes.c_int32 * NG_MAX_SPECIES) * NG_MAX_SPECIES
@@ -88,6 +88,7 @@ def lib():
         L.ng_tree_force.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_uint64)]
         L.ng_count_interactions.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_uint64)]
         L.ng_set_acc_old.argtypes = [vp, i64, vp]
+        L.ng_timestep.argtypes = [vp, i64, vp, d, d, ctypes.POINTER(d), ctypes.POINTER(ctypes.c_float)]
         L.ng_pm_force.argtypes = [vp, vp]
         L.ng_step.argtypes = [vp, i64, vp, vp, vp, vp, vp, i32, i32, d]
         L.ng_tree_export.argtypes = [vp, ctypes.POINTER(i64)] + [vp] * 9
@@ -125,7 +126,7 @@ def lib():
                   "ng_batch_step", "ng_batch_size", "ng_batch_walk_launches",
                   "ng_batch_launch_count", "ng_serve_create", "ng_serve_destroy",
                   "ng_serve_submit", "ng_serve_cancel", "ng_serve_poll", "ng_serve_pending",
-                  "ng_serve_wait", "ng_serve", "ng_set_acc_old"):
+                  "ng_serve_wait", "ng_serve", "ng_set_acc_old", "ng_timestep"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -140,7 +141,7 @@ def exported_symbols():
             "ng_batch_launch_count", "ng_batch_last_error", "ng_serve_create",
             "ng_serve_destroy", "ng_serve_submit", "ng_serve_cancel", "ng_serve_poll",
             "ng_serve_pending", "ng_serve_wait", "ng_serve", "ng_serve_last_error",
-            "ng_serve_request_bytes", "ng_sort_keys_noalloc", "ng_set_acc_old"]
+            "ng_serve_request_bytes", "ng_sort_keys_noalloc", "ng_set_acc_old", "ng_timestep"]
 
 
 def _check(ctx, code):
@@ -221,6 +222,14 @@ def ng_set_acc_old(ctx, acc_old):
     """|a_old| for the relative criterion from a device float32[3][n] tensor."""
     n = acc_old.shape[-1]
     _check(ctx, lib().ng_set_acc_old(ctx, int(n), _ptr(acc_old)))
+
+
+def ng_timestep(ctx, acc, eta, dt_max):
+    """Synchronous step of Eq. (our_timestep); returns (dt, |a|_max)."""
+    dt, amax = ctypes.c_double(0.0), ctypes.c_float(0.0)
+    _check(ctx, lib().ng_timestep(ctx, int(acc.shape[-1]), _ptr(acc), float(eta), float(dt_max),
+                                  ctypes.byref(dt), ctypes.byref(amax)))
+    return dt.value, amax.value
 
 
 def ng_tree_force(ctx, acc_out, count=False):

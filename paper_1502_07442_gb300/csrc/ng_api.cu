@@ -55,12 +55,13 @@ void release(DevBuf& b) {
 // Sec. 3.2 long-range kernel scaled by exp(-mu^2 r_s^2)): the remaining
 // real-space potential -a S(rho)/rho with
 //   S = [e^{-mu rho} erfc(v - mu r_s) + e^{mu rho} erfc(v + mu r_s)] / 2,
-// v = rho / 2 r_s, contributes a (S - rho dS/drho).
+// v = rho / 2 r_s, contributes a (S - rho dS/drho). The pure Yukawa law
+// (C = 0, Sec. 3.2) has that part alone.
 double short_law_factor(int law, double a, double l, double rs, double rho) {
   const double v = rho / (2.0 * rs);
   const double gauss = std::exp(-v * v);
-  double T = std::erfc(v) + (2.0 / std::sqrt(M_PI)) * v * gauss;
-  if (law == NG_YUKAWA) {
+  double T = law == NG_YUKAWA_PURE ? 0.0 : std::erfc(v) + (2.0 / std::sqrt(M_PI)) * v * gauss;
+  if (law == NG_YUKAWA || law == NG_YUKAWA_PURE) {
     const double mu = 1.0 / l;
     const double lo = std::exp(-mu * rho) * std::erfc(v - mu * rs);
     const double ec = std::erfc(v + mu * rs);
@@ -84,8 +85,8 @@ int build_tables(ng_ctx* c) {
   std::vector<Law> laws;
   for (int i = 0; i < D; ++i)
     for (int j = 0; j < D; ++j) {
-      Law w{p.law[i][j], p.law[i][j] == NG_YUKAWA ? p.yuk_a[i][j] : 0.0,
-            p.law[i][j] == NG_YUKAWA ? p.yuk_l[i][j] : 0.0};
+      const bool yk = p.law[i][j] == NG_YUKAWA || p.law[i][j] == NG_YUKAWA_PURE;
+      Law w{p.law[i][j], yk ? p.yuk_a[i][j] : 0.0, yk ? p.yuk_l[i][j] : 0.0};
       int id = -1;
       for (size_t u = 0; u < laws.size(); ++u)
         if (laws[u].kind == w.kind && laws[u].a == w.a && laws[u].l == w.l) id = (int)u;
@@ -346,9 +347,11 @@ int validate(ng_ctx* c, const ng_params* p) {
   for (int i = 0; i < p->D; ++i)
     for (int j = 0; j < p->D; ++j) {
       if (!std::isfinite(p->G[i][j])) return fail(c, NG_EINVAL, "G[%d][%d] not finite", i, j);
-      if (p->law[i][j] != NG_NEWTON && p->law[i][j] != NG_YUKAWA)
+      if (p->law[i][j] != NG_NEWTON && p->law[i][j] != NG_YUKAWA &&
+          p->law[i][j] != NG_YUKAWA_PURE)
         return fail(c, NG_EINVAL, "law[%d][%d]=%d unknown", i, j, p->law[i][j]);
-      if (p->law[i][j] == NG_YUKAWA && (!(p->yuk_l[i][j] > 0) || !std::isfinite(p->yuk_a[i][j])))
+      if (p->law[i][j] != NG_NEWTON &&
+          (!(p->yuk_l[i][j] > 0) || !std::isfinite(p->yuk_l[i][j]) || !std::isfinite(p->yuk_a[i][j])))
         return fail(c, NG_EINVAL, "Yukawa range yuk_l[%d][%d] must be > 0", i, j);
     }
   const double rs = p->pm_mesh > 0 ? p->asmth * p->box / p->pm_mesh : p->asmth * p->box;
@@ -493,6 +496,63 @@ int ng_tree_force(ng_ctx* c, float* acc_out, uint64_t* interactions_out) {
     NG_TRY(check_flags(c, st[ST_FLAGS]));
     *interactions_out = v;
   }
+  return NG_OK;
+}
+
+// Largest |a| (FP32, each operation rounded) over n bodies: non-negative
+// floats order like their bit patterns, so an unsigned maximum of the bits
+// is the maximum of the values.
+__global__ void k_amax(int64_t n, const float* __restrict__ acc, unsigned int* out) {
+  unsigned int m = 0u;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const float x = acc[i], y = acc[n + i], z = acc[2 * n + i];
+    const float a = __fsqrt_rn(__fadd_rn(__fadd_rn(__fmul_rn(x, x), __fmul_rn(y, y)), __fmul_rn(z, z)));
+    const unsigned int b = __float_as_uint(a);
+    m = a == a && b > m ? b : m;   // a NaN acceleration is reported through its own check
+  }
+  for (int o = 16; o; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0 && m) atomicMax(out, m);
+}
+
+// A_max of Eq. (our_timestep): sup over r of |f_ij(r)| r^2 / (G_ij M), times
+// G_ij, over all pairs of the context's laws.
+static double law_amax(const ng_params& p) {
+  double A = 0.0;
+  for (int i = 0; i < p.D; ++i)
+    for (int j = 0; j < p.D; ++j) {
+      // Yukawa factor a (1 + r/l) e^{-r/l} runs over (0, a]
+      double s = 1.0;
+      if (p.law[i][j] == NG_YUKAWA) s = std::max(1.0, std::fabs(1.0 + p.yuk_a[i][j]));
+      if (p.law[i][j] == NG_YUKAWA_PURE) s = std::fabs(p.yuk_a[i][j]);
+      A = std::max(A, std::fabs(p.G[i][j]) * s);
+    }
+  return A;
+}
+
+int ng_timestep(ng_ctx* c, int64_t n, const float* acc, double eta, double dt_max,
+                double* dt_out, float* amax_out) {
+  if (!c) return NG_EINVAL;
+  if (n < 1 || n >= (int64_t)1 << 31) return fail(c, NG_EINVAL, "n outside [1, 2^31)");
+  if (!acc || !dt_out) return fail(c, NG_EINVAL, "NULL pointer");
+  if (!(eta > 0) || !(dt_max > 0) || !std::isfinite(eta) || !std::isfinite(dt_max))
+    return fail(c, NG_EINVAL, "eta and dt_max must be > 0");
+  NG_TRY(ensure(c, c->counter, 8));
+  NG_CUDA(c, cudaMemsetAsync(c->counter.p, 0, 4, c->stream));
+  k_amax<<<work_grid(c, n, 8), 256, 0, c->stream>>>(n, acc, as<unsigned int>(c->counter));
+  c->launches += 1;
+  NG_CUDA(c, cudaGetLastError());
+  unsigned int bits = 0;
+  NG_CUDA(c, cudaMemcpyAsync(&bits, c->counter.p, 4, cudaMemcpyDeviceToHost, c->stream));
+  NG_CUDA(c, cudaStreamSynchronize(c->stream));
+  float amax = 0.f;
+  std::memcpy(&amax, &bits, 4);
+  const double A = law_amax(c->p);
+  double dt = dt_max;
+  if (amax > 0.f && A > 0.0)
+    dt = std::min(dt_max, std::sqrt(2.0 * eta * c->p.eps / (A * (double)amax)));
+  *dt_out = dt;
+  if (amax_out) *amax_out = amax;
   return NG_OK;
 }
 

@@ -7,8 +7,9 @@
 // D inverse transforms give phi_i, and each particle of passive species i
 // interpolates -grad phi_i (4-point differences at the 8 CIC corners).
 //
-// K_ij(k) = -4 pi G_ij [1/k^2 + a_ij e^{-mu^2 r_s^2}/(k^2 + mu^2)] e^{-k^2 r_s^2}
-//           / W(k)^2 / L^3,   W = prod_d sinc^2(pi n_d / N), K(0) = 0.
+// K_ij(k) = -4 pi G_ij [C_ij/k^2 + a_ij e^{-mu^2 r_s^2}/(k^2 + mu^2)] e^{-k^2 r_s^2}
+//           / W(k)^2 / L^3,   W = prod_d sinc^2(pi n_d / N), K(0) = 0,
+// with C_ij = 0 for the pure Yukawa law and 1 otherwise.
 // The 1/L^3 folds the cell volume of the density and the 1/N^3 of the
 // unnormalised inverse transform.
 #include <cmath>
@@ -23,6 +24,7 @@ struct PmLaw {
   float G[kMaxD][kMaxD];
   float yfac[kMaxD][kMaxD];   // a_ij exp(-mu^2 r_s^2), 0 for Newtonian pairs
   float mu2[kMaxD][kMaxD];
+  float cnew[kMaxD][kMaxD];   // C of Eq. (yukawa): 1, or 0 for the pure Yukawa law
 };
 
 __global__ void k_cic_deposit(int64_t n, const uint32_t* __restrict__ order,
@@ -87,13 +89,13 @@ __global__ void k_kspace(cufftComplex* __restrict__ mesh, int N, float kf, float
     const float sx = sinc_pi(nx, N), sy = sinc_pi(ny, N), sz = sinc_pi(nz, N);
     const float w = sx * sx * sy * sy * sz * sz;
     const float filt = expf(-k2 * rs2) / (w * w) * pref;
-    const float newton = 1.f / k2;
+    const float inv_k2 = 1.f / k2;
 #pragma unroll
     for (int i = 0; i < D; ++i) {
       float re = 0.f, im = 0.f;
 #pragma unroll
       for (int j = 0; j < D; ++j) {
-        float K = newton;
+        float K = law.cnew[i][j] * inv_k2;
         if (law.yfac[i][j] != 0.f) K += law.yfac[i][j] / (k2 + law.mu2[i][j]);
         K *= law.G[i][j] * filt;
         re = fmaf(K, in[j].x, re);
@@ -210,7 +212,8 @@ int pm_force(ng_ctx* c, float* acc, bool accumulate) {
   for (int i = 0; i < kMaxD; ++i)
     for (int j = 0; j < kMaxD; ++j) {
       law.G[i][j] = (float)c->p.G[i][j];
-      if (i < D && j < D && c->p.law[i][j] == NG_YUKAWA) {
+      law.cnew[i][j] = i < D && j < D && c->p.law[i][j] == NG_YUKAWA_PURE ? 0.f : 1.f;
+      if (i < D && j < D && (c->p.law[i][j] == NG_YUKAWA || c->p.law[i][j] == NG_YUKAWA_PURE)) {
         const double mu = 1.0 / c->p.yuk_l[i][j];
         law.mu2[i][j] = (float)(mu * mu);
         law.yfac[i][j] = (float)(c->p.yuk_a[i][j] * std::exp(-mu * mu * c->rs * c->rs));
