@@ -27,6 +27,7 @@ _lib = None
 NEWTON = 0
 YUKAWA = 1
 YUKAWA_PURE = 2
+MAHALO = 3
 
 
 class OrParams(ctypes.Structure):
@@ -49,6 +50,9 @@ class OrParams(ctypes.Structure):
         ("opening", ctypes.c_int32),
         ("pad1", ctypes.c_int32),
         ("alpha", ctypes.c_double),
+        ("pure_tree", ctypes.c_int32),
+        ("ignore_nperp", ctypes.c_int32),
+        ("beta", ctypes.c_double),
     ]
 
 
@@ -79,6 +83,8 @@ def lib():
         L.or_full_factor.restype = d
         L.or_long_kernel.argtypes = [ctypes.c_int, d, d, d, d]
         L.or_long_kernel.restype = d
+        L.or_mahalo_factor.argtypes = [d, d, d]
+        L.or_mahalo_factor.restype = d
         L.or_keys.argtypes = [i64, vp, vp, d, vp]
         L.or_sort_perm.argtypes = [i64, vp, vp]
         L.or_tree.argtypes = [P, i64, vp, vp, vp, i64] + [vp] * 9
@@ -110,12 +116,14 @@ def set_threads(n: int = 0) -> int:
 
 
 def make_params(D, G, *, box=1.0, eps, rs, rcut, theta=0.5, leaf_size=8, pm_mesh=0,
-                law=None, ya=None, yl=None, opening=0, alpha=0.005) -> OrParams:
+                law=None, ya=None, yl=None, opening=0, alpha=0.005, pure_tree=0,
+                ignore_nperp=0, beta=0.0) -> OrParams:
     """Build the oracle's parameter block from plain numbers / nested lists.
     opening 0: geometric criterion (theta); 1: relative criterion (alpha, with
     the previous acceleration magnitudes given to tree_walk)."""
     p = OrParams()
     p.opening, p.alpha = int(opening), float(alpha)
+    p.pure_tree, p.ignore_nperp, p.beta = int(pure_tree), int(ignore_nperp), float(beta)
     p.D, p.leaf_size, p.pm_mesh = int(D), int(leaf_size), int(pm_mesh)
     p.box, p.eps, p.rs, p.rcut, p.theta = float(box), float(eps), float(rs), float(rcut), float(theta)
     G = np.asarray(G, dtype=np.float64)
@@ -139,6 +147,11 @@ def _soa(pos):
 
 def short_factor(law, a, l, rs, rho):
     return lib().or_short_factor(int(law), float(a), float(l), float(rs), float(rho))
+
+
+def mahalo_factor(beta, scale, r):
+    """|F| r^2 / (G M m) of the Sec. 3.3 law with core scale `scale`."""
+    return lib().or_mahalo_factor(float(beta), float(scale), float(r))
 
 
 def full_factor(law, a, l, r):

@@ -42,6 +42,16 @@
  *    inverse FFTs, 4-point finite-difference gradient, CIC interpolation to
  *    passive particles; CIC window divided out twice; k = 0 mode zeroed.
  *  - Sec. 2.1.1: kick-drift-kick leapfrog at fixed dt.
+ *  - Sec. 3.3 accumulator ("Mahalo") laws, pure tree mode only: a species j
+ *    is cored when law[j][j] is the Mahalo law; a Mahalo pair (passive i,
+ *    active j) has phi = -(2 M m / (pi r)) atan(4 pi beta r / s) with the
+ *    core scale s = (j cored ? M / N_perp : 0) + (i cored ? m : 0), N_perp the
+ *    number of bodies of species j behind the monopole (1 for a body). This
+ *    is Eq. (bambam) for i = j cored and Eq. (01) for a point passive
+ *    species; for a cored passive and point active species it gives
+ *    atan(4 pi beta r / m), where the printed Eq. (10) also carries N_perp
+ *    (read as a misprint: the softening scale is the cored object's alone,
+ *    and only then is the monopole exact for N_perp coincident bodies).
  *
  * Parity notes: every routine is pinned by tests/test_oracle_*.py against a
  * route that does not go through this file (closed forms, numerical
@@ -78,9 +88,12 @@ typedef struct {
   int32_t opening;      /* 0 geometric (theta), 1 relative (alpha, previous |a|) */
   int32_t pad1;
   double alpha;         /* relative criterion tolerance */
+  int32_t pure_tree;    /* 1: no split, full laws truncated at rcut, no PM */
+  int32_t ignore_nperp; /* 1: Mahalo monopoles as single objects (N_perp := 1) */
+  double beta;          /* Mahalo scale beta (Sec. 3.3) */
 } or_params;
 
-enum { OR_NEWTON = 0, OR_YUKAWA = 1, OR_YUKAWA_PURE = 2 };
+enum { OR_NEWTON = 0, OR_YUKAWA = 1, OR_YUKAWA_PURE = 2, OR_MAHALO = 3 };
 
 /* ------------------------------------------------------------------ laws */
 
@@ -155,16 +168,38 @@ static double min_image(double d, double L) {
   return d - L * std::nearbyint(d / L);
 }
 
-/* Acceleration on a passive particle of species s from a point of active
- * mass M and species t at min-image separation d (source - target); mag
- * (optional) accumulates the magnitude of the term. */
-static void pair_accel(const or_params* p, int s, int t, double M,
+/* Mahalo force factor |F| r^2 / (G M m) of phi = -(2 M m/(pi r)) atan(r/a),
+ * a = s / (4 pi beta): (2/pi) [atan(x) - x / (1 + x^2)], x = r / a. */
+double or_mahalo_factor(double beta, double scale, double r) {
+  const double x = 4.0 * M_PI * beta * r / scale;
+  return (2.0 / M_PI) * (std::atan(x) - x / (1.0 + x * x));
+}
+
+/* Force factor of pair (s, t) at (softened) separation rho: the short-range
+ * part of the law, or in pure tree mode the whole law. nperp and mpass enter
+ * only the Mahalo law: bodies behind the monopole, passive mass. */
+static double pair_factor(const or_params* p, int s, int t, double M, double nperp,
+                          double mpass, double rho) {
+  const int law = p->law[s][t];
+  if (!p->pure_tree) return or_short_factor(law, p->ya[s][t], p->yl[s][t], p->rs, rho);
+  if (law != OR_MAHALO) return or_full_factor(law, p->ya[s][t], p->yl[s][t], rho);
+  const double np = p->ignore_nperp ? 1.0 : nperp;
+  const double scale = (p->law[t][t] == OR_MAHALO ? M / np : 0.0) +
+                       (p->law[s][s] == OR_MAHALO ? mpass : 0.0);
+  return or_mahalo_factor(p->beta, scale, rho);
+}
+
+/* Acceleration on a passive particle of species s and mass mpass from a point
+ * of active mass M and species t standing for nperp bodies, at min-image
+ * separation d (source - target); mag (optional) accumulates the magnitude
+ * of the term. */
+static void pair_accel(const or_params* p, int s, int t, double M, double nperp, double mpass,
                        const double d[3], double acc[3], double* mag = nullptr) {
   const double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
   const double q = r2 + p->eps * p->eps;
   if (!(q < p->rcut * p->rcut)) return;
   const double rho = std::sqrt(q);
-  const double T = or_short_factor(p->law[s][t], p->ya[s][t], p->yl[s][t], p->rs, rho);
+  const double T = pair_factor(p, s, t, M, nperp, mpass, rho);
   const double f = p->G[s][t] * M * T / (rho * rho * rho);
   acc[0] += f * d[0];
   acc[1] += f * d[1];
@@ -389,7 +424,7 @@ void or_direct_mag(const or_params* p, int64_t n, const double* pos,
       if (k == i) continue;
       double d[3];
       for (int c = 0; c < 3; ++c) d[c] = min_image(pos[c * n + k] - pos[c * n + i], L);
-      pair_accel(p, type[i], type[k], mass[k], d, a, &m);
+      pair_accel(p, type[i], type[k], mass[k], 1.0, mass[i], d, a, &m);
     }
     for (int c = 0; c < 3; ++c) acc[c * ntgt + q] = a[c];
     if (mag) mag[q] = m;
@@ -431,7 +466,7 @@ void or_direct_cells(const or_params* p, int64_t n, const double* pos,
             if (k == i) continue;
             double d[3];
             for (int c = 0; c < 3; ++c) d[c] = min_image(pos[c * n + k] - pos[c * n + i], L);
-            pair_accel(p, type[i], type[k], mass[k], d, a);
+            pair_accel(p, type[i], type[k], mass[k], 1.0, mass[i], d, a);
           }
         }
     for (int c = 0; c < 3; ++c) acc[c * ntgt + q] = a[c];
@@ -559,7 +594,7 @@ static void tree_walk(const or_params* p, int64_t n, const double* pos, const ui
             if (!(M > 0.0)) continue;
             double d[3];
             for (int e = 0; e < 3; ++e) d[e] = min_image(T.com[(k * D + t) * 3 + e] - x[e], L);
-            pair_accel(p, s, t, M, d, a);
+            pair_accel(p, s, t, M, (double)T.cnt[k * D + t], smass[si], d, a);
             ++cntq;
           }
           continue;
@@ -570,7 +605,7 @@ static void tree_walk(const or_params* p, int64_t n, const double* pos, const ui
           if (b == si) continue;
           double d[3];
           for (int e = 0; e < 3; ++e) d[e] = min_image(spos[e * n + b] - x[e], L);
-          pair_accel(p, s, stype[b], smass[b], d, a);
+          pair_accel(p, s, stype[b], smass[b], 1.0, smass[si], d, a);
           ++cntq;
         }
       } else {

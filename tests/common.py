@@ -13,7 +13,9 @@ def oracle_params(prm, **over):
     return oracle.make_params(q["D"], q["G"], box=q["box"], eps=q["eps"], rs=q["rs"],
                               rcut=q["rcut"], theta=q["theta"], leaf_size=q.get("leaf_size", 8),
                               pm_mesh=q["pm_mesh"], law=q["law"], ya=q["ya"], yl=q["yl"],
-                              opening=q.get("opening", 0), alpha=q.get("alpha", 0.005))
+                              opening=q.get("opening", 0), alpha=q.get("alpha", 0.005),
+                              pure_tree=q.get("pure_tree", 0), ignore_nperp=q.get("ignore_nperp", 0),
+                              beta=q.get("beta", 0.0))
 
 
 def ng_params(prm, **over):
