@@ -49,7 +49,7 @@ enum {
   NG_ESTATE = -6     /* call out of order (e.g. force before build) */
 };
 
-enum { NG_NEWTON = 0, NG_YUKAWA = 1, NG_YUKAWA_PURE = 2 };
+enum { NG_NEWTON = 0, NG_YUKAWA = 1, NG_YUKAWA_PURE = 2, NG_MAHALO = 3 };
 enum { NG_OPEN_GEOMETRIC = 0, NG_OPEN_RELATIVE = 1 };
 
 /*
@@ -61,6 +61,14 @@ enum { NG_OPEN_GEOMETRIC = 0, NG_OPEN_RELATIVE = 1 };
  *                 Sec. 3.2): phi_ij(r) = -G_ij M yuk_a[i][j] exp(-r / yuk_l[i][j]) / r.
  *                 Both Yukawa kinds need yuk_l > 0; their long-range k-space
  *                 part carries the factor exp(-r_s^2 / yuk_l^2) of Sec. 3.2.
+ *                 NG_MAHALO (pure tree mode only): the accumulator laws of
+ *                 Sec. 3.3, phi_ij(r) = -G_ij (2 M m / (pi r)) atan(4 pi beta r / s)
+ *                 with s = (j cored ? M / N_perp : 0) + (i cored ? m : 0), where
+ *                 species k is cored when law[k][k] == NG_MAHALO, M and N_perp
+ *                 are the active mass and body count behind a monopole (N_perp =
+ *                 1 for a body) and m the passive mass (Eqs. (bambam), (01);
+ *                 for a cored passive and point active species the scale is m
+ *                 alone). At least one of i, j must be cored.
  *  eps            Plummer softening length (> 0): the radial law is
  *                 evaluated at rho = sqrt(r^2 + eps^2).
  *  box            periodic box side L.
@@ -82,6 +90,12 @@ enum { NG_OPEN_GEOMETRIC = 0, NG_OPEN_RELATIVE = 1 };
  *                 (see ng_set_acc_old). Until a context holds |a_old| for its
  *                 bodies, the geometric criterion with theta is used.
  *  alpha          relative criterion tolerance (> 0 when opening is relative).
+ *  pure_tree      1: pure tree mode (needs pm_mesh == 0): no TreePM split, every
+ *                 law is evaluated whole, truncated at r_cut = rcut_over_rs *
+ *                 asmth * L (< L/2, minimum image), by a per-particle walk.
+ *  ignore_nperp   1: Mahalo monopoles are treated as single objects (N_perp = 1),
+ *                 the "without tracking" comparison of Sec. 3.3.
+ *  beta           Mahalo scale beta (> 0 when a Mahalo law is used).
  *  leaf_size      maximum bodies per tree leaf (1..64, 0 = 8).
  *  group_size     particles per walk group (32 or 64, 0 = 32).
  *  table_size     short-range table entries per law (0 = automatic).
@@ -108,6 +122,9 @@ typedef struct {
   int32_t opening;
   int32_t reserved1;   /* must be 0 */
   double alpha;
+  int32_t pure_tree;
+  int32_t ignore_nperp;
+  double beta;
 } ng_params;
 
 typedef struct ng_ctx ng_ctx;
@@ -244,8 +261,9 @@ int ng_type_order(ng_ctx* ctx, int64_t* type_offsets, uint32_t* order_out);
  */
 typedef struct ng_batch ng_batch;
 
-/* nsim >= 1 parameter blocks (validated as in ng_create); stream as in
- * ng_create. *out is released with ng_batch_destroy. */
+/* nsim >= 1 parameter blocks (validated as in ng_create; pure tree mode is
+ * not batched: NG_EINVAL); stream as in ng_create. *out is released with
+ * ng_batch_destroy. */
 int ng_batch_create(ng_batch** out, int nsim, const ng_params* params, void* stream);
 int ng_batch_destroy(ng_batch* b);
 

@@ -315,7 +315,7 @@ int force_stages(ng_ctx* c, float* acc) {
     NG_TRY(pm_force(c, acc, false));
     NG_TRY(launch_walk(c, acc, true, false));
   } else {
-    NG_TRY(launch_walk(c, acc, false, false));
+    NG_TRY(launch_tree_force(c, acc, false, false));
   }
   NG_TRY(update_aold(c, acc));
   return NG_OK;
@@ -334,6 +334,17 @@ int validate(ng_ctx* c, const ng_params* p) {
   if (p->opening != NG_OPEN_GEOMETRIC && p->opening != NG_OPEN_RELATIVE)
     return fail(c, NG_EINVAL, "opening must be NG_OPEN_GEOMETRIC or NG_OPEN_RELATIVE");
   if (p->reserved1 != 0) return fail(c, NG_EINVAL, "reserved1 must be 0");
+  if (p->pure_tree != 0 && p->pure_tree != 1) return fail(c, NG_EINVAL, "pure_tree must be 0 or 1");
+  if (p->ignore_nperp != 0 && p->ignore_nperp != 1)
+    return fail(c, NG_EINVAL, "ignore_nperp must be 0 or 1");
+  if (p->pure_tree && p->pm_mesh != 0) return fail(c, NG_EINVAL, "pure tree mode needs pm_mesh = 0");
+  if (p->pure_tree) {
+    bool mahalo = false;
+    for (int i = 0; i < p->D; ++i)
+      for (int j = 0; j < p->D; ++j) mahalo = mahalo || p->law[i][j] == NG_MAHALO;
+    if (mahalo && (!(p->beta > 0) || !std::isfinite(p->beta)))
+      return fail(c, NG_EINVAL, "beta must be > 0 for Mahalo laws");
+  }
   if (p->opening == NG_OPEN_RELATIVE && (!(p->alpha > 0) || !std::isfinite(p->alpha)))
     return fail(c, NG_EINVAL, "alpha must be > 0 for the relative criterion");
   if (p->pm_mesh != 0 && (!is_pow2(p->pm_mesh) || p->pm_mesh < 8 || p->pm_mesh > 1024))
@@ -348,8 +359,14 @@ int validate(ng_ctx* c, const ng_params* p) {
     for (int j = 0; j < p->D; ++j) {
       if (!std::isfinite(p->G[i][j])) return fail(c, NG_EINVAL, "G[%d][%d] not finite", i, j);
       if (p->law[i][j] != NG_NEWTON && p->law[i][j] != NG_YUKAWA &&
-          p->law[i][j] != NG_YUKAWA_PURE)
+          p->law[i][j] != NG_YUKAWA_PURE && p->law[i][j] != NG_MAHALO)
         return fail(c, NG_EINVAL, "law[%d][%d]=%d unknown", i, j, p->law[i][j]);
+      if (p->law[i][j] == NG_MAHALO) {
+        if (!p->pure_tree) return fail(c, NG_EINVAL, "Mahalo laws need pure tree mode");
+        if (p->law[i][i] != NG_MAHALO && p->law[j][j] != NG_MAHALO)
+          return fail(c, NG_EINVAL, "Mahalo pair (%d, %d) has no cored species", i, j);
+        continue;
+      }
       if (p->law[i][j] != NG_NEWTON &&
           (!(p->yuk_l[i][j] > 0) || !std::isfinite(p->yuk_l[i][j]) || !std::isfinite(p->yuk_a[i][j])))
         return fail(c, NG_EINVAL, "Yukawa range yuk_l[%d][%d] must be > 0", i, j);
@@ -486,7 +503,7 @@ int ng_tree_force(ng_ctx* c, float* acc_out, uint64_t* interactions_out) {
   if (!acc_out) return fail(c, NG_EINVAL, "acc_out is NULL");
   if (interactions_out)
     NG_CUDA(c, cudaMemsetAsync(c->counter.p, 0, 8, c->stream));
-  NG_TRY(launch_walk(c, acc_out, false, interactions_out != nullptr));
+  NG_TRY(launch_tree_force(c, acc_out, false, interactions_out != nullptr));
   NG_TRY(update_aold(c, acc_out));
   if (interactions_out) {
     unsigned long long v = 0;

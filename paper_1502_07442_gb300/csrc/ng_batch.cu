@@ -77,6 +77,8 @@ extern "C" {
 int ng_batch_create(ng_batch** out, int nsim, const ng_params* params, void* stream) {
   if (!out || nsim < 1 || !params) return NG_EINVAL;
   *out = nullptr;
+  for (int i = 0; i < nsim; ++i)
+    if (params[i].pure_tree) return NG_EINVAL;   // batches run the group walk only
   ng_batch* b = new (std::nothrow) ng_batch();
   if (!b) return NG_ENOMEM;
   b->stream = (cudaStream_t)stream;

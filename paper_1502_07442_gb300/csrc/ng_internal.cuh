@@ -203,6 +203,10 @@ int launch_walk_descs(ng_ctx* c, cudaStream_t stream, const WalkDesc* d_descs, i
                       uint32_t* d_prefix, uint32_t* d_work, unsigned long long* counter,
                       int64_t groups);
 int launch_count(ng_ctx* c, int64_t* counts);  // per-particle walk counts
+// Pure tree mode: per-particle walk with the full laws (incl. Mahalo).
+int launch_walk_exact(ng_ctx* c, float* acc, bool accumulate, bool count);
+// The tree force of a context: the group walk, or in pure tree mode the exact walk.
+int launch_tree_force(ng_ctx* c, float* acc, bool accumulate, bool count);
 // Relative opening criterion: active when the context asks for it and holds
 // |a_old| for its current bodies; G_max of the law table; |acc| -> aold.
 bool relative_active(const ng_ctx* c);
