@@ -85,6 +85,8 @@ def lib():
         L.or_long_kernel.restype = d
         L.or_mahalo_factor.argtypes = [d, d, d]
         L.or_mahalo_factor.restype = d
+        L.or_lattice_correction.argtypes = [ctypes.c_int, d, d, ctypes.c_void_p, ctypes.c_void_p]
+        L.or_lattice_correction.restype = None
         L.or_keys.argtypes = [i64, vp, vp, d, vp]
         L.or_sort_perm.argtypes = [i64, vp, vp]
         L.or_tree.argtypes = [P, i64, vp, vp, vp, i64] + [vp] * 9
@@ -147,6 +149,15 @@ def _soa(pos):
 
 def short_factor(law, a, l, rs, rho):
     return lib().or_short_factor(int(law), float(a), float(l), float(rs), float(rho))
+
+
+def lattice_correction(law, a, l_box, d):
+    """Lattice correction (all images but the nearest) of law (kind, a, l) at
+    offset d (source - target, box units, L = 1) per unit G M."""
+    dd = np.ascontiguousarray(d, np.float64)
+    out = np.zeros(3)
+    lib().or_lattice_correction(int(law), float(a), float(l_box), _p(dd), _p(out))
+    return out
 
 
 def mahalo_factor(beta, scale, r):

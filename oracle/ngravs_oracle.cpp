@@ -42,6 +42,13 @@
  *    inverse FFTs, 4-point finite-difference gradient, CIC interpolation to
  *    passive particles; CIC window divided out twice; k = 0 mode zeroed.
  *  - Sec. 2.1.1: kick-drift-kick leapfrog at fixed dt.
+ *  - Sec. 2.3 lattice corrections (pure tree mode 2): the force of a source
+ *    and all its periodic images is the nearest image's plus a correction
+ *    that is smooth inside the cube |d_i| <= L/2; it is tabulated once per
+ *    law on a grid over [0, L/2]^3 (Ewald summation for the Newtonian part,
+ *    a plain image sum for the exponentially decaying Yukawa part) and
+ *    interpolated trilinearly, with the sign of each component following its
+ *    own axis. Softening applies to the nearest image only.
  *  - Sec. 3.3 accumulator ("Mahalo") laws, pure tree mode only: a species j
  *    is cored when law[j][j] is the Mahalo law; a Mahalo pair (passive i,
  *    active j) has phi = -(2 M m / (pi r)) atan(4 pi beta r / s) with the
@@ -62,6 +69,7 @@
 #include <cstdint>
 #include <cstring>
 #include <algorithm>
+#include <deque>
 #include <numeric>
 #include <vector>
 #ifdef _OPENMP
@@ -88,7 +96,9 @@ typedef struct {
   int32_t opening;      /* 0 geometric (theta), 1 relative (alpha, previous |a|) */
   int32_t pad1;
   double alpha;         /* relative criterion tolerance */
-  int32_t pure_tree;    /* 1: no split, full laws truncated at rcut, no PM */
+  int32_t pure_tree;    /* 1: no split, full laws truncated at rcut, no PM;
+                           2: no split, every image: nearest image plus the
+                           tabulated lattice correction, no cut-off, no PM */
   int32_t ignore_nperp; /* 1: Mahalo monopoles as single objects (N_perp := 1) */
   double beta;          /* Mahalo scale beta (Sec. 3.3) */
 } or_params;
@@ -168,6 +178,137 @@ static double min_image(double d, double L) {
   return d - L * std::nearbyint(d / L);
 }
 
+/* ------------------------------------------------- lattice corrections */
+
+enum { kEwaldGrid = 64 };   /* grid intervals per axis over [0, L/2] */
+
+/* Periodic acceleration toward a unit source and all its images at offset d
+ * (source - target, box units, L = 1) minus the nearest image's d/|d|^3:
+ * Ewald summation with splitting alpha = 2, real-space images |n_i| <= 3
+ * (the first left out is >= 3.1 L away: erfc(6.2) ~ 1e-18), reciprocal
+ * vectors |m_i| <= 5 (the first left out has exp(-k^2/4 alpha^2) ~ 1e-39). */
+static void ewald_newton_correction(const double d[3], double out[3]) {
+  const double alpha = 2.0;
+  double a[3] = {0, 0, 0};
+  for (int nx = -3; nx <= 3; ++nx)
+    for (int ny = -3; ny <= 3; ++ny)
+      for (int nz = -3; nz <= 3; ++nz) {
+        const double v[3] = {d[0] + nx, d[1] + ny, d[2] + nz};
+        const double r = std::sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+        if (r == 0.0) continue;
+        const double f = (std::erfc(alpha * r) +
+                          2.0 * alpha * r / std::sqrt(M_PI) * std::exp(-alpha * alpha * r * r)) /
+                         (r * r * r);
+        for (int e = 0; e < 3; ++e) a[e] += f * v[e];
+      }
+  for (int mx = -5; mx <= 5; ++mx)
+    for (int my = -5; my <= 5; ++my)
+      for (int mz = -5; mz <= 5; ++mz) {
+        if (mx == 0 && my == 0 && mz == 0) continue;
+        const double k[3] = {2 * M_PI * mx, 2 * M_PI * my, 2 * M_PI * mz};
+        const double k2 = k[0] * k[0] + k[1] * k[1] + k[2] * k[2];
+        const double w = 4.0 * M_PI / k2 * std::exp(-k2 / (4.0 * alpha * alpha)) *
+                         std::sin(k[0] * d[0] + k[1] * d[1] + k[2] * d[2]);
+        for (int e = 0; e < 3; ++e) a[e] += w * k[e];
+      }
+  const double r = std::sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+  for (int e = 0; e < 3; ++e) out[e] = a[e] - (r > 0.0 ? d[e] / (r * r * r) : 0.0);
+}
+
+/* Images other than the nearest of the Yukawa force a (1 + mu r) e^{-mu r} / r^2
+ * (box units), |n_i| <= 4; the library requires mu >= 8 / L. */
+static void yukawa_image_correction(double a, double mu, const double d[3], double out[3]) {
+  out[0] = out[1] = out[2] = 0.0;
+  for (int nx = -4; nx <= 4; ++nx)
+    for (int ny = -4; ny <= 4; ++ny)
+      for (int nz = -4; nz <= 4; ++nz) {
+        if (nx == 0 && ny == 0 && nz == 0) continue;
+        const double v[3] = {d[0] + nx, d[1] + ny, d[2] + nz};
+        const double r = std::sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+        const double f = a * (1.0 + mu * r) * std::exp(-mu * r) / (r * r * r);
+        for (int e = 0; e < 3; ++e) out[e] += f * v[e];
+      }
+}
+
+/* Lattice correction of law (kind, a, l) at offset d in box units (L = 1),
+ * per unit G M: the Newtonian part (C = 1) by Ewald, the Yukawa part by
+ * images. Exported for the tests. */
+void or_lattice_correction(int kind, double a, double l_box, const double d[3], double out[3]) {
+  out[0] = out[1] = out[2] = 0.0;
+  if (kind != OR_YUKAWA_PURE) ewald_newton_correction(d, out);
+  if (kind == OR_YUKAWA || kind == OR_YUKAWA_PURE) {
+    double y[3];
+    yukawa_image_correction(a, 1.0 / l_box, d, y);
+    for (int e = 0; e < 3; ++e) out[e] += y[e];
+  }
+}
+
+struct LatticeTable {
+  int kind;
+  double a, l_box;
+  std::vector<double> v;   /* [(N+1)^3][3] over [0, 1/2]^3, box units */
+};
+
+static std::deque<LatticeTable>& lattice_cache() {   /* references stay valid */
+  static std::deque<LatticeTable> cache;
+  return cache;
+}
+
+static const LatticeTable& lattice_table(int kind, double a, double l_box) {
+  auto& cache = lattice_cache();
+  for (const auto& t : cache)
+    if (t.kind == kind && t.a == a && t.l_box == l_box) return t;
+  LatticeTable t{kind, a, l_box, {}};
+  const int N = kEwaldGrid, P = N + 1;
+  t.v.assign((size_t)P * P * P * 3, 0.0);
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int i = 0; i < P; ++i)
+    for (int j = 0; j < P; ++j)
+      for (int k = 0; k < P; ++k) {
+        const double d[3] = {0.5 * i / N, 0.5 * j / N, 0.5 * k / N};
+        or_lattice_correction(kind, a, l_box, d, &t.v[(((size_t)i * P + j) * P + k) * 3]);
+      }
+  cache.push_back(std::move(t));
+  return cache.back();
+}
+
+/* The table of pair (s, t); built beforehand by prepare_lattice (the walks
+ * and sums call this from parallel loops, which only read the cache). */
+static const LatticeTable& pair_table(const or_params* p, int s, int t) {
+  const int law = p->law[s][t];
+  return lattice_table(law, law == OR_NEWTON ? 0.0 : p->ya[s][t],
+                       law == OR_NEWTON ? 0.0 : p->yl[s][t] / p->box);
+}
+
+static void prepare_lattice(const or_params* p) {
+  if (p->pure_tree != 2) return;
+  for (int s = 0; s < p->D; ++s)
+    for (int t = 0; t < p->D; ++t) pair_table(p, s, t);
+}
+
+/* Trilinear interpolation of the table at offset d (physical, min image),
+ * returned per unit G M in physical units. */
+static void lattice_interp(const LatticeTable& t, double L, const double d[3], double out[3]) {
+  const int N = kEwaldGrid, P = N + 1;
+  int i0[3];
+  double f[3], sg[3];
+  for (int e = 0; e < 3; ++e) {
+    const double u = std::fabs(d[e]) / L * 2.0 * N;
+    const double uc = std::min(u, (double)N);
+    i0[e] = std::min((int)std::floor(uc), N - 1);
+    f[e] = uc - i0[e];
+    sg[e] = d[e] < 0.0 ? -1.0 : 1.0;
+  }
+  double c[3] = {0, 0, 0};
+  for (int corner = 0; corner < 8; ++corner) {
+    const int bx = corner >> 2, by = (corner >> 1) & 1, bz = corner & 1;
+    const double w = (bx ? f[0] : 1 - f[0]) * (by ? f[1] : 1 - f[1]) * (bz ? f[2] : 1 - f[2]);
+    const double* v = &t.v[((((size_t)(i0[0] + bx)) * P + (i0[1] + by)) * P + (i0[2] + bz)) * 3];
+    for (int e = 0; e < 3; ++e) c[e] += w * v[e];
+  }
+  for (int e = 0; e < 3; ++e) out[e] = sg[e] * c[e] / (L * L);
+}
+
 /* Mahalo force factor |F| r^2 / (G M m) of phi = -(2 M m/(pi r)) atan(r/a),
  * a = s / (4 pi beta): (2/pi) [atan(x) - x / (1 + x^2)], x = r / a. */
 double or_mahalo_factor(double beta, double scale, double r) {
@@ -197,7 +338,13 @@ static void pair_accel(const or_params* p, int s, int t, double M, double nperp,
                        const double d[3], double acc[3], double* mag = nullptr) {
   const double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
   const double q = r2 + p->eps * p->eps;
-  if (!(q < p->rcut * p->rcut)) return;
+  if (p->pure_tree == 2) {
+    double cv[3];
+    lattice_interp(pair_table(p, s, t), p->box, d, cv);
+    for (int e = 0; e < 3; ++e) acc[e] += p->G[s][t] * M * cv[e];
+  } else if (!(q < p->rcut * p->rcut)) {
+    return;
+  }
   const double rho = std::sqrt(q);
   const double T = pair_factor(p, s, t, M, nperp, mpass, rho);
   const double f = p->G[s][t] * M * T / (rho * rho * rho);
@@ -416,6 +563,7 @@ void or_direct_mag(const or_params* p, int64_t n, const double* pos,
                    const uint8_t* type, const float* mass, int64_t ntgt,
                    const int64_t* tgt, double* acc, double* mag) {
   const double L = p->box;
+  prepare_lattice(p);
 #pragma omp parallel for schedule(dynamic, 16)
   for (int64_t q = 0; q < ntgt; ++q) {
     const int64_t i = tgt[q];
@@ -436,7 +584,8 @@ void or_direct_cells(const or_params* p, int64_t n, const double* pos,
                      const uint8_t* type, const float* mass, int64_t ntgt,
                      const int64_t* tgt, double* acc) {
   const double L = p->box;
-  const int nc = (int)std::floor(L / p->rcut);
+  prepare_lattice(p);
+  const int nc = p->pure_tree == 2 ? 0 : (int)std::floor(L / p->rcut);
   if (nc < 3) {
     or_direct(p, n, pos, type, mass, ntgt, tgt, acc);
     return;
@@ -523,6 +672,7 @@ void or_tree_walk_aold(const or_params* p, int64_t n, const double* pos, const u
 static void tree_walk(const or_params* p, int64_t n, const double* pos, const uint8_t* type,
                       const float* mass, const float* aold, int64_t ntgt, const int64_t* tgt,
                       double* acc, int64_t* counts, double* times) {
+  prepare_lattice(p);
   const double t0 = wall_seconds();
   std::vector<uint64_t> skeys;
   std::vector<uint32_t> perm;
@@ -537,7 +687,7 @@ static void tree_walk(const or_params* p, int64_t n, const double* pos, const ui
   const double t1 = wall_seconds();
   const double L = p->box;
   const int D = p->D;
-  const double rc2 = p->rcut * p->rcut;
+  const double rc2 = p->pure_tree == 2 ? INFINITY : p->rcut * p->rcut;
   const bool relative = p->opening == 1 && aold != nullptr;
   double gmax = 0.0;
   for (int i = 0; i < D; ++i)
