@@ -93,6 +93,14 @@ enum { NG_OPEN_GEOMETRIC = 0, NG_OPEN_RELATIVE = 1 };
  *  pure_tree      1: pure tree mode (needs pm_mesh == 0): no TreePM split, every
  *                 law is evaluated whole, truncated at r_cut = rcut_over_rs *
  *                 asmth * L (< L/2, minimum image), by a per-particle walk.
+ *                 2: periodic pure tree mode with the lattice corrections of
+ *                 Sec. 2.3: no cut-off; every term is the nearest image's
+ *                 plus the force of all other images of its source, tabulated
+ *                 per law on a 64^3 grid over [0, L/2]^3 (Ewald sum for the
+ *                 Newtonian part, image sum for Yukawa parts, which need
+ *                 yuk_l <= L/8) and interpolated; not with Mahalo laws. The
+ *                 tables are computed on the device when the context is
+ *                 configured.
  *  ignore_nperp   1: Mahalo monopoles are treated as single objects (N_perp = 1),
  *                 the "without tracking" comparison of Sec. 3.3.
  *  beta           Mahalo scale beta (> 0 when a Mahalo law is used).

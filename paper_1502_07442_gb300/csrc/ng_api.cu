@@ -104,7 +104,9 @@ int build_tables(ng_ctx* c) {
   }
   if (ncut < 16) return fail(c, NG_EINVAL, "table_size %d too small", ncut);
   c->ncut = ncut;
-  c->dr_phys = c->rcut / (ncut - 0.5);
+  // pure tree mode evaluates the laws directly: the table is kept (zero) only
+  // so that every context has one
+  c->dr_phys = p.pure_tree ? 1.0 : c->rcut / (ncut - 0.5);
   // separations in table units must stay below 2^22 for the float-bit index
   if (std::sqrt(3.0) * c->L / c->dr_phys > 4.0e6)
     return fail(c, NG_EINVAL, "box too large relative to the table spacing (box/dr = %.3g)",
@@ -112,6 +114,7 @@ int build_tables(ng_ctx* c) {
   std::vector<float> h((size_t)c->nlaws * (ncut + 1) * 2, 0.f);
   for (int u = 0; u < c->nlaws; ++u) {
     float* t = h.data() + (size_t)u * (ncut + 1) * 2;
+    if (p.pure_tree) continue;
     auto T = [&](double rho) { return short_law_factor(laws[u].kind, laws[u].a, laws[u].l, c->rs, rho); };
     const double dr = c->dr_phys;
     t[0] = (float)T(0.0);
@@ -140,6 +143,17 @@ int build_tables(ng_ctx* c) {
   std::memcpy(c->h_tab_pinned, h.data(), h.size() * sizeof(float));
   NG_CUDA(c, cudaMemcpyAsync(c->d_tab.p, c->h_tab_pinned, h.size() * sizeof(float),
                              cudaMemcpyHostToDevice, c->stream));
+  c->lattice_grid = 0;
+  if (p.pure_tree == 2) {
+    std::vector<int> kinds;
+    std::vector<double> as, ls;
+    for (const Law& w : laws) {
+      kinds.push_back(w.kind);
+      as.push_back(w.a);
+      ls.push_back(w.l);
+    }
+    NG_TRY(build_lattice(c, (int)laws.size(), kinds.data(), as.data(), ls.data()));
+  }
   return NG_OK;
 }
 
@@ -334,10 +348,19 @@ int validate(ng_ctx* c, const ng_params* p) {
   if (p->opening != NG_OPEN_GEOMETRIC && p->opening != NG_OPEN_RELATIVE)
     return fail(c, NG_EINVAL, "opening must be NG_OPEN_GEOMETRIC or NG_OPEN_RELATIVE");
   if (p->reserved1 != 0) return fail(c, NG_EINVAL, "reserved1 must be 0");
-  if (p->pure_tree != 0 && p->pure_tree != 1) return fail(c, NG_EINVAL, "pure_tree must be 0 or 1");
+  if (p->pure_tree < 0 || p->pure_tree > 2) return fail(c, NG_EINVAL, "pure_tree must be 0, 1 or 2");
   if (p->ignore_nperp != 0 && p->ignore_nperp != 1)
     return fail(c, NG_EINVAL, "ignore_nperp must be 0 or 1");
   if (p->pure_tree && p->pm_mesh != 0) return fail(c, NG_EINVAL, "pure tree mode needs pm_mesh = 0");
+  if (p->pure_tree == 2)
+    for (int i = 0; i < p->D; ++i)
+      for (int j = 0; j < p->D; ++j) {
+        if (p->law[i][j] == NG_MAHALO)
+          return fail(c, NG_EINVAL, "Mahalo laws have no lattice corrections (pure_tree 1 only)");
+        if ((p->law[i][j] == NG_YUKAWA || p->law[i][j] == NG_YUKAWA_PURE) &&
+            !(p->yuk_l[i][j] <= p->box / 8))
+          return fail(c, NG_EINVAL, "lattice corrections need yuk_l <= box/8 (yuk_l[%d][%d])", i, j);
+      }
   if (p->pure_tree) {
     bool mahalo = false;
     for (int i = 0; i < p->D; ++i)
@@ -372,7 +395,7 @@ int validate(ng_ctx* c, const ng_params* p) {
         return fail(c, NG_EINVAL, "Yukawa range yuk_l[%d][%d] must be > 0", i, j);
     }
   const double rs = p->pm_mesh > 0 ? p->asmth * p->box / p->pm_mesh : p->asmth * p->box;
-  if (!(p->rcut_over_rs * rs < 0.5 * p->box))
+  if (p->pure_tree != 2 && !(p->rcut_over_rs * rs < 0.5 * p->box))
     return fail(c, NG_EINVAL, "r_cut = %.4g must be below box/2", p->rcut_over_rs * rs);
   return NG_OK;
 }
@@ -385,7 +408,7 @@ int ctx_configure(ng_ctx* c, const ng_params* p) {
   if (c->p.group_cell == 0) c->p.group_cell = c->p.group_size;
   c->L = p->box;
   c->rs = p->pm_mesh > 0 ? p->asmth * p->box / p->pm_mesh : p->asmth * p->box;
-  c->rcut = p->rcut_over_rs * c->rs;
+  c->rcut = p->pure_tree == 2 ? INFINITY : p->rcut_over_rs * c->rs;
   c->built = false;
   if (c->step_exec) {
     cudaGraphExecDestroy(c->step_exec);
@@ -423,7 +446,7 @@ int ng_create(ng_ctx** out, const ng_params* p, void* stream) {
   c->stream = (cudaStream_t)stream;
   c->L = p->box;
   c->rs = p->pm_mesh > 0 ? p->asmth * p->box / p->pm_mesh : p->asmth * p->box;
-  c->rcut = p->rcut_over_rs * c->rs;
+  c->rcut = p->pure_tree == 2 ? INFINITY : p->rcut_over_rs * c->rs;
   cudaError_t e = cudaGetDevice(&c->device);
   int v = 0;
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, c->device);

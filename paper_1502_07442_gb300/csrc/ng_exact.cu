@@ -16,6 +16,13 @@
 // and the acceleration G M f(rho) d / rho^3 at the softened separation rho,
 // for rho < r_cut (minimum image, r_cut < L/2). A species is cored when its
 // own pair law is the Mahalo law.
+//
+// Pure tree mode 2 (Sec. 2.3 lattice corrections): no cut-off, and every
+// term adds the force of all other periodic images of its source, read by
+// trilinear interpolation from a table of the correction over [0, L/2]^3
+// (one per distinct law; each component odd in its own axis, even in the
+// others). The tables are computed here in FP64: an Ewald sum for the
+// Newtonian part, an image sum for Yukawa parts (yuk_l <= L/8).
 #include "ng_internal.cuh"
 
 namespace ng {
@@ -49,6 +56,11 @@ struct ExactArgs {
   int8_t kind[kMaxD][kMaxD];
   float G[kMaxD][kMaxD], ya[kMaxD][kMaxD], inv_l[kMaxD][kMaxD];
   uint8_t cored[kMaxD];
+  const float4* lattice;   // [law][(N+1)^3] corrections per unit G M (box units), or nullptr
+  int lat_n;               // N
+  float lat_scale;         // 2 N / L
+  float lat_inv_l2;        // 1 / L^2
+  int8_t tabid[kMaxD][kMaxD];
   float* acc;              // [3][n] caller order
   int accumulate;
   unsigned long long* counter;   // executed terms (optional)
@@ -101,6 +113,36 @@ __device__ __forceinline__ void exact_term(const ExactArgs& a, int s, int t, flo
   ax = fmaf(g, dx, ax);
   ay = fmaf(g, dy, ay);
   az = fmaf(g, dz, az);
+  if (a.lattice) {
+    // all other images: trilinear interpolation at |d|, signs per axis
+    const int N = a.lat_n, P = N + 1;
+    const float4* T = a.lattice + (size_t)a.tabid[s][t] * P * P * P;
+    const float dv[3] = {dx, dy, dz};
+    int i0[3];
+    float fr[3];
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+      const float u = fminf(fabsf(dv[e]) * a.lat_scale, (float)N);
+      i0[e] = min((int)u, N - 1);
+      fr[e] = u - (float)i0[e];
+    }
+    float cx = 0.f, cy = 0.f, cz = 0.f;
+#pragma unroll
+    for (int corner = 0; corner < 8; ++corner) {
+      const int bx = corner >> 2, by = (corner >> 1) & 1, bz = corner & 1;
+      const float w = (bx ? fr[0] : 1.f - fr[0]) * (by ? fr[1] : 1.f - fr[1]) *
+                      (bz ? fr[2] : 1.f - fr[2]);
+      const float4 v = __ldg(T + ((size_t)(i0[0] + bx) * P + (i0[1] + by)) * P + (i0[2] + bz));
+      cx = fmaf(w, v.x, cx);
+      cy = fmaf(w, v.y, cy);
+      cz = fmaf(w, v.z, cz);
+    }
+    const float gc = a.G[s][t] * M * a.lat_inv_l2;
+    // the table holds d_e >= 0; the component flips with the sign of d_e
+    ax = fmaf(gc, dx < 0.f ? -cx : cx, ax);
+    ay = fmaf(gc, dy < 0.f ? -cy : cy, ay);
+    az = fmaf(gc, dz < 0.f ? -cz : cz, az);
+  }
 }
 
 __global__ void __launch_bounds__(128) k_walk_exact(ExactArgs a) {
@@ -265,6 +307,12 @@ int launch_walk_exact(ng_ctx* c, float* acc, bool accumulate, bool count) {
       a.inv_l[i][j] = in && c->p.yuk_l[i][j] > 0 ? (float)(1.0 / c->p.yuk_l[i][j]) : 0.f;
     }
   }
+  a.lattice = c->lattice_grid > 0 ? as<float4>(c->lattice) : nullptr;
+  a.lat_n = c->lattice_grid;
+  a.lat_scale = (float)(2.0 * c->lattice_grid / c->L);
+  a.lat_inv_l2 = (float)(1.0 / (c->L * c->L));
+  for (int i = 0; i < kMaxD; ++i)
+    for (int j = 0; j < kMaxD; ++j) a.tabid[i][j] = c->tabid[i][j];
   a.acc = acc;
   a.accumulate = accumulate ? 1 : 0;
   a.counter = count ? as<unsigned long long>(c->counter) : nullptr;
@@ -273,6 +321,77 @@ int launch_walk_exact(ng_ctx* c, float* acc, bool accumulate, bool count) {
   k_walk_exact<<<blocks, 128, 0, c->stream>>>(a);
   c->launches += 1;
   NG_CUDA(c, cudaGetLastError());
+  return NG_OK;
+}
+
+// ------------------------------------------------ lattice-correction tables
+
+// Correction of one law at grid point (i, j, k) of [0, 1/2]^3 (box units,
+// L = 1), per unit G M, FP64: all images but the nearest. Newtonian part by
+// Ewald summation (splitting 2; real-space images |n_i| <= 3, reciprocal
+// vectors |m_i| <= 5); Yukawa part a (1 + mu r) e^{-mu r} / r^2 by images
+// |n_i| <= 4.
+__global__ void k_lattice_table(int kind, double ya, double mu, int N, float4* out) {
+  const int P = N + 1;
+  const int64_t total = (int64_t)P * P * P;
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < total;
+       g += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(g / ((int64_t)P * P)), j = (int)((g / P) % P), k = (int)(g % P);
+    const double d[3] = {0.5 * i / N, 0.5 * j / N, 0.5 * k / N};
+    double acc[3] = {0.0, 0.0, 0.0};
+    if (kind != NG_YUKAWA_PURE) {
+      const double al = 2.0;
+      for (int nx = -3; nx <= 3; ++nx)
+        for (int ny = -3; ny <= 3; ++ny)
+          for (int nz = -3; nz <= 3; ++nz) {
+            const double v[3] = {d[0] + nx, d[1] + ny, d[2] + nz};
+            const double r = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+            if (r == 0.0) continue;
+            const double f = (erfc(al * r) + 2.0 * al * r * 0.56418958354775628 *
+                                                 exp(-al * al * r * r)) / (r * r * r);
+            for (int e = 0; e < 3; ++e) acc[e] += f * v[e];
+          }
+      for (int mx = -5; mx <= 5; ++mx)
+        for (int my = -5; my <= 5; ++my)
+          for (int mz = -5; mz <= 5; ++mz) {
+            if (mx == 0 && my == 0 && mz == 0) continue;
+            const double kv[3] = {2.0 * M_PI * mx, 2.0 * M_PI * my, 2.0 * M_PI * mz};
+            const double k2 = kv[0] * kv[0] + kv[1] * kv[1] + kv[2] * kv[2];
+            const double w = 4.0 * M_PI / k2 * exp(-k2 / (4.0 * al * al)) *
+                             sin(kv[0] * d[0] + kv[1] * d[1] + kv[2] * d[2]);
+            for (int e = 0; e < 3; ++e) acc[e] += w * kv[e];
+          }
+      const double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+      if (r > 0.0)
+        for (int e = 0; e < 3; ++e) acc[e] -= d[e] / (r * r * r);
+    }
+    if (kind == NG_YUKAWA || kind == NG_YUKAWA_PURE) {
+      for (int nx = -4; nx <= 4; ++nx)
+        for (int ny = -4; ny <= 4; ++ny)
+          for (int nz = -4; nz <= 4; ++nz) {
+            if (nx == 0 && ny == 0 && nz == 0) continue;
+            const double v[3] = {d[0] + nx, d[1] + ny, d[2] + nz};
+            const double r = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+            const double f = ya * (1.0 + mu * r) * exp(-mu * r) / (r * r * r);
+            for (int e = 0; e < 3; ++e) acc[e] += f * v[e];
+          }
+    }
+    out[g] = make_float4((float)acc[0], (float)acc[1], (float)acc[2], 0.f);
+  }
+}
+
+int build_lattice(ng_ctx* c, int nlaws, const int* kind, const double* a, const double* l) {
+  constexpr int N = 64;
+  const size_t P3 = (size_t)(N + 1) * (N + 1) * (N + 1);
+  NG_TRY(ensure(c, c->lattice, (size_t)nlaws * P3 * sizeof(float4)));
+  for (int u = 0; u < nlaws; ++u) {
+    const bool yk = kind[u] == NG_YUKAWA || kind[u] == NG_YUKAWA_PURE;
+    k_lattice_table<<<work_grid(c, (int64_t)P3, 4), 256, 0, c->stream>>>(
+        kind[u], yk ? a[u] : 0.0, yk ? c->L / l[u] : 0.0, N, as<float4>(c->lattice) + u * P3);
+    c->launches += 1;
+    NG_CUDA(c, cudaGetLastError());
+  }
+  c->lattice_grid = N;
   return NG_OK;
 }
 

@@ -132,6 +132,8 @@ struct ng_ctx {
   ng::DevBuf status;     // uint32[ST_COUNT]
   ng::DevBuf walk_desc, walk_prefix;
   ng::DevBuf counter;    // unsigned long long
+  ng::DevBuf lattice;    // float4[nlaws][(N+1)^3] lattice corrections (pure tree mode 2)
+  int lattice_grid = 0;  // N of the lattice tables (0: none)
   ng::DevBuf aold;       // float[n] |previous acceleration| per body (caller order)
   int64_t aold_n = -1;   // bodies aold holds (-1: none)
   ng::DevBuf acc_tmp;    // float[3][n] scratch for summing short + long
@@ -207,6 +209,8 @@ int launch_count(ng_ctx* c, int64_t* counts);  // per-particle walk counts
 int launch_walk_exact(ng_ctx* c, float* acc, bool accumulate, bool count);
 // The tree force of a context: the group walk, or in pure tree mode the exact walk.
 int launch_tree_force(ng_ctx* c, float* acc, bool accumulate, bool count);
+// Lattice-correction tables of pure tree mode 2, one per distinct law.
+int build_lattice(ng_ctx* c, int nlaws, const int* kind, const double* a, const double* l);
 // Relative opening criterion: active when the context asks for it and holds
 // |a_old| for its current bodies; G_max of the law table; |acc| -> aold.
 bool relative_active(const ng_ctx* c);

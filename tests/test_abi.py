@@ -57,7 +57,7 @@ def test_params_layout_matches_c(binding, tmp_path):
     ("D", 0, "D=0"), ("D", 7, "D=7"), ("eps", 0.0, "eps"), ("box", -1.0, "box"),
     ("pm_mesh", 48, "pm_mesh"), ("leaf_size", 65, "leaf_size"), ("theta", -0.1, "theta"),
     ("rcut_over_rs", 1000.0, "r_cut"), ("opening", 2, "opening"), ("reserved1", 1, "reserved1"),
-    ("pure_tree", 1, "pm_mesh"), ("pure_tree", 2, "pure_tree"), ("ignore_nperp", 3, "ignore_nperp"),
+    ("pure_tree", 1, "pm_mesh"), ("pure_tree", 3, "pure_tree"), ("ignore_nperp", 3, "ignore_nperp"),
 ])
 def test_create_rejects_bad_params(binding, field, value, needle):
     p = binding.make_params(2, np.ones((2, 2)), eps=1e-3, pm_mesh=32)
@@ -87,6 +87,18 @@ def test_mahalo_validation(binding, law, beta, needle):
     pure = needle != "pure tree"
     p = binding.make_params(2, np.ones((2, 2)), eps=1e-3, pm_mesh=0 if pure else 32, law=law,
                             pure_tree=1 if pure else 0, beta=beta)
+    ctx = ctypes.c_void_p()
+    assert binding.lib().ng_create(ctypes.byref(ctx), ctypes.byref(p), None) == binding.NG_EINVAL
+    assert needle in binding.lib().ng_last_error(None).decode()
+
+
+@pytest.mark.parametrize("law,yl,needle", [
+    ([[3, 3], [3, 3]], 0.05, "Mahalo"),          # Mahalo laws have no lattice corrections
+    ([[1, 1], [1, 1]], 0.2, "yuk_l"),            # Yukawa image sums need yuk_l <= L/8
+])
+def test_lattice_mode_validation(binding, law, yl, needle):
+    p = binding.make_params(2, np.ones((2, 2)), eps=1e-3, pm_mesh=0, law=law, yuk_a=np.ones((2, 2)),
+                            yuk_l=np.full((2, 2), yl), pure_tree=2, beta=1e-3)
     ctx = ctypes.c_void_p()
     assert binding.lib().ng_create(ctypes.byref(ctx), ctypes.byref(p), None) == binding.NG_EINVAL
     assert needle in binding.lib().ng_last_error(None).decode()
