@@ -244,6 +244,18 @@ int ng_step(ng_ctx* ctx, int64_t n, double* pos, float* vel, const uint8_t* type
  * cnt uint32[node][D] (N_perp per species), mass double[node][D],
  * com double[node][D][3]. Synchronises the stream.
  */
+/*
+ * ng_step on host arrays (Sec. 2.1.1): the same integration for callers that
+ * hold the particles in host memory (page-locked memory, e.g. from
+ * cudaHostAlloc, copies at full link speed; pageable memory works but is
+ * staged). pos (double[3][n]), vel (float[3][n]) and acc (float[3][n]) are
+ * read and written back; type (uint8[n]) and mass (float[n]) are read. The
+ * context keeps device copies of the arrays between calls (so a repeated call
+ * with the same n replays the captured step). Synchronises the stream.
+ */
+int ng_step_host(ng_ctx* ctx, int64_t n, double* pos, float* vel, const uint8_t* type,
+                 const float* mass, float* acc, int acc_valid, int nsteps, double dt);
+
 int ng_tree_export(ng_ctx* ctx, int64_t* nnodes, int32_t* level, uint64_t* prefix,
                    int64_t* first, int64_t* count, int32_t* nchild, int64_t* child_first,
                    uint32_t* cnt, double* mass, double* com);

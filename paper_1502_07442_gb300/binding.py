@@ -89,6 +89,7 @@ def lib():
         L.ng_tree_force.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_uint64)]
         L.ng_count_interactions.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_uint64)]
         L.ng_set_acc_old.argtypes = [vp, i64, vp]
+        L.ng_step_host.argtypes = [vp, i64, vp, vp, vp, vp, vp, i32, i32, d]
         L.ng_timestep.argtypes = [vp, i64, vp, d, d, ctypes.POINTER(d), ctypes.POINTER(ctypes.c_float)]
         L.ng_pm_force.argtypes = [vp, vp]
         L.ng_step.argtypes = [vp, i64, vp, vp, vp, vp, vp, i32, i32, d]
@@ -127,7 +128,7 @@ def lib():
                   "ng_batch_step", "ng_batch_size", "ng_batch_walk_launches",
                   "ng_batch_launch_count", "ng_serve_create", "ng_serve_destroy",
                   "ng_serve_submit", "ng_serve_cancel", "ng_serve_poll", "ng_serve_pending",
-                  "ng_serve_wait", "ng_serve", "ng_set_acc_old", "ng_timestep"):
+                  "ng_serve_wait", "ng_serve", "ng_set_acc_old", "ng_timestep", "ng_step_host"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -142,7 +143,7 @@ def exported_symbols():
             "ng_batch_launch_count", "ng_batch_last_error", "ng_serve_create",
             "ng_serve_destroy", "ng_serve_submit", "ng_serve_cancel", "ng_serve_poll",
             "ng_serve_pending", "ng_serve_wait", "ng_serve", "ng_serve_last_error",
-            "ng_serve_request_bytes", "ng_sort_keys_noalloc", "ng_set_acc_old", "ng_timestep"]
+            "ng_serve_request_bytes", "ng_sort_keys_noalloc", "ng_set_acc_old", "ng_timestep", "ng_step_host"]
 
 
 def _check(ctx, code):
@@ -256,6 +257,13 @@ def ng_step(ctx, pos, vel, typ, mass, acc, acc_valid, nsteps, dt):
     n = typ.numel()
     _check(ctx, lib().ng_step(ctx, n, _ptr(pos), _ptr(vel), _ptr(typ), _ptr(mass), _ptr(acc),
                               int(bool(acc_valid)), int(nsteps), float(dt)))
+
+
+def ng_step_host(ctx, pos, vel, typ, mass, acc, acc_valid, nsteps, dt):
+    """ng_step on host tensors/arrays (updated in place); pinned memory copies fastest."""
+    n = typ.shape[-1]
+    _check(ctx, lib().ng_step_host(ctx, int(n), _ptr(pos), _ptr(vel), _ptr(typ), _ptr(mass),
+                                   _ptr(acc), int(bool(acc_valid)), int(nsteps), float(dt)))
 
 
 def ng_tree_export(ctx, D):

@@ -490,7 +490,8 @@ int ng_destroy(ng_ctx* c) {
                     &c->tperm, &c->scan_part, &c->n_level, &c->n_prefix, &c->n_first,
                     &c->n_count, &c->n_child, &c->n_nchild, &c->n_tmp, &c->n_off, &c->n_m64,
                     &c->n_cnt, &c->n_geo, &c->n_com, &c->n_link, &c->n_mono, &c->groups, &c->gsize, &c->grank,
-                    &c->status, &c->counter, &c->acc_tmp, &c->aold, &c->rho, &c->rhok, &c->phi,
+                    &c->status, &c->counter, &c->acc_tmp, &c->aold, &c->io_pos, &c->io_vel, &c->io_type, &c->io_mass,
+                    &c->io_acc, &c->lattice, &c->rho, &c->rhok, &c->phi,
                     &c->walk_desc, &c->walk_prefix};
   for (DevBuf* b : bufs) release(*b);
   delete c;
@@ -721,6 +722,34 @@ int ng_step(ng_ctx* c, int64_t n, double* pos, float* vel, const uint8_t* type,
   NG_TRY(read_status(c, st));
   NG_TRY(check_flags(c, st[ST_FLAGS]));
   c->built = true;
+  return NG_OK;
+}
+
+int ng_step_host(ng_ctx* c, int64_t n, double* pos, float* vel, const uint8_t* type,
+                 const float* mass, float* acc, int acc_valid, int nsteps, double dt) {
+  if (!c) return NG_EINVAL;
+  if (n < 1 || n >= (int64_t)1 << 31) return fail(c, NG_EINVAL, "n outside [1, 2^31)");
+  if (!pos || !vel || !type || !mass || !acc) return fail(c, NG_EINVAL, "NULL array");
+  NG_TRY(ensure(c, c->io_pos, (size_t)n * 24));
+  NG_TRY(ensure(c, c->io_vel, (size_t)n * 12));
+  NG_TRY(ensure(c, c->io_type, (size_t)n));
+  NG_TRY(ensure(c, c->io_mass, (size_t)n * 4));
+  NG_TRY(ensure(c, c->io_acc, (size_t)n * 12));
+  double* dpos = as<double>(c->io_pos);
+  float* dvel = as<float>(c->io_vel);
+  float* dacc = as<float>(c->io_acc);
+  NG_CUDA(c, cudaMemcpyAsync(dpos, pos, (size_t)n * 24, cudaMemcpyHostToDevice, c->stream));
+  NG_CUDA(c, cudaMemcpyAsync(dvel, vel, (size_t)n * 12, cudaMemcpyHostToDevice, c->stream));
+  NG_CUDA(c, cudaMemcpyAsync(c->io_type.p, type, (size_t)n, cudaMemcpyHostToDevice, c->stream));
+  NG_CUDA(c, cudaMemcpyAsync(c->io_mass.p, mass, (size_t)n * 4, cudaMemcpyHostToDevice, c->stream));
+  if (acc_valid)
+    NG_CUDA(c, cudaMemcpyAsync(dacc, acc, (size_t)n * 12, cudaMemcpyHostToDevice, c->stream));
+  NG_TRY(ng_step(c, n, dpos, dvel, as<uint8_t>(c->io_type), as<float>(c->io_mass), dacc,
+                 acc_valid, nsteps, dt));
+  NG_CUDA(c, cudaMemcpyAsync(pos, dpos, (size_t)n * 24, cudaMemcpyDeviceToHost, c->stream));
+  NG_CUDA(c, cudaMemcpyAsync(vel, dvel, (size_t)n * 12, cudaMemcpyDeviceToHost, c->stream));
+  NG_CUDA(c, cudaMemcpyAsync(acc, dacc, (size_t)n * 12, cudaMemcpyDeviceToHost, c->stream));
+  NG_CUDA(c, cudaStreamSynchronize(c->stream));
   return NG_OK;
 }
 

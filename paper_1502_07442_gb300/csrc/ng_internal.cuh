@@ -132,6 +132,7 @@ struct ng_ctx {
   ng::DevBuf status;     // uint32[ST_COUNT]
   ng::DevBuf walk_desc, walk_prefix;
   ng::DevBuf counter;    // unsigned long long
+  ng::DevBuf io_pos, io_vel, io_type, io_mass, io_acc;   // device copies for ng_step_host
   ng::DevBuf lattice;    // float4[nlaws][(N+1)^3] lattice corrections (pure tree mode 2)
   int lattice_grid = 0;  // N of the lattice tables (0: none)
   ng::DevBuf aold;       // float[n] |previous acceleration| per body (caller order)

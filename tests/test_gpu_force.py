@@ -170,3 +170,34 @@ def test_kdk_steps_match_oracle(ng):
     x2, v2, _ = oracle.kdk(oracle_params(prm), x_ref, v_ref, w["type"], w["mass"], 2, 1e-3)
     check_pos(pos.cpu().numpy(), x2, x_ref)
     sim.close()
+
+
+def test_step_host_matches_device_step(ng):
+    """ng_step_host (host arrays in and out) runs the device ng_step."""
+    import torch
+    w = small_clustered(5000, 2, 61, mesh=32)
+    rng = inputs.rng_for(62)
+    vel0 = (0.01 * rng.standard_normal((3, 5000))).astype(np.float32)
+    pos, typ, mass = device_arrays(w)
+    vel = torch.from_numpy(vel0.copy()).to(pos.device)
+    acc = torch.empty((3, 5000), dtype=torch.float32, device=pos.device)
+    sim = ng.Simulation(ng_params(w["params"]))
+    ng.ng_step(sim.ctx, pos, vel, typ, mass, acc, False, 3, 1e-3)
+    torch.cuda.synchronize()
+    sim.close()
+    hp = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory()
+          for k, v in dict(pos=w["pos"], vel=vel0, typ=w["type"], mass=w["mass"],
+                           acc=np.zeros((3, 5000), np.float32)).items()}
+    sim = ng.Simulation(ng_params(w["params"]))
+    ng.ng_step_host(sim.ctx, hp["pos"], hp["vel"], hp["typ"], hp["mass"], hp["acc"], False, 2, 1e-3)
+    ng.ng_step_host(sim.ctx, hp["pos"], hp["vel"], hp["typ"], hp["mass"], hp["acc"], True, 1, 1e-3)
+    sim.close()
+    # the same computation; the PM deposit's FP32 atomics make the last bits
+    # order-dependent, so compare at FP32 rounding level
+    err, _ = rel_err(hp["acc"].numpy(), acc.cpu().numpy())
+    assert err.max() <= 1e-4, err.max()
+    dx = hp["pos"].numpy() - pos.cpu().numpy()
+    dx -= np.rint(dx)
+    assert np.abs(dx).max() <= 1e-7     # bodies move ~3e-5 in these three steps
+    v_dev = vel.cpu().numpy()
+    assert np.abs(hp["vel"].numpy() - v_dev).max() <= 1e-5 * np.abs(v_dev).max()
