@@ -48,6 +48,25 @@ DEFAULT_WORKLOAD = "clustered16m_d4_yukawa"
 REF_LEAF = 8
 
 
+def job_totals(units, ms, world):
+    """Whole-job totals of a replicas run: the units every rank processed
+    (summed) and the timed region of the slowest rank (maximum). Ranks run
+    independent problems, so this is the only exchange; world == 1 returns the
+    inputs. Works with any initialised process group (NCCL here, gloo in the
+    tests), the tensors living on the group's device."""
+    if world <= 1:
+        return float(units), float(ms)
+    import torch
+    import torch.distributed as dist
+    dev = torch.device("cuda", torch.cuda.current_device()) \
+        if dist.get_backend() == "nccl" else torch.device("cpu")
+    u = torch.tensor([float(units)], dtype=torch.float64, device=dev)
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=dev)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(u.item()), float(t.item())
+
+
 def walk_traffic(workload, n_override, leaf, cell):
     """DRAM bytes (read + write) of one walk launch, from the ncu capture recorded in
     profiles/ for this workload and walk configuration; None unless that capture was
@@ -296,11 +315,10 @@ def main():
     count_tuned_leaf = ng.ng_count_interactions(sim.ctx)
     ref.close()
     count = 0.5 * (count0 + count1)
-    if ws > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    value = count * args.steps * ws / (ms / 1e3)
+    # every rank integrates its own simulation: sum the units, take the slowest clock
+    job_count, ms = job_totals(count, ms, ws)
+    job_n, _ = job_totals(n, ms, ws)
+    value = job_count * args.steps / (ms / 1e3)
 
     # dominant kernel: the walk alone, events on the launching stream
     walk_ms = []
@@ -350,11 +368,8 @@ def main():
         f1.record(stream)
         barrier()
         ems = f0.elapsed_time(f1)
-        if ws > 1:
-            t = torch.tensor([ems], device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ems = float(t.item())
-        e2e = {"value": count * ksteps * ws / (ems / 1e3), "unit": "interactions/s",
+        _, ems = job_totals(0, ems, ws)
+        e2e = {"value": job_count * ksteps / (ems / 1e3), "unit": "interactions/s",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                "ms_per_step": ems / ksteps}
 
@@ -375,7 +390,7 @@ def main():
                 "count_basis": f"per-particle walk (theta {w['params']['theta']}) on the canonical "
                                f"tree with leaf size {REF_LEAF}",
                 "interactions_per_step_at_walk_leaf": int(count_tuned_leaf),
-                "particles_per_s": n * args.steps * ws / (ms / 1e3),
+                "particles_per_s": job_n * args.steps / (ms / 1e3),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
                 "gpu_launches": int(launches), "autotune": tuned}
         print(json.dumps(line))
@@ -391,6 +406,9 @@ def bench_batch(args, ws, rank, local):
     import torch
     from paper_1502_07442_gb300 import binding as ng, inputs
     torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     dev = torch.device("cuda", local)
     specs = inputs.batch_specs(seed=1003 + 7919 * rank)
     state = []
@@ -424,14 +442,20 @@ def bench_batch(args, ws, rank, local):
     torch.cuda.synchronize()
     l0 = ng.ng_batch_launch_count(b)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if ws > 1:
+        torch.distributed.barrier()
     with Clocks(local) as clk:
         e0.record()
         ng.ng_batch_step(b, L("pos"), L("vel"), L("typ"), L("mass"), L("acc"), True, args.steps, 1e-3)
         e1.record()
         torch.cuda.synchronize()
+        if ws > 1:
+            torch.distributed.barrier()
     ms = e0.elapsed_time(e1)
-    nbodies = sum(x["typ"].numel() for x in state)
-    line = {"metric": "particle-node interactions/s", "value": sum(counts) * args.steps / (ms / 1e3),
+    # every rank advances its own 64 simulations: sum the units, slowest clock
+    job_count, ms = job_totals(sum(counts), ms, ws)
+    nbodies, _ = job_totals(sum(x["typ"].numel() for x in state), ms, ws)
+    line = {"metric": "particle-node interactions/s", "value": job_count * args.steps / (ms / 1e3),
             "unit": "interactions/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -446,6 +470,8 @@ def bench_batch(args, ws, rank, local):
     ng.ng_batch_destroy(b)
     if rank == 0:
         print(json.dumps(line))
+    if ws > 1:
+        torch.distributed.destroy_process_group()
 
 
 def bench_serve(args, ws, rank, local):
