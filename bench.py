@@ -99,6 +99,8 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--n", type=int, default=None, help="override N (smaller test runs)")
+    ap.add_argument("--species", type=int, default=None,
+                    help="override the species count D (the paper's 1/D scaling)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline leg")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -253,7 +255,8 @@ def main():
     if args.workload == "serve2000":
         return bench_serve(args, ws, rank, local)
     from paper_1502_07442_gb300 import inputs
-    w = inputs.workload(args.workload, n=args.n, seed=None if rank == 0 else 1002 + 7919 * rank)
+    w = inputs.workload(args.workload, n=args.n, seed=None if rank == 0 else 1002 + 7919 * rank,
+                        species=args.species)
     if args.impl == "reference":
         return run_reference(args, w, ws, rank)
 
@@ -337,7 +340,8 @@ def main():
     med = clocks.get("sm_mhz") or 2070.0
     roofline = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 2),
                 "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
-                "traffic": walk_traffic(args.workload, args.n, int(w["params"]["leaf_size"]),
+                "traffic": walk_traffic(args.workload, args.n if args.species is None else -1,
+                                        int(w["params"]["leaf_size"]),
                                         int(w["params"].get("group_cell", 0) or 32)),
                 "kernel": "k_walk", "walk_ms": round(walk, 3),
                 "peak_at_median_clock": round(nsm * 128 * 2 * med * 1e6 / 1e12, 2),

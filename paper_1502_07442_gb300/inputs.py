@@ -105,8 +105,11 @@ def _params(D, coup, n, mesh, theta, box=1.0, asmth=1.25, rcut_over_rs=4.5, eps_
                 rcut=rcut_over_rs * rs, theta=theta, pm_mesh=mesh, leaf_size=leaf_size)
 
 
-def workload(name: str, n: int | None = None, seed: int | None = None) -> dict:
-    """Inputs and parameters of a named workload (optionally at another N).
+def workload(name: str, n: int | None = None, seed: int | None = None,
+             species: int | None = None) -> dict:
+    """Inputs and parameters of a named workload (optionally at another N, or
+    with another species count: couplings of the workload's kind drawn for
+    that D, Newtonian ones where the workload fixes a 2 x 2 table).
 
     Returns dict(pos [3][n] f64, type [n] u8, mass [n] f32, vel [3][n] f32,
     params dict, steps, dt).
@@ -114,13 +117,13 @@ def workload(name: str, n: int | None = None, seed: int | None = None) -> dict:
     spec = WORKLOADS[name]
     n = spec["n"] if n is None else int(n)
     rng = rng_for(spec["seed"] if seed is None else seed)
-    D = spec["D"]
+    D = spec["D"] if species is None else int(species)
     if spec["gen"] == "uniform":
         pos = uniform(n, rng)
     else:
         pos = clustered(n, rng)
     typ = species_blocks(n, D, rng) if spec["species"] == "blocks" else species_uniform(n, D, rng)
-    if spec["couplings"] == "cfg0":
+    if spec["couplings"] == "cfg0" and D == 2:
         coup = dict(G=np.array([[1.0, 0.8], [0.8, 1.2]]), law=np.zeros((2, 2), np.int32),
                     ya=np.zeros((2, 2)), yl=np.ones((2, 2)))
     elif spec["couplings"] == "yukawa":
@@ -130,7 +133,8 @@ def workload(name: str, n: int | None = None, seed: int | None = None) -> dict:
     mass = np.full(n, 1.0 / n, np.float32)
     params = _params(D, coup, n, spec["mesh"], spec["theta"])
     return dict(pos=pos, type=typ, mass=mass, vel=np.zeros((3, n), np.float32),
-                params=params, steps=spec.get("steps", 1), dt=spec.get("dt", 1e-3), name=name)
+                params=params, steps=spec.get("steps", 1), dt=spec.get("dt", 1e-3),
+                name=name if species is None else f"{name} with D={D}")
 
 
 #: The measured workloads. Names state what each is.
