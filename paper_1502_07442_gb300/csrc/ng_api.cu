@@ -486,11 +486,11 @@ int ng_destroy(ng_ctx* c) {
     }
   }
   DevBuf* bufs[] = {&c->d_tab, &c->keys_a, &c->keys_b, &c->vals_a, &c->vals_b, &c->blockhist,
-                    &c->skeys, &c->perm, &c->spos, &c->smass, &c->stype, &c->body, &c->bleaf,
+                    &c->spos, &c->smass, &c->stype, &c->body, &c->bleaf,
                     &c->tperm, &c->scan_part, &c->n_level, &c->n_prefix, &c->n_first,
-                    &c->n_count, &c->n_child, &c->n_nchild, &c->n_tmp, &c->n_off, &c->n_m64,
+                    &c->n_count, &c->n_child, &c->n_nchild, &c->n_tmp, &c->n_m64,
                     &c->n_cnt, &c->n_geo, &c->n_com, &c->n_link, &c->n_mono, &c->groups, &c->gsize, &c->grank,
-                    &c->status, &c->counter, &c->acc_tmp, &c->aold, &c->io_pos, &c->io_vel, &c->io_type, &c->io_mass,
+                    &c->status, &c->counter, &c->aold, &c->io_pos, &c->io_vel, &c->io_type, &c->io_mass,
                     &c->io_acc, &c->lattice, &c->rho, &c->rhok, &c->phi,
                     &c->walk_desc, &c->walk_prefix};
   for (DevBuf* b : bufs) release(*b);

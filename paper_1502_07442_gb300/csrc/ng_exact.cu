@@ -67,18 +67,6 @@ struct ExactArgs {
   uint32_t* status;
 };
 
-__device__ __forceinline__ uint32_t xcompact3(uint64_t v) {
-  v &= 0x1249249249249249ull;
-  v = (v ^ (v >> 2)) & 0x10c30c30c30c30c3ull;
-  v = (v ^ (v >> 4)) & 0x100f00f00f00f00full;
-  v = (v ^ (v >> 8)) & 0x1f0000ff0000ffull;
-  v = (v ^ (v >> 16)) & 0x1f00000000ffffull;
-  v = (v ^ (v >> 32)) & 0x1fffffull;
-  return (uint32_t)v;
-}
-
-__device__ __forceinline__ double ximage(double d) { return __dsub_rn(d, rint(d)); }
-
 constexpr int kExactStack = 192;
 
 // One term: passive species s of mass mp, active species t of mass M behind
@@ -169,15 +157,15 @@ __global__ void __launch_bounds__(128) k_walk_exact(ExactArgs a) {
       const uint32_t nd = stack[--sp];
       const uint64_t pre = a.prefix[nd];
       const double side = 1.0 / (double)(1u << a.level[nd]);
-      const double c[3] = {((double)xcompact3(pre >> 2) + 0.5) * side,
-                           ((double)xcompact3(pre >> 1) + 0.5) * side,
-                           ((double)xcompact3(pre) + 0.5) * side};
+      const double c[3] = {((double)morton_compact3(pre >> 2) + 0.5) * side,
+                           ((double)morton_compact3(pre >> 1) + 0.5) * side,
+                           ((double)morton_compact3(pre) + 0.5) * side};
       const double half = __dmul_rn(0.5, side);
       double g2 = 0.0, dcs[3];
       bool inside = true;
 #pragma unroll
       for (int e = 0; e < 3; ++e) {
-        const double dc = ximage(__dsub_rn(c[e], x[e]));
+        const double dc = nearest_image_unit(__dsub_rn(c[e], x[e]));
         dcs[e] = dc;
         double gap = __dsub_rn(fabs(dc), half);
         gap = gap > 0.0 ? gap : 0.0;
@@ -199,7 +187,7 @@ __global__ void __launch_bounds__(128) k_walk_exact(ExactArgs a) {
         double dd2 = 0.0;
 #pragma unroll
         for (int e = 0; e < 3; ++e) {
-          const double v = ximage(__dsub_rn(com[e], x[e]));
+          const double v = nearest_image_unit(__dsub_rn(com[e], x[e]));
           dd2 = __dadd_rn(dd2, __dmul_rn(v, v));
         }
         bool accept;
@@ -220,9 +208,9 @@ __global__ void __launch_bounds__(128) k_walk_exact(ExactArgs a) {
           for (int t = 0; t < a.D; ++t) {
             const double* m = a.m64 + ((size_t)nd * a.D + t) * 4;
             if (!(m[0] > 0.0)) continue;
-            const double d[3] = {ximage(__dsub_rn(m[1] / m[0], x[0])) * a.L,
-                                 ximage(__dsub_rn(m[2] / m[0], x[1])) * a.L,
-                                 ximage(__dsub_rn(m[3] / m[0], x[2])) * a.L};
+            const double d[3] = {nearest_image_unit(__dsub_rn(m[1] / m[0], x[0])) * a.L,
+                                 nearest_image_unit(__dsub_rn(m[2] / m[0], x[1])) * a.L,
+                                 nearest_image_unit(__dsub_rn(m[3] / m[0], x[2])) * a.L};
             exact_term(a, s, t, (float)m[0], (float)a.cnt[(size_t)nd * a.D + t], mp, d, ax, ay,
                        az);
             ++cnt;
@@ -234,9 +222,9 @@ __global__ void __launch_bounds__(128) k_walk_exact(ExactArgs a) {
         const uint32_t f = a.first[nd], c2 = a.count[nd];
         for (uint32_t b = f; b < f + c2; ++b) {
           if ((int64_t)b == k) continue;
-          const double d[3] = {ximage(__dsub_rn(a.spos[b] * a.invL, x[0])) * a.L,
-                               ximage(__dsub_rn(a.spos[a.n + b] * a.invL, x[1])) * a.L,
-                               ximage(__dsub_rn(a.spos[2 * a.n + b] * a.invL, x[2])) * a.L};
+          const double d[3] = {nearest_image_unit(__dsub_rn(a.spos[b] * a.invL, x[0])) * a.L,
+                               nearest_image_unit(__dsub_rn(a.spos[a.n + b] * a.invL, x[1])) * a.L,
+                               nearest_image_unit(__dsub_rn(a.spos[2 * a.n + b] * a.invL, x[2])) * a.L};
           exact_term(a, s, a.stype[b], a.smass[b], 1.f, mp, d, ax, ay, az);
           ++cnt;
         }

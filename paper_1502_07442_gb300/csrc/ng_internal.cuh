@@ -50,6 +50,21 @@ constexpr int kWalkMaxWarps = 32;
 // Warps per walk block by species count: as many as the per-warp lists and a
 // 64 KB law table leave room for in 227 KB of shared memory; the register
 // budget follows (65536 / threads).
+// Every third bit of v, from bit 0, packed into the low 21 bits: one axis
+// of a Morton key or node prefix (x from v >> 2, y from v >> 1, z from v).
+__device__ __forceinline__ uint32_t morton_compact3(uint64_t v) {
+  v &= 0x1249249249249249ull;
+  v = (v ^ (v >> 2)) & 0x10c30c30c30c30c3ull;
+  v = (v ^ (v >> 4)) & 0x100f00f00f00f00full;
+  v = (v ^ (v >> 8)) & 0x1f0000ff0000ffull;
+  v = (v ^ (v >> 16)) & 0x1f00000000ffffull;
+  v = (v ^ (v >> 32)) & 0x1fffffull;
+  return (uint32_t)v;
+}
+
+// A box-unit offset wrapped to its nearest periodic image, rounded once.
+__device__ __forceinline__ double nearest_image_unit(double d) { return __dsub_rn(d, rint(d)); }
+
 __host__ __device__ constexpr int walk_warps(int D) { return D <= 3 ? 24 : D == 4 ? 24 : D == 5 ? 20 : 16; }
 
 // Per-simulation inputs of the walk (device memory, one per simulation).
@@ -119,13 +134,12 @@ struct ng_ctx {
   int64_t n = 0;
   bool built = false;
   ng::DevBuf keys_a, keys_b, vals_a, vals_b, blockhist;
-  ng::DevBuf skeys, perm, spos, smass, stype, body, bleaf, tperm, scan_part;
-  int64_t toffs[ng::kMaxD + 1]{};
+  ng::DevBuf spos, smass, stype, body, bleaf, tperm, scan_part;
 
   // tree
   int64_t cap_nodes = 0, nnodes = 0;
   int64_t ngroups = 0, ngroups_n = -1;   // walk groups of the last checked build, for n = ngroups_n
-  ng::DevBuf n_level, n_prefix, n_first, n_count, n_child, n_nchild, n_tmp, n_off;
+  ng::DevBuf n_level, n_prefix, n_first, n_count, n_child, n_nchild, n_tmp;
   ng::DevBuf n_m64, n_cnt, n_geo, n_com, n_link, n_mono;
   ng::DevBuf groups;
   ng::DevBuf gsize, grank;          // group size at its first body, rank of each group start
@@ -137,7 +151,6 @@ struct ng_ctx {
   int lattice_grid = 0;  // N of the lattice tables (0: none)
   ng::DevBuf aold;       // float[n] |previous acceleration| per body (caller order)
   int64_t aold_n = -1;   // bodies aold holds (-1: none)
-  ng::DevBuf acc_tmp;    // float[3][n] scratch for summing short + long
 
   // PM: cuFFT plans cached per (mesh, species count); a context reused for
   // requests of other sizes keeps its plans
@@ -225,7 +238,6 @@ int type_order(ng_ctx* c);
 int build_tables(ng_ctx* c);
 double short_law_factor(int law, double a, double l, double rs, double rho);
 
-int device_grid(ng_ctx* c, int per_sm);
 // Blocks of 256 threads for a grid-stride kernel over `items` items: enough
 // to cover them, at most per_sm blocks per SM, at least one.
 int work_grid(ng_ctx* c, int64_t items, int per_sm);

@@ -316,7 +316,6 @@ __global__ void k_iota(int64_t n, uint32_t* out) {
     out[k] = (uint32_t)k;
 }
 
-int device_grid(ng_ctx* c, int per_sm) { return c->nsm * per_sm; }
 
 int work_grid(ng_ctx* c, int64_t items, int per_sm) {
   const int64_t need = (items + 255) / 256;

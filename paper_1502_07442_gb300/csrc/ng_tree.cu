@@ -185,22 +185,12 @@ int build_octree(ng_ctx* c) {
 
 // --------------------------------------------------------- monopoles
 
-__device__ __forceinline__ uint32_t compact3(uint64_t v) {
-  v &= 0x1249249249249249ull;
-  v = (v ^ (v >> 2)) & 0x10c30c30c30c30c3ull;
-  v = (v ^ (v >> 4)) & 0x100f00f00f00f00full;
-  v = (v ^ (v >> 8)) & 0x1f0000ff0000ffull;
-  v = (v ^ (v >> 16)) & 0x1f00000000ffffull;
-  v = (v ^ (v >> 32)) & 0x1fffffull;
-  return (uint32_t)v;
-}
-
 // Centre (box units) of a node from its level and Morton prefix.
 __device__ __forceinline__ void node_centre(int lvl, uint64_t pre, double c[3], double* side) {
   const double s = 1.0 / (double)(1u << lvl);
-  c[0] = ((double)compact3(pre >> 2) + 0.5) * s;
-  c[1] = ((double)compact3(pre >> 1) + 0.5) * s;
-  c[2] = ((double)compact3(pre) + 0.5) * s;
+  c[0] = ((double)morton_compact3(pre >> 2) + 0.5) * s;
+  c[1] = ((double)morton_compact3(pre >> 1) + 0.5) * s;
+  c[2] = ((double)morton_compact3(pre) + 0.5) * s;
   *side = s;
 }
 

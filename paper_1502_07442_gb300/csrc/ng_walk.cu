@@ -619,18 +619,6 @@ struct CountArgs {
   int relative;
 };
 
-__device__ __forceinline__ uint32_t compact3c(uint64_t v) {
-  v &= 0x1249249249249249ull;
-  v = (v ^ (v >> 2)) & 0x10c30c30c30c30c3ull;
-  v = (v ^ (v >> 4)) & 0x100f00f00f00f00full;
-  v = (v ^ (v >> 8)) & 0x1f0000ff0000ffull;
-  v = (v ^ (v >> 16)) & 0x1f00000000ffffull;
-  v = (v ^ (v >> 32)) & 0x1fffffull;
-  return (uint32_t)v;
-}
-
-__device__ __forceinline__ double min_image_d(double d) { return __dsub_rn(d, rint(d)); }
-
 constexpr int kCountStack = 192;
 
 __global__ void __launch_bounds__(128) k_count(CountArgs a) {
@@ -654,15 +642,15 @@ __global__ void __launch_bounds__(128) k_count(CountArgs a) {
       const int lvl = a.level[nd];
       const uint64_t pre = a.prefix[nd];
       const double side = 1.0 / (double)(1u << lvl);
-      const double c[3] = {((double)compact3c(pre >> 2) + 0.5) * side,
-                           ((double)compact3c(pre >> 1) + 0.5) * side,
-                           ((double)compact3c(pre) + 0.5) * side};
+      const double c[3] = {((double)morton_compact3(pre >> 2) + 0.5) * side,
+                           ((double)morton_compact3(pre >> 1) + 0.5) * side,
+                           ((double)morton_compact3(pre) + 0.5) * side};
       const double half = __dmul_rn(0.5, side);
       double g2 = 0.0, dcs[3];
       bool inside = true;
 #pragma unroll
       for (int e = 0; e < 3; ++e) {
-        const double dc = min_image_d(__dsub_rn(c[e], x[e]));
+        const double dc = nearest_image_unit(__dsub_rn(c[e], x[e]));
         dcs[e] = dc;
         double gap = __dsub_rn(fabs(dc), half);
         gap = gap > 0.0 ? gap : 0.0;
@@ -686,7 +674,7 @@ __global__ void __launch_bounds__(128) k_count(CountArgs a) {
         double dd2 = 0.0;
 #pragma unroll
         for (int e = 0; e < 3; ++e) {
-          const double v = min_image_d(__dsub_rn(com[e], x[e]));
+          const double v = nearest_image_unit(__dsub_rn(com[e], x[e]));
           dd2 = __dadd_rn(dd2, __dmul_rn(v, v));
         }
         bool accept;
