@@ -258,16 +258,20 @@ __global__ void __launch_bounds__(walk_warps(D) * 32, 1) k_walk(WalkLaunch L) {
         // ---- one chunk of up to 32 queued leaf bodies into the lists of their species
         const int f = qdone + lane;
         const bool has = f < qtotal;
+        // leaf holding queued body f: the number of leaf starts <= f, minus
+        // one. Lane j holds the start of leaf j; the starts inside this chunk
+        // become one bit mask, those before it one count (no search)
+        const int sj = lane < nl ? ws->leafo[lane] : 0x7fffffff;
+        const uint32_t starts = __reduce_or_sync(
+            0xffffffffu, sj >= qdone && sj < qdone + 32 ? 1u << (sj - qdone) : 0u);
+        const int before = __popc(__ballot_sync(0xffffffffu, sj < qdone));
+        const uint32_t upto = lane == 31 ? 0xffffffffu : (2u << lane) - 1u;
+        const int lo = before + __popc(starts & upto) - 1;
+        const int lstart = __shfl_sync(0xffffffffu, sj, lo & 31);
         float4 rec = make_float4(0.f, 0.f, 0.f, 0.f);
         int bt = -1;
         if (has) {
-          // leaf holding queued body f: last leaf whose prefix is <= f
-          int lo = 0, hi = nl - 1;
-          while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (ws->leafo[mid] <= f) lo = mid; else hi = mid - 1;
-          }
-          const int b = ws->leafb[lo].x + (f - ws->leafo[lo]);
+          const int b = ws->leafb[lo].x + (f - lstart);
           const float4 lc4 = ws->leafc[lo];
           const float4 bb = DESC(body)[b];
           const float px = lc4.x + bb.x, py = lc4.y + bb.y, pz = lc4.z + bb.z;
