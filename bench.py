@@ -99,6 +99,8 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--n", type=int, default=None, help="override N (smaller test runs)")
+    ap.add_argument("--acc64", action="store_true",
+                    help="the FP64-accumulated walk variant (per-body sums in FP64)")
     ap.add_argument("--species", type=int, default=None,
                     help="override the species count D (the paper's 1/D scaling)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline leg")
@@ -244,7 +246,8 @@ def workload_config(w, args):
             "leaf_size": int(prm["leaf_size"]), "dt": float(w["dt"]),
             "step": "KDK: kick, drift, sort, octree, monopoles, PM, group walk, kick",
             "l2": "inputs larger than L2 (particle state and tree >> 129 MB, no flush)",
-            "parallelism": f"replicas{args.gpus}"}
+            "parallelism": f"replicas{args.gpus}",
+            "accumulation": "fp64 per-body sums" if prm.get("accumulate_fp64") else "fp32"}
 
 
 def main():
@@ -285,6 +288,8 @@ def main():
         w["params"] = dict(w["params"], leaf_size=best["leaf_size"], group_cell=best["group_cell"])
         tuned = {"leaf_size": best["leaf_size"], "group_cell": best["group_cell"],
                  "trials": len(trials), "build_plus_walk_ms": round(best["ms"], 2)}
+    if args.acc64:
+        w["params"] = dict(w["params"], accumulate_fp64=1)
     sim = ng.Simulation(ng.params_from_workload(w["params"]), stream)
     dt = float(w["dt"])
 
@@ -340,7 +345,8 @@ def main():
     med = clocks.get("sm_mhz") or 2070.0
     roofline = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 2),
                 "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
-                "traffic": walk_traffic(args.workload, args.n if args.species is None else -1,
+                "traffic": walk_traffic(args.workload,
+                                        args.n if args.species is None and not args.acc64 else -1,
                                         int(w["params"]["leaf_size"]),
                                         int(w["params"].get("group_cell", 0) or 32)),
                 "kernel": "k_walk", "walk_ms": round(walk, 3),

@@ -104,6 +104,9 @@ enum { NG_OPEN_GEOMETRIC = 0, NG_OPEN_RELATIVE = 1 };
  *  ignore_nperp   1: Mahalo monopoles are treated as single objects (N_perp = 1),
  *                 the "without tracking" comparison of Sec. 3.3.
  *  beta           Mahalo scale beta (> 0 when a Mahalo law is used).
+ *  accumulate_fp64  1: the group walk adds each evaluated list's FP32 sum into
+ *                 an FP64 per-body accumulator (the FP64-accumulated variant);
+ *                 0: FP32 accumulation throughout (default).
  *  leaf_size      maximum bodies per tree leaf (1..64, 0 = 8).
  *  group_size     particles per walk group (32 or 64, 0 = 32).
  *  table_size     short-range table entries per law (0 = automatic).
@@ -133,6 +136,8 @@ typedef struct {
   int32_t pure_tree;
   int32_t ignore_nperp;
   double beta;
+  int32_t accumulate_fp64;
+  int32_t reserved2;   /* must be 0 */
 } ng_params;
 
 typedef struct ng_ctx ng_ctx;

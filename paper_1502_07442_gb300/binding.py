@@ -39,6 +39,7 @@ class NgParams(ctypes.Structure):
         ("rcut_over_rs", ctypes.c_double), ("theta", ctypes.c_double),
         ("opening", ctypes.c_int32), ("reserved1", ctypes.c_int32), ("alpha", ctypes.c_double),
         ("pure_tree", ctypes.c_int32), ("ignore_nperp", ctypes.c_int32), ("beta", ctypes.c_double),
+        ("accumulate_fp64", ctypes.c_int32), ("reserved2", ctypes.c_int32),
     ]
 
 
@@ -154,7 +155,8 @@ def _check(ctx, code):
 
 def make_params(D, G, *, eps, box=1.0, pm_mesh=0, asmth=1.25, rcut_over_rs=4.5, theta=0.5,
                 leaf_size=8, group_size=32, table_size=0, law=None, yuk_a=None, yuk_l=None,
-                group_cell=0, opening=0, alpha=0.0, pure_tree=0, ignore_nperp=0, beta=0.0):
+                group_cell=0, opening=0, alpha=0.0, pure_tree=0, ignore_nperp=0, beta=0.0,
+                accumulate_fp64=0):
     p = NgParams()
     p.D, p.pm_mesh, p.leaf_size, p.group_size, p.table_size = (int(D), int(pm_mesh), int(leaf_size),
                                                                int(group_size), int(table_size))
@@ -163,6 +165,7 @@ def make_params(D, G, *, eps, box=1.0, pm_mesh=0, asmth=1.25, rcut_over_rs=4.5, 
     p.group_cell = int(group_cell)
     p.opening, p.reserved1, p.alpha = int(opening), 0, float(alpha)
     p.pure_tree, p.ignore_nperp, p.beta = int(pure_tree), int(ignore_nperp), float(beta)
+    p.accumulate_fp64, p.reserved2 = int(accumulate_fp64), 0
     G = np.asarray(G, np.float64)
     law = np.zeros((D, D), np.int32) if law is None else np.asarray(law, np.int32)
     ya = np.zeros((D, D)) if yuk_a is None else np.asarray(yuk_a, np.float64)
@@ -190,7 +193,7 @@ def params_from_workload(w: dict, **over) -> NgParams:
                        table_size=q.get("table_size", 0), group_cell=q.get("group_cell", 0),
                        opening=q.get("opening", 0), alpha=q.get("alpha", 0.0),
                        pure_tree=q.get("pure_tree", 0), ignore_nperp=q.get("ignore_nperp", 0),
-                       beta=q.get("beta", 0.0))
+                       beta=q.get("beta", 0.0), accumulate_fp64=q.get("accumulate_fp64", 0))
 
 
 def _ptr(t):

@@ -348,6 +348,9 @@ int validate(ng_ctx* c, const ng_params* p) {
   if (p->opening != NG_OPEN_GEOMETRIC && p->opening != NG_OPEN_RELATIVE)
     return fail(c, NG_EINVAL, "opening must be NG_OPEN_GEOMETRIC or NG_OPEN_RELATIVE");
   if (p->reserved1 != 0) return fail(c, NG_EINVAL, "reserved1 must be 0");
+  if (p->reserved2 != 0) return fail(c, NG_EINVAL, "reserved2 must be 0");
+  if (p->accumulate_fp64 != 0 && p->accumulate_fp64 != 1)
+    return fail(c, NG_EINVAL, "accumulate_fp64 must be 0 or 1");
   if (p->pure_tree < 0 || p->pure_tree > 2) return fail(c, NG_EINVAL, "pure_tree must be 0, 1 or 2");
   if (p->ignore_nperp != 0 && p->ignore_nperp != 1)
     return fail(c, NG_EINVAL, "ignore_nperp must be 0 or 1");

@@ -24,6 +24,8 @@
 // cut-off); the force is m * value * inv^3 * d, summed over one species list;
 // each list's sum is scaled by the coupling G[s][t] of the body's species s
 // and the list's species t and added to one accumulator per body.
+#include <type_traits>
+
 #include "ng_internal.cuh"
 
 namespace ng {
@@ -78,8 +80,11 @@ __device__ __forceinline__ float2 lds_f2(uint32_t addr) {
 // memory into shared memory and reads the fields from there.
 #define DESC(f) (ws->desc.f)
 
-template <int D>
+// ACC64: the FP64-accumulated variant (each evaluated list's FP32 sum is
+// added into an FP64 per-body accumulator); otherwise FP32 throughout.
+template <int D, bool ACC64>
 __global__ void __launch_bounds__(walk_warps(D) * 32, 1) k_walk(WalkLaunch L) {
+  using Acc = typename std::conditional<ACC64, double, float>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2* tab = reinterpret_cast<float2*>(smem_raw);
   const int ntab = L.nlaws * L.tab_entries;
@@ -169,7 +174,7 @@ __global__ void __launch_bounds__(walk_warps(D) * 32, 1) k_walk(WalkLaunch L) {
     const float yr = (wrap_unit(lg.y - oy) + bd.y) * s_tab;
     const float zr = (wrap_unit(lg.z - oz) + bd.z) * s_tab;
 
-    float ax = 0.f, ay = 0.f, az = 0.f;
+    Acc ax = 0, ay = 0, az = 0;   // per-body accumulator
     int lc[D];                      // records per species list (same in every lane)
 #pragma unroll
     for (int t = 0; t < D; ++t) lc[t] = 0;
@@ -244,9 +249,15 @@ __global__ void __launch_bounds__(walk_warps(D) * 32, 1) k_walk(WalkLaunch L) {
           const float sx = sx2.x + sx2.y, sy = sy2.x + sy2.y, sz = sz2.x + sz2.y;
           __syncwarp();
           const float G = DESC(G[s][t]);
-          ax = fmaf(G, sx, ax);
-          ay = fmaf(G, sy, ay);
-          az = fmaf(G, sz, az);
+          if constexpr (ACC64) {
+            ax = fma((double)G, (double)sx, ax);
+            ay = fma((double)G, (double)sy, ay);
+            az = fma((double)G, (double)sz, az);
+          } else {
+            ax = fmaf(G, sx, ax);
+            ay = fmaf(G, sy, ay);
+            az = fmaf(G, sz, az);
+          }
 #pragma unroll
           for (int q = 0; q < D; ++q) lc[q] = (q == t) ? 0 : lc[q];
           nint += (unsigned long long)cnt * (unsigned long long)nact;
@@ -418,13 +429,11 @@ __global__ void __launch_bounds__(walk_warps(D) * 32, 1) k_walk(WalkLaunch L) {
       continue;
     }
     if (active) {
-      float fx = ax, fy = ay, fz = az;
+      const Acc sc = (Acc)DESC(out_scale);
+      const float fx = (float)(ax * sc), fy = (float)(ay * sc), fz = (float)(az * sc);
       const uint32_t i = DESC(perm)[p];
       float* acc = DESC(acc);
       const int64_t nb = DESC(n);
-      fx *= DESC(out_scale);
-      fy *= DESC(out_scale);
-      fz *= DESC(out_scale);
       if (DESC(accumulate)) {
         acc[i] += fx;
         acc[nb + i] += fy;
@@ -486,7 +495,7 @@ static size_t walk_smem(int nlaws, int entries, int nwarps) {
   return tab_bytes + (size_t)nwarps * sizeof(WarpSmem<D>);
 }
 
-template <int D>
+template <int D, bool ACC64>
 static int launch_walk_d(ng_ctx* c, cudaStream_t stream, const WalkLaunch& L, int64_t groups) {
   int nwarps = walk_warps(D);
   while (nwarps > 1 && walk_smem<D>(L.nlaws, L.tab_entries, nwarps) > c->smem_optin) --nwarps;
@@ -495,17 +504,17 @@ static int launch_walk_d(ng_ctx* c, cudaStream_t stream, const WalkLaunch& L, in
     return fail(c, NG_ENOMEM, "walk needs %zu B shared memory (max %zu)", smem, c->smem_optin);
   // the attribute is a per-function ceiling shared by every thread that
   // launches the walk: always raise it to the device maximum, never lower it
-  NG_CUDA(c, cudaFuncSetAttribute(k_walk<D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  NG_CUDA(c, cudaFuncSetAttribute(k_walk<D, ACC64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)c->smem_optin));
   int per_sm = 0;
-  NG_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walk<D>, nwarps * 32,
+  NG_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walk<D, ACC64>, nwarps * 32,
                                                            smem));
   if (per_sm < 1) per_sm = 1;
   // persistent warps take groups from a counter: no more blocks than the
   // expected groups need, so small problems leave SMs to concurrent work
   const int64_t want = (std::max<int64_t>(groups, 1) + nwarps - 1) / nwarps;
   const int grid = (int)std::min<int64_t>((int64_t)c->nsm * per_sm, want);
-  k_walk<D><<<grid, nwarps * 32, smem, stream>>>(L);
+  k_walk<D, ACC64><<<grid, nwarps * 32, smem, stream>>>(L);
   c->launches += 1;
   NG_CUDA(c, cudaGetLastError());
   return NG_OK;
@@ -540,15 +549,21 @@ void fill_walk_desc(ng_ctx* c, float* acc, bool accumulate, WalkDesc* d) {
   d->rel_scale = (float)(c->p.alpha * c->L * c->L / coupling_max(c));
 }
 
-static int dispatch_walk(ng_ctx* c, cudaStream_t stream, const WalkLaunch& L, int64_t groups) {
+template <bool ACC64>
+static int dispatch_walk_acc(ng_ctx* c, cudaStream_t stream, const WalkLaunch& L, int64_t groups) {
   switch (c->p.D) {
-    case 1: return launch_walk_d<1>(c, stream, L, groups);
-    case 2: return launch_walk_d<2>(c, stream, L, groups);
-    case 3: return launch_walk_d<3>(c, stream, L, groups);
-    case 4: return launch_walk_d<4>(c, stream, L, groups);
-    case 5: return launch_walk_d<5>(c, stream, L, groups);
-    default: return launch_walk_d<6>(c, stream, L, groups);
+    case 1: return launch_walk_d<1, ACC64>(c, stream, L, groups);
+    case 2: return launch_walk_d<2, ACC64>(c, stream, L, groups);
+    case 3: return launch_walk_d<3, ACC64>(c, stream, L, groups);
+    case 4: return launch_walk_d<4, ACC64>(c, stream, L, groups);
+    case 5: return launch_walk_d<5, ACC64>(c, stream, L, groups);
+    default: return launch_walk_d<6, ACC64>(c, stream, L, groups);
   }
+}
+
+static int dispatch_walk(ng_ctx* c, cudaStream_t stream, const WalkLaunch& L, int64_t groups) {
+  return c->p.accumulate_fp64 ? dispatch_walk_acc<true>(c, stream, L, groups)
+                              : dispatch_walk_acc<false>(c, stream, L, groups);
 }
 
 int64_t walk_groups_hint(const ng_ctx* c) {

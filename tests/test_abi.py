@@ -40,16 +40,17 @@ def test_header_functions_are_exported(binding):
 def test_params_layout_matches_c(binding, tmp_path):
     src = tmp_path / "sz.c"
     src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "ngravs.h"\n'
-                   'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(ng_params),'
+                   'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(ng_params),'
                    ' offsetof(ng_params,G), offsetof(ng_params,law), offsetof(ng_params,eps),'
                    ' offsetof(ng_params,theta), offsetof(ng_params,opening), offsetof(ng_params,alpha),'
-                   ' offsetof(ng_params,pure_tree), offsetof(ng_params,beta));return 0;}\n')
+                   ' offsetof(ng_params,pure_tree), offsetof(ng_params,beta), offsetof(ng_params,accumulate_fp64));return 0;}\n')
     exe = tmp_path / "sz"
     subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
     got = list(map(int, subprocess.check_output([str(exe)]).split()))
     P = binding.NgParams
     want = [ctypes.sizeof(P), P.G.offset, P.law.offset, P.eps.offset, P.theta.offset,
-            P.opening.offset, P.alpha.offset, P.pure_tree.offset, P.beta.offset]
+            P.opening.offset, P.alpha.offset, P.pure_tree.offset, P.beta.offset,
+            P.accumulate_fp64.offset]
     assert got == want
 
 
@@ -57,6 +58,7 @@ def test_params_layout_matches_c(binding, tmp_path):
     ("D", 0, "D=0"), ("D", 7, "D=7"), ("eps", 0.0, "eps"), ("box", -1.0, "box"),
     ("pm_mesh", 48, "pm_mesh"), ("leaf_size", 65, "leaf_size"), ("theta", -0.1, "theta"),
     ("rcut_over_rs", 1000.0, "r_cut"), ("opening", 2, "opening"), ("reserved1", 1, "reserved1"),
+    ("accumulate_fp64", 2, "accumulate_fp64"), ("reserved2", 1, "reserved2"),
     ("pure_tree", 1, "pm_mesh"), ("pure_tree", 3, "pure_tree"), ("ignore_nperp", 3, "ignore_nperp"),
 ])
 def test_create_rejects_bad_params(binding, field, value, needle):

@@ -122,4 +122,4 @@ def test_fullsize_pm_2m(ng):
     ref = oracle.pm(oracle_params(prm), w["pos"], w["type"], w["mass"])
     rms = np.sqrt(np.mean(np.sum(ref ** 2, axis=0)))
     err = np.linalg.norm(got - ref, axis=0) / rms
-    assert err.max() <= 2e-4, (err.max(), err.mean())
+    assert err.max() <= 1e-5, (err.max(), err.mean())
