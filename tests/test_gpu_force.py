@@ -51,11 +51,19 @@ def _short_force(ng, prm, w, count=False):
     return (out, nint) if count else out
 
 
+def _sparse_species(n, seed):
+    """D = 6 with only species 0 and 5 present: four species without bodies."""
+    w = small_clustered(n, 6, seed)
+    w["type"] = np.where(w["type"] < 3, 0, 5).astype(np.uint8)
+    return w
+
+
 DIRECT_CASES = [
     ("cfg0", lambda: inputs.workload("uniform4k_d2_newton")),
     ("clustered_d3_yukawa", lambda: small_clustered(20000, 3, 51, yukawa=True)),
     ("clustered_d6", lambda: small_clustered(12000, 6, 52)),
     ("uniform_d1_ragged", lambda: small_clustered(1000 + 17, 1, 53)),
+    ("d6_two_species_present", lambda: _sparse_species(8000, 56)),
 ]
 
 
@@ -78,6 +86,7 @@ TREE_CASES = [
     ("cfg0", lambda: inputs.workload("uniform4k_d2_newton")),
     ("clustered_d4_yukawa", lambda: small_clustered(30000, 4, 54, yukawa=True)),
     ("clustered_d2", lambda: small_clustered(30000, 2, 55)),
+    ("d6_two_species_present", lambda: _sparse_species(20000, 57)),
 ]
 
 
@@ -115,6 +124,7 @@ PM_CASES = [
     ("cfg0", lambda: inputs.workload("uniform4k_d2_newton")),
     ("clustered_d4_yukawa_m64", lambda: small_clustered(30000, 4, 57, yukawa=True, mesh=64)),
     ("clustered_d5_m32", lambda: small_clustered(9000, 5, 58, mesh=32)),
+    ("d6_two_species_present", lambda: _sparse_species(8000, 59)),
 ]
 
 
