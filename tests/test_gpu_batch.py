@@ -52,9 +52,15 @@ def _rel_change(got, want, start):
     return np.linalg.norm(d, axis=0) / np.maximum(np.linalg.norm(m, axis=0), 1e-300)
 
 
-def test_batch_matches_each_simulation_alone(ng):
+@pytest.mark.parametrize("variant", [{}, {"opening": 1, "alpha": 0.005}, {"accumulate_fp64": 1}],
+                         ids=["geometric", "relative", "fp64_accumulated"])
+def test_batch_matches_each_simulation_alone(ng, variant):
+    """Also with the relative criterion (|a_old| refreshed inside the captured
+    batch step) and with the FP64-accumulated walk."""
     import torch
     sims = _sims()
+    for w in sims:
+        w["params"] = dict(w["params"], **variant)
     steps, dt = 3, 1e-3
     alone = []
     for w in sims:
