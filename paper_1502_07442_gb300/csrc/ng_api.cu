@@ -807,7 +807,7 @@ int ng_type_order(ng_ctx* c, int64_t* type_offsets, uint32_t* order_out) {
   if (!c) return NG_EINVAL;
   if (!c->built) return fail(c, NG_ESTATE, "no tree built");
   const int64_t n = c->n;
-  const int nblocks = (int)((n + 4095) / 4096);
+  const int nblocks = (int)((n + kRadixTile - 1) / kRadixTile);
   if (type_offsets) {
     NG_CUDA(c, cudaStreamSynchronize(c->stream));
     for (int d = 0; d < c->p.D; ++d) {

@@ -65,6 +65,10 @@ __device__ __forceinline__ uint32_t morton_compact3(uint64_t v) {
 // A box-unit offset wrapped to its nearest periodic image, rounded once.
 __device__ __forceinline__ double nearest_image_unit(double d) { return __dsub_rn(d, rint(d)); }
 
+// Keys per block of the radix sort; the per-block digit histograms (and the
+// type offsets read back from the last pass's) are laid out by it.
+constexpr int kRadixTile = 2048;
+
 __host__ __device__ constexpr int walk_warps(int D) { return D <= 3 ? 24 : D == 4 ? 24 : D == 5 ? 20 : 16; }
 
 // Per-simulation inputs of the walk (device memory, one per simulation).

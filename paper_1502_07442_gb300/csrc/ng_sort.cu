@@ -206,9 +206,10 @@ __global__ void k_keys(int64_t n, const double* __restrict__ pos, const uint8_t*
 // ---------------------------------------------------------- radix sort
 
 constexpr int kRsThreads = 256;
-constexpr int kRsItems = 16;                       // keys per lane
+constexpr int kRsItems = 8;                        // keys per lane
 constexpr int kRsWarps = kRsThreads / 32;
-constexpr int kRsTile = kRsThreads * kRsItems;     // 4096 keys per block
+constexpr int kRsTile = kRsThreads * kRsItems;     // 2048 keys per block
+static_assert(kRsTile == kRadixTile, "radix tile and histogram layout disagree");
 
 __global__ void __launch_bounds__(kRsThreads)
 k_rs_hist(const uint64_t* __restrict__ keys, int64_t n, int shift, uint32_t mask,
@@ -225,17 +226,25 @@ k_rs_hist(const uint64_t* __restrict__ keys, int64_t n, int shift, uint32_t mask
   hist[(int64_t)threadIdx.x * nblocks + blockIdx.x] = cnt[threadIdx.x];
 }
 
-// Stable scatter of one digit: each warp ranks its contiguous sub-tile in
-// order (match_any groups equal digits), warps are then ordered per digit.
+// Stable scatter of one digit. Each warp ranks its contiguous sub-tile in
+// order (match_any groups equal digits); warps are ordered per digit. The
+// tile is then reordered by digit in shared memory and written out by
+// consecutive threads, so each digit's run of the tile (16 keys on average)
+// leaves as one contiguous segment instead of one sector per key.
 __global__ void __launch_bounds__(kRsThreads)
 k_rs_scatter(const uint64_t* __restrict__ kin, const uint32_t* __restrict__ vin,
              uint64_t* __restrict__ kout, uint32_t* __restrict__ vout, int64_t n, int shift,
              uint32_t mask, const uint32_t* __restrict__ offs, int nblocks) {
-  __shared__ uint32_t wcnt[kRsWarps][256];
+  __shared__ uint32_t wcnt[kRsWarps][256];   // per warp and digit: count, then tile position
+  __shared__ uint32_t dstart[256];           // tile position of each digit's run
+  __shared__ uint32_t gdst[256];             // global position of each digit's run
+  __shared__ uint64_t tk[kRsTile];
+  __shared__ uint32_t tv[kRsTile];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   for (int j = threadIdx.x; j < kRsWarps * 256; j += kRsThreads) (&wcnt[0][0])[j] = 0;
   __syncthreads();
-  const int64_t sub0 = (int64_t)blockIdx.x * kRsTile + (int64_t)w * (kRsTile / kRsWarps);
+  const int64_t t0 = (int64_t)blockIdx.x * kRsTile;
+  const int64_t sub0 = t0 + (int64_t)w * (kRsTile / kRsWarps);
   const uint32_t lt = (1u << lane) - 1u;
   uint64_t k[kRsItems];
   uint32_t v[kRsItems], rank[kRsItems];
@@ -256,11 +265,30 @@ k_rs_scatter(const uint64_t* __restrict__ kin, const uint32_t* __restrict__ vin,
   }
   __syncthreads();
   {
-    uint32_t run = offs[(int64_t)threadIdx.x * nblocks + blockIdx.x];
+    // thread d: the digit's total in the tile, its run's tile start (block
+    // scan over digits) and the warps' positions inside the run
+    const int d = threadIdx.x;
+    uint32_t total = 0;
+#pragma unroll
+    for (int ww = 0; ww < kRsWarps; ++ww) total += wcnt[ww][d];
+    uint32_t incl = total;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    __shared__ uint32_t wsum[kRsWarps];
+    if (lane == 31) wsum[w] = incl;
+    __syncthreads();
+    uint32_t wbase = 0;
+    for (int ww = 0; ww < w; ++ww) wbase += wsum[ww];
+    uint32_t run = wbase + incl - total;
+    dstart[d] = run;
+    gdst[d] = offs[(int64_t)d * nblocks + blockIdx.x];
 #pragma unroll
     for (int ww = 0; ww < kRsWarps; ++ww) {
-      const uint32_t t = wcnt[ww][threadIdx.x];
-      wcnt[ww][threadIdx.x] = run;
+      const uint32_t t = wcnt[ww][d];
+      wcnt[ww][d] = run;
       run += t;
     }
   }
@@ -270,10 +298,19 @@ k_rs_scatter(const uint64_t* __restrict__ kin, const uint32_t* __restrict__ vin,
     const int64_t i = sub0 + it * 32 + lane;
     if (i < n) {
       const uint32_t d = (uint32_t)(k[it] >> shift) & mask;
-      const uint32_t dst = wcnt[w][d] + rank[it];
-      kout[dst] = k[it];
-      vout[dst] = v[it];
+      const uint32_t pos = wcnt[w][d] + rank[it];
+      tk[pos] = k[it];
+      tv[pos] = v[it];
     }
+  }
+  __syncthreads();
+  const int valid = (int)((n - t0) < kRsTile ? (n - t0) : kRsTile);
+  for (int p = threadIdx.x; p < valid; p += kRsThreads) {
+    const uint64_t key = tk[p];
+    const uint32_t d = (uint32_t)(key >> shift) & mask;
+    const uint32_t dst = gdst[d] + ((uint32_t)p - dstart[d]);
+    kout[dst] = key;
+    vout[dst] = tv[p];
   }
 }
 
