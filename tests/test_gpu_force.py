@@ -125,6 +125,8 @@ PM_CASES = [
     ("clustered_d4_yukawa_m64", lambda: small_clustered(30000, 4, 57, yukawa=True, mesh=64)),
     ("clustered_d5_m32", lambda: small_clustered(9000, 5, 58, mesh=32)),
     ("d6_two_species_present", lambda: _sparse_species(8000, 59)),
+    # more bodies than mesh points
+    ("clustered_d3_m16_dense", lambda: small_clustered(20000, 3, 60, mesh=16)),
 ]
 
 
