@@ -210,8 +210,11 @@ int batch_step_once(ng_batch* b, const int64_t* n, double* const* pos, float* co
     uint32_t* pre = as<uint32_t>(k.pre);
     int64_t groups = 0;
     for (int m : k.members) groups += walk_groups_hint(b->sims[m]);
+    bool rel = false;   // some member uses the relative criterion
+    for (const WalkDesc& h : k.h) rel = rel || h.aold != nullptr;
     if (r == NG_OK)
-      r = launch_walk_descs(rep, origin, as<WalkDesc>(k.d), nd, pre, pre + nd + 1, nullptr, groups);
+      r = launch_walk_descs(rep, origin, as<WalkDesc>(k.d), nd, pre, pre + nd + 1, nullptr, groups,
+                            rel);
     rep->stream = keep;
     if (r != NG_OK) return from_sim(b, k.members[0], r);
   }

@@ -221,7 +221,7 @@ void fill_walk_desc(ng_ctx* c, float* acc, bool accumulate, WalkDesc* d);
 int64_t walk_groups_hint(const ng_ctx* c);
 int launch_walk_descs(ng_ctx* c, cudaStream_t stream, const WalkDesc* d_descs, int ndesc,
                       uint32_t* d_prefix, uint32_t* d_work, unsigned long long* counter,
-                      int64_t groups);
+                      int64_t groups, bool rel);
 int launch_count(ng_ctx* c, int64_t* counts);  // per-particle walk counts
 // Pure tree mode: per-particle walk with the full laws (incl. Mahalo).
 int launch_walk_exact(ng_ctx* c, float* acc, bool accumulate, bool count);

@@ -82,7 +82,9 @@ __device__ __forceinline__ float2 lds_f2(uint32_t addr) {
 
 // ACC64: the FP64-accumulated variant (each evaluated list's FP32 sum is
 // added into an FP64 per-body accumulator); otherwise FP32 throughout.
-template <int D, bool ACC64>
+// REL: some simulation of the launch may use the relative criterion (an
+// instance without it carries none of that code).
+template <int D, bool ACC64, bool REL>
 __global__ void __launch_bounds__(walk_warps(D) * 32, 1) k_walk(WalkLaunch L) {
   using Acc = typename std::conditional<ACC64, double, float>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -159,7 +161,7 @@ __global__ void __launch_bounds__(walk_warps(D) * 32, 1) k_walk(WalkLaunch L) {
     }
     // relative criterion: the group accepts a node only when every body of it
     // would, so it uses the smallest |a_old| of the group
-    const bool rel = DESC(aold) != nullptr;
+    const bool rel = REL && DESC(aold) != nullptr;
     float thr = 0.f;
     if (rel) {
       float a = active ? DESC(aold)[DESC(perm)[p]] : 3.0e38f;
@@ -495,7 +497,7 @@ static size_t walk_smem(int nlaws, int entries, int nwarps) {
   return tab_bytes + (size_t)nwarps * sizeof(WarpSmem<D>);
 }
 
-template <int D, bool ACC64>
+template <int D, bool ACC64, bool REL>
 static int launch_walk_d(ng_ctx* c, cudaStream_t stream, const WalkLaunch& L, int64_t groups) {
   int nwarps = walk_warps(D);
   while (nwarps > 1 && walk_smem<D>(L.nlaws, L.tab_entries, nwarps) > c->smem_optin) --nwarps;
@@ -504,17 +506,17 @@ static int launch_walk_d(ng_ctx* c, cudaStream_t stream, const WalkLaunch& L, in
     return fail(c, NG_ENOMEM, "walk needs %zu B shared memory (max %zu)", smem, c->smem_optin);
   // the attribute is a per-function ceiling shared by every thread that
   // launches the walk: always raise it to the device maximum, never lower it
-  NG_CUDA(c, cudaFuncSetAttribute(k_walk<D, ACC64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  NG_CUDA(c, cudaFuncSetAttribute(k_walk<D, ACC64, REL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)c->smem_optin));
   int per_sm = 0;
-  NG_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walk<D, ACC64>, nwarps * 32,
+  NG_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walk<D, ACC64, REL>, nwarps * 32,
                                                            smem));
   if (per_sm < 1) per_sm = 1;
   // persistent warps take groups from a counter: no more blocks than the
   // expected groups need, so small problems leave SMs to concurrent work
   const int64_t want = (std::max<int64_t>(groups, 1) + nwarps - 1) / nwarps;
   const int grid = (int)std::min<int64_t>((int64_t)c->nsm * per_sm, want);
-  k_walk<D, ACC64><<<grid, nwarps * 32, smem, stream>>>(L);
+  k_walk<D, ACC64, REL><<<grid, nwarps * 32, smem, stream>>>(L);
   c->launches += 1;
   NG_CUDA(c, cudaGetLastError());
   return NG_OK;
@@ -549,21 +551,25 @@ void fill_walk_desc(ng_ctx* c, float* acc, bool accumulate, WalkDesc* d) {
   d->rel_scale = (float)(c->p.alpha * c->L * c->L / coupling_max(c));
 }
 
-template <bool ACC64>
+template <bool ACC64, bool REL>
 static int dispatch_walk_acc(ng_ctx* c, cudaStream_t stream, const WalkLaunch& L, int64_t groups) {
   switch (c->p.D) {
-    case 1: return launch_walk_d<1, ACC64>(c, stream, L, groups);
-    case 2: return launch_walk_d<2, ACC64>(c, stream, L, groups);
-    case 3: return launch_walk_d<3, ACC64>(c, stream, L, groups);
-    case 4: return launch_walk_d<4, ACC64>(c, stream, L, groups);
-    case 5: return launch_walk_d<5, ACC64>(c, stream, L, groups);
-    default: return launch_walk_d<6, ACC64>(c, stream, L, groups);
+    case 1: return launch_walk_d<1, ACC64, REL>(c, stream, L, groups);
+    case 2: return launch_walk_d<2, ACC64, REL>(c, stream, L, groups);
+    case 3: return launch_walk_d<3, ACC64, REL>(c, stream, L, groups);
+    case 4: return launch_walk_d<4, ACC64, REL>(c, stream, L, groups);
+    case 5: return launch_walk_d<5, ACC64, REL>(c, stream, L, groups);
+    default: return launch_walk_d<6, ACC64, REL>(c, stream, L, groups);
   }
 }
 
-static int dispatch_walk(ng_ctx* c, cudaStream_t stream, const WalkLaunch& L, int64_t groups) {
-  return c->p.accumulate_fp64 ? dispatch_walk_acc<true>(c, stream, L, groups)
-                              : dispatch_walk_acc<false>(c, stream, L, groups);
+static int dispatch_walk(ng_ctx* c, cudaStream_t stream, const WalkLaunch& L, int64_t groups,
+                         bool rel) {
+  if (c->p.accumulate_fp64)
+    return rel ? dispatch_walk_acc<true, true>(c, stream, L, groups)
+               : dispatch_walk_acc<true, false>(c, stream, L, groups);
+  return rel ? dispatch_walk_acc<false, true>(c, stream, L, groups)
+             : dispatch_walk_acc<false, false>(c, stream, L, groups);
 }
 
 int64_t walk_groups_hint(const ng_ctx* c) {
@@ -574,7 +580,7 @@ int64_t walk_groups_hint(const ng_ctx* c) {
 
 int launch_walk_descs(ng_ctx* c, cudaStream_t stream, const WalkDesc* d_descs, int ndesc,
                       uint32_t* d_prefix, uint32_t* d_work, unsigned long long* counter,
-                      int64_t groups) {
+                      int64_t groups, bool rel) {
   k_walk_prep<<<1, 1024, 0, stream>>>(d_descs, ndesc, d_prefix, d_work);
   c->launches += 1;
   NG_CUDA(c, cudaGetLastError());
@@ -588,7 +594,7 @@ int launch_walk_descs(ng_ctx* c, cudaStream_t stream, const WalkDesc* d_descs, i
   L.ncut = c->ncut;
   L.nlaws = c->nlaws;
   L.counter = counter;
-  return dispatch_walk(c, stream, L, groups);
+  return dispatch_walk(c, stream, L, groups, rel);
 }
 
 // The descriptor travels as a kernel argument (captured by value, also in
@@ -609,7 +615,7 @@ int launch_walk(ng_ctx* c, float* acc, bool accumulate, bool count) {
   uint32_t* pre = as<uint32_t>(c->walk_prefix);
   return launch_walk_descs(c, c->stream, as<WalkDesc>(c->walk_desc), 1, pre, pre + 2,
                            count ? as<unsigned long long>(c->counter) : nullptr,
-                           walk_groups_hint(c));
+                           walk_groups_hint(c), d.aold != nullptr);
 }
 
 // ------------------------------------------------ per-particle count walk
