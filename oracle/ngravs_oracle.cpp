@@ -12,8 +12,7 @@
  * cores. Built with -ffp-contract=off so that the integer-producing steps
  * (periodic wrap, Morton quantisation) round the same way on every host.
  *
- * Readings of the paper that these routines take (every one is listed again
- * in the design doc):
+ * Readings of the paper that these routines take:
  *  - Sec. 2, Eq. (map): f_ij with i the passive and j the active species;
  *    G is stored [passive][active].
  *  - Eq. (yukawa) with C = 1: phi_ij(r) = -G_ij M (1 + a_ij exp(-r/l_ij)) / r;
