@@ -236,8 +236,9 @@ __global__ void __launch_bounds__(walk_warps(D) * 32, 1) k_walk(WalkLaunch L) {
             sy2 = __ffma2_rn(f, dy, sy2);
             sz2 = __ffma2_rn(f, dz, sz2);
           };
-          // four records of each component per 16-byte load
-#pragma unroll 1
+          // four records of each component per 16-byte load; two loop
+          // bodies per iteration give the scheduler loads to hoist
+#pragma unroll 2
           for (int j = 0; j < cnt4; j += 4) {
             const float4 X = *reinterpret_cast<const float4*>(lt4 + j);
             const float4 Y = *reinterpret_cast<const float4*>(lt4 + kListCap + j);
