@@ -209,9 +209,11 @@ __global__ void __launch_bounds__(walk_warps(D) * 32, 1) k_walk(WalkLaunch L) {
               (uint32_t)__cvta_generic_to_shared(tab + (int)DESC(tabid[s][t]) * L.tab_entries) -
               ((uint32_t)kMagicBits << 3);
           float* lt4 = reinterpret_cast<float*>(ws->list[t]);
-          // pad to a multiple of 4 with massless records (zero force)
-          const int cnt4 = (cnt + 3) & ~3;
-          if (lane < cnt4 - cnt) put_rec(ws->list[t], cnt + lane, 0.f, 0.f, 0.f, 0.f);
+          // pad to an even count with a massless record (zero force); full
+          // quads of records, then at most one pair
+          const int cnt2 = (cnt + 1) & ~1;
+          const int nq = cnt2 & ~3;
+          if (lane < cnt2 - cnt) put_rec(ws->list[t], cnt + lane, 0.f, 0.f, 0.f, 0.f);
           __syncwarp();
           // (record j, record j + 1) in the two halves of packed FP32x2
           // operations; each half rounds exactly as the scalar operation
@@ -239,7 +241,7 @@ __global__ void __launch_bounds__(walk_warps(D) * 32, 1) k_walk(WalkLaunch L) {
           // four records of each component per 16-byte load; two loop
           // bodies per iteration give the scheduler loads to hoist
 #pragma unroll 2
-          for (int j = 0; j < cnt4; j += 4) {
+          for (int j = 0; j < nq; j += 4) {
             const float4 X = *reinterpret_cast<const float4*>(lt4 + j);
             const float4 Y = *reinterpret_cast<const float4*>(lt4 + kListCap + j);
             const float4 Z = *reinterpret_cast<const float4*>(lt4 + 2 * kListCap + j);
@@ -248,6 +250,13 @@ __global__ void __launch_bounds__(walk_warps(D) * 32, 1) k_walk(WalkLaunch L) {
                  make_float2(M.x, M.y));
             pair(make_float2(X.z, X.w), make_float2(Y.z, Y.w), make_float2(Z.z, Z.w),
                  make_float2(M.z, M.w));
+          }
+          if (cnt2 != nq) {
+            const float2 X = *reinterpret_cast<const float2*>(lt4 + nq);
+            const float2 Y = *reinterpret_cast<const float2*>(lt4 + kListCap + nq);
+            const float2 Z = *reinterpret_cast<const float2*>(lt4 + 2 * kListCap + nq);
+            const float2 M = *reinterpret_cast<const float2*>(lt4 + 3 * kListCap + nq);
+            pair(X, Y, Z, M);
           }
           const float sx = sx2.x + sx2.y, sy = sy2.x + sy2.y, sz = sz2.x + sz2.y;
           __syncwarp();
