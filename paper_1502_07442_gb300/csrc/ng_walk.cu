@@ -238,9 +238,9 @@ __global__ void __launch_bounds__(walk_warps(D) * 32, 1) k_walk(WalkLaunch L) {
             sy2 = __ffma2_rn(f, dy, sy2);
             sz2 = __ffma2_rn(f, dz, sz2);
           };
-          // four records of each component per 16-byte load; two loop
+          // four records of each component per 16-byte load; four loop
           // bodies per iteration give the scheduler loads to hoist
-#pragma unroll 2
+#pragma unroll 4
           for (int j = 0; j < nq; j += 4) {
             const float4 X = *reinterpret_cast<const float4*>(lt4 + j);
             const float4 Y = *reinterpret_cast<const float4*>(lt4 + kListCap + j);
@@ -301,12 +301,17 @@ __global__ void __launch_bounds__(walk_warps(D) * 32, 1) k_walk(WalkLaunch L) {
           bt = near_box(px, py, pz, gx, gy, gz, rc2_keep) ? (int)DESC(btype)[b] : -1;
           rec = make_float4(px * s_tab, py * s_tab, pz * s_tab, bb.w);
         }
+        // each body goes to the list of its species: its slot is taken while
+        // the list counts advance, then one append per lane
+        int slot = 0;
 #pragma unroll
         for (int t = 0; t < D; ++t) {
           const uint32_t m = __ballot_sync(0xffffffffu, bt == t);
-          if (bt == t) put_rec(ws->list[t], lc[t] + __popc(m & lt), rec.x, rec.y, rec.z, rec.w);
+          if (bt == t) slot = lc[t] + __popc(m & lt);
           lc[t] += __popc(m);
         }
+        // (bt = -1: beyond r_cut of the box; the gather stores only species < D)
+        if ((unsigned)bt < (unsigned)D) put_rec(ws->list[bt], slot, rec.x, rec.y, rec.z, rec.w);
         qdone += 32;
         __syncwarp();
         continue;
