@@ -229,6 +229,18 @@ int ng_count_interactions(ng_ctx* ctx, int64_t* counts_out, uint64_t* total_out)
 int ng_pm_force(ng_ctx* ctx, float* acc_out);
 
 /*
+ * Total acceleration of the bodies of the last build (Sec. 2.4.1: the TreePM
+ * split of every law into a short-range part summed by the tree walk and a
+ * long-range part from the mesh): the PM acceleration of ng_pm_force when
+ * pm_mesh > 0, plus the short-range tree acceleration of ng_tree_force,
+ * summed on the device into acc_out (device float[3][n], caller order,
+ * overwritten). With pm_mesh == 0 it is the tree force alone. With the
+ * relative criterion, |a_old| is then replaced by the magnitude of this
+ * total. NG_ESTATE before ng_build_tree. Asynchronous on the stream.
+ */
+int ng_force(ng_ctx* ctx, float* acc_out);
+
+/*
  * Kick-drift-kick leapfrog (Sec. 2.1.1) at fixed dt for nsteps steps:
  *   v += a dt/2 (float); x += v dt (double); wrap; a = a_short + a_long; v += a dt/2.
  * pos (double[3][n]) and vel (float[3][n]) are updated in place; acc
@@ -378,6 +390,14 @@ const char* ng_serve_last_error(const ng_server* s);
 /* Device bytes the server budgets for a request (particle arrays, sort and
  * tree buffers, PM meshes). */
 size_t ng_serve_request_bytes(const ng_request* r);
+/* Bookkeeping (no paper counterpart): bytes the slots hold now, the largest
+ * sum seen after any admission or tree regrow (never above the budget), and
+ * the number of requests rerun with a larger tree capacity. A request whose
+ * tree outgrows the slot is rerun only if the slot's larger holding fits the
+ * budget beside the other slots; otherwise it fails with NG_ENOMEM. Any
+ * output pointer may be NULL. */
+int ng_serve_stats(const ng_server* s, size_t* held_bytes, size_t* peak_held_bytes,
+                   int64_t* node_retries);
 
 /*
  * Number of CUDA kernels this context has launched so far (host-side count,
@@ -398,10 +418,12 @@ int ng_launch_count(const ng_ctx* ctx, uint64_t* out);
  * pos (double[3][n]), type (uint8[n]), keys_out (uint64[n]) and perm_out
  * (uint32[n]) are caller DEVICE arrays; stream as in ng_create. Returns
  * NG_EINVAL for n outside [1, 2^18], NULL arrays or box <= 0, NG_ECUDA if a
- * CUDA call fails. The first call on a device looks the scratch address up
- * (cudaGetSymbolAddress) and should come before any stream capture. All
- * calls share the one scratch array: calls whose work overlaps on the GPU
- * (other streams or host threads) race on it. Asynchronous on the stream.
+ * CUDA call or launch fails. Every call looks the scratch address up on the
+ * current device (cudaGetSymbolAddress, never cached); the first call on a
+ * device may load the library's device code there and should come before
+ * any stream capture. All calls share the one scratch array: calls whose
+ * work overlaps on the GPU (other streams or host threads) race on it.
+ * Asynchronous on the stream.
  */
 int ng_sort_keys_noalloc(int64_t n, const double* pos, const uint8_t* type, double box,
                          uint64_t* keys_out, uint32_t* perm_out, void* stream);

@@ -93,6 +93,7 @@ def lib():
         L.ng_step_host.argtypes = [vp, i64, vp, vp, vp, vp, vp, i32, i32, d]
         L.ng_timestep.argtypes = [vp, i64, vp, d, d, ctypes.POINTER(d), ctypes.POINTER(ctypes.c_float)]
         L.ng_pm_force.argtypes = [vp, vp]
+        L.ng_force.argtypes = [vp, vp]
         L.ng_step.argtypes = [vp, i64, vp, vp, vp, vp, vp, i32, i32, d]
         L.ng_tree_export.argtypes = [vp, ctypes.POINTER(i64)] + [vp] * 9
         L.ng_type_order.argtypes = [vp, vp, vp]
@@ -116,6 +117,9 @@ def lib():
         L.ng_serve.argtypes = [vp, ctypes.POINTER(NgRequest), ctypes.POINTER(NgResult), i32, vp, d]
         L.ng_sort_keys_noalloc.argtypes = [i64, vp, vp, d, vp, vp, vp]
         L.ng_sort_keys_noalloc.restype = ctypes.c_int
+        L.ng_serve_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t),
+                                     ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(i64)]
+        L.ng_serve_stats.restype = ctypes.c_int
         L.ng_serve_request_bytes.argtypes = [ctypes.POINTER(NgRequest)]
         L.ng_serve_request_bytes.restype = ctypes.c_size_t
         L.ng_serve_last_error.argtypes = [vp]
@@ -124,7 +128,7 @@ def lib():
         L.ng_last_error.restype = ctypes.c_char_p
         L.ng_version.restype = ctypes.c_char_p
         for f in ("ng_create", "ng_destroy", "ng_set_stream", "ng_build_tree", "ng_tree_force",
-                  "ng_count_interactions", "ng_pm_force", "ng_step", "ng_tree_export",
+                  "ng_count_interactions", "ng_pm_force", "ng_force", "ng_step", "ng_tree_export",
                   "ng_type_order", "ng_launch_count", "ng_batch_create", "ng_batch_destroy",
                   "ng_batch_step", "ng_batch_size", "ng_batch_walk_launches",
                   "ng_batch_launch_count", "ng_serve_create", "ng_serve_destroy",
@@ -138,13 +142,15 @@ def lib():
 def exported_symbols():
     """Names the header declares (used by the ABI test)."""
     return ["ng_create", "ng_destroy", "ng_set_stream", "ng_build_tree", "ng_tree_force",
-            "ng_count_interactions", "ng_pm_force", "ng_step", "ng_tree_export", "ng_type_order",
+            "ng_count_interactions", "ng_pm_force", "ng_force", "ng_step", "ng_tree_export",
+            "ng_type_order",
             "ng_launch_count", "ng_last_error", "ng_version", "ng_batch_create",
             "ng_batch_destroy", "ng_batch_step", "ng_batch_size", "ng_batch_walk_launches",
             "ng_batch_launch_count", "ng_batch_last_error", "ng_serve_create",
             "ng_serve_destroy", "ng_serve_submit", "ng_serve_cancel", "ng_serve_poll",
             "ng_serve_pending", "ng_serve_wait", "ng_serve", "ng_serve_last_error",
-            "ng_serve_request_bytes", "ng_sort_keys_noalloc", "ng_set_acc_old", "ng_timestep", "ng_step_host"]
+            "ng_serve_request_bytes", "ng_serve_stats", "ng_sort_keys_noalloc", "ng_set_acc_old",
+            "ng_timestep", "ng_step_host"]
 
 
 def _check(ctx, code):
@@ -254,6 +260,11 @@ def ng_count_interactions(ctx, counts_out=None):
 
 def ng_pm_force(ctx, acc_out):
     _check(ctx, lib().ng_pm_force(ctx, _ptr(acc_out)))
+
+
+def ng_force(ctx, acc_out):
+    """Short-range tree plus long-range PM acceleration, summed in the library."""
+    _check(ctx, lib().ng_force(ctx, _ptr(acc_out)))
 
 
 def ng_step(ctx, pos, vel, typ, mass, acc, acc_valid, nsteps, dt):
@@ -381,6 +392,13 @@ def ng_serve(s, reqs, results, arrival_s=None, timeout_s=600.0):
     _scheck(s, lib().ng_serve(s, reqs, results, len(reqs), arr, float(timeout_s)))
 
 
+def ng_serve_stats(s):
+    """(bytes held now, peak bytes held, requests rerun with a larger tree)."""
+    held, peak, retries = ctypes.c_size_t(0), ctypes.c_size_t(0), ctypes.c_int64(0)
+    _scheck(s, lib().ng_serve_stats(s, ctypes.byref(held), ctypes.byref(peak), ctypes.byref(retries)))
+    return int(held.value), int(peak.value), int(retries.value)
+
+
 def ng_serve_request_bytes(req: NgRequest):
     return int(lib().ng_serve_request_bytes(ctypes.byref(req)))
 
@@ -431,15 +449,16 @@ class Simulation:
             pass
 
     def force(self, pos, typ, mass, acc=None, pm=True):
-        """Short (+ long when the context has a mesh) acceleration, float32 [3, n]."""
+        """Build the tree, then the total acceleration (ng_force: short + long
+        when the context has a mesh) or, with pm=False, the short-range tree
+        acceleration alone (ng_tree_force); float32 [3, n]."""
         import torch
         n = typ.numel()
         if acc is None:
             acc = torch.empty((3, n), dtype=torch.float32, device=pos.device)
         ng_build_tree(self.ctx, pos, typ, mass)
-        ng_tree_force(self.ctx, acc)
         if pm:
-            long_ = torch.empty_like(acc)
-            ng_pm_force(self.ctx, long_)
-            acc += long_
+            ng_force(self.ctx, acc)
+        else:
+            ng_tree_force(self.ctx, acc)
         return acc

@@ -49,30 +49,6 @@ void release(DevBuf& b) {
 
 // ------------------------------------------------------ short-range laws
 
-// Short-range force factor T(rho) of Sec. 2.4.1: the acceleration from a
-// source of active mass M is G M T(rho) d / rho^3. Newtonian part:
-// -rho^2 d/drho [erfc(rho / 2 r_s) / rho]. Yukawa part (Eq. (yukawa), C = 1,
-// Sec. 3.2 long-range kernel scaled by exp(-mu^2 r_s^2)): the remaining
-// real-space potential -a S(rho)/rho with
-//   S = [e^{-mu rho} erfc(v - mu r_s) + e^{mu rho} erfc(v + mu r_s)] / 2,
-// v = rho / 2 r_s, contributes a (S - rho dS/drho). The pure Yukawa law
-// (C = 0, Sec. 3.2) has that part alone.
-double short_law_factor(int law, double a, double l, double rs, double rho) {
-  const double v = rho / (2.0 * rs);
-  const double gauss = std::exp(-v * v);
-  double T = law == NG_YUKAWA_PURE ? 0.0 : std::erfc(v) + (2.0 / std::sqrt(M_PI)) * v * gauss;
-  if (law == NG_YUKAWA || law == NG_YUKAWA_PURE) {
-    const double mu = 1.0 / l;
-    const double lo = std::exp(-mu * rho) * std::erfc(v - mu * rs);
-    const double ec = std::erfc(v + mu * rs);
-    const double hi = ec > 0.0 ? std::exp(mu * rho + std::log(ec)) : 0.0;
-    const double S = 0.5 * (lo + hi);
-    const double dS = 0.5 * mu * (hi - lo) - gauss * std::exp(-mu * mu * rs * rs) / (rs * std::sqrt(M_PI));
-    T += a * (S - rho * dS);
-  }
-  return T;
-}
-
 // One table per distinct law; segment k (k < ncut) is the chord of T over
 // [(k - 1/2) dr, (k + 1/2) dr] (segment 0 over [0, dr/2]), c0 + t c1 with
 // t = rho/dr - k, stored as {c0 - k c1, c1}; entry ncut is zero (beyond the cut-off,
@@ -327,7 +303,7 @@ int build_checked(ng_ctx* c, int64_t n, const double* pos, const uint8_t* type,
 int force_stages(ng_ctx* c, float* acc) {
   if (c->p.pm_mesh > 0) {
     NG_TRY(pm_force(c, acc, false));
-    NG_TRY(launch_walk(c, acc, true, false));
+    NG_TRY(launch_tree_force(c, acc, true, false));
   } else {
     NG_TRY(launch_tree_force(c, acc, false, false));
   }
@@ -403,12 +379,16 @@ int validate(ng_ctx* c, const ng_params* p) {
   return NG_OK;
 }
 
+void normalize_params(ng_params* p) {
+  if (p->leaf_size == 0) p->leaf_size = 8;
+  if (p->group_size == 0) p->group_size = 32;
+  if (p->group_cell == 0) p->group_cell = p->group_size;
+}
+
 int ctx_configure(ng_ctx* c, const ng_params* p) {
   NG_TRY(validate(c, p));
   c->p = *p;
-  if (c->p.leaf_size == 0) c->p.leaf_size = 8;
-  if (c->p.group_size == 0) c->p.group_size = 32;
-  if (c->p.group_cell == 0) c->p.group_cell = c->p.group_size;
+  normalize_params(&c->p);
   c->L = p->box;
   c->rs = p->pm_mesh > 0 ? p->asmth * p->box / p->pm_mesh : p->asmth * p->box;
   c->rcut = p->pure_tree == 2 ? INFINITY : p->rcut_over_rs * c->rs;
@@ -443,9 +423,7 @@ int ng_create(ng_ctx** out, const ng_params* p, void* stream) {
     return r;
   }
   c->p = *p;
-  if (c->p.leaf_size == 0) c->p.leaf_size = 8;
-  if (c->p.group_size == 0) c->p.group_size = 32;
-  if (c->p.group_cell == 0) c->p.group_cell = c->p.group_size;
+  normalize_params(&c->p);
   c->stream = (cudaStream_t)stream;
   c->L = p->box;
   c->rs = p->pm_mesh > 0 ? p->asmth * p->box / p->pm_mesh : p->asmth * p->box;
@@ -625,6 +603,13 @@ int ng_pm_force(ng_ctx* c, float* acc_out) {
   if (!c->built) return fail(c, NG_ESTATE, "ng_pm_force before ng_build_tree");
   if (!acc_out) return fail(c, NG_EINVAL, "acc_out is NULL");
   return pm_force(c, acc_out, false);
+}
+
+int ng_force(ng_ctx* c, float* acc_out) {
+  if (!c) return NG_EINVAL;
+  if (!c->built) return fail(c, NG_ESTATE, "ng_force before ng_build_tree");
+  if (!acc_out) return fail(c, NG_EINVAL, "acc_out is NULL");
+  return force_stages(c, acc_out);
 }
 
 static int step_once(ng_ctx* c, int64_t n, double* pos, float* vel, const uint8_t* type,

@@ -383,10 +383,13 @@ int build_lattice(ng_ctx* c, int nlaws, const int* kind, const double* a, const 
   return NG_OK;
 }
 
-// The short-range (or, in pure tree mode, the whole) tree force of a context.
+// The short-range (or, in pure tree mode, the whole) tree force of a context:
+// the exact-law walk in pure tree mode, the FP64 pair sum in direct mode
+// (theta = 0), the FP32 group walk otherwise.
 int launch_tree_force(ng_ctx* c, float* acc, bool accumulate, bool count) {
-  return c->p.pure_tree ? launch_walk_exact(c, acc, accumulate, count)
-                        : launch_walk(c, acc, accumulate, count);
+  if (c->p.pure_tree) return launch_walk_exact(c, acc, accumulate, count);
+  if (direct_mode(c)) return launch_direct64(c, acc, accumulate, count);
+  return launch_walk(c, acc, accumulate, count);
 }
 
 }  // namespace ng

@@ -1,6 +1,8 @@
 // Internal declarations of the ngravs CUDA library (not part of the ABI).
 #pragma once
 
+#include <cmath>
+
 #include <cuda_runtime.h>
 #include <cufft.h>
 #include <stdint.h>
@@ -64,6 +66,77 @@ __device__ __forceinline__ uint32_t morton_compact3(uint64_t v) {
 
 // A box-unit offset wrapped to its nearest periodic image, rounded once.
 __device__ __forceinline__ double nearest_image_unit(double d) { return __dsub_rn(d, rint(d)); }
+
+// ------------------------------------------------------------------ keys
+// Wrap, quantisation and interleaving of the sort keys (Sec. 2.4), shared by
+// every kernel that forms keys so that all of them round identically.
+
+// x / L rounded once. For a power-of-two L the product with 1/L is the same
+// number (both exact), and FP64 division costs ~10 FP64 operations here.
+__device__ __forceinline__ double div_box(double x, double L, double invL, bool pow2) {
+  return pow2 ? __dmul_rn(x, invL) : __ddiv_rn(x, L);
+}
+
+// Periodic wrap x - L floor(x / L) with each operation rounded separately
+// (no fused multiply-add), so that the host reference rounds identically.
+// FP64 issues at 1/64 of the FP32 rate here, so for a power-of-two box the
+// common case is decided on the bits: a non-negative double orders like its
+// bit pattern, and for x in [+0, L) x / L is exact and below 1, so the wrap
+// returns x itself.
+__device__ __forceinline__ double wrap_box(double x, double L, double invL, bool pow2) {
+  if (pow2) {
+    const long long b = __double_as_longlong(x);
+    if (b >= 0 && b < __double_as_longlong(L)) return x;
+  }
+  const double f = floor(div_box(x, L, invL, pow2));
+  return __dsub_rn(x, __dmul_rn(L, f));
+}
+
+// floor(w / L * 2^20) clamped to [0, 2^20 - 1]. For a box L = 2^ebox the
+// scaled value is w * 2^(20 - ebox) exactly, and its integer part is read
+// from the exponent and mantissa bits (the same number the FP64 formula
+// gives, without FP64 instructions).
+__device__ __forceinline__ uint64_t quantise20(double w, double L, double invL, bool pow2,
+                                               int ebox) {
+  if (pow2) {
+    const long long b = __double_as_longlong(w);
+    const int e = (int)((b >> 52) & 0x7ff);
+    if (b <= 0) return 0;                        // +0, -0 and negative w
+    if (e != 0x7ff) {                            // finite w > 0
+      const int sh = e - 1023 + 20 - ebox;      // w * 2^(20 - ebox) = 1.m * 2^sh
+      if (sh < 0) return 0;
+      if (sh >= 20) return 1048575;
+      const uint64_t m = ((uint64_t)b & ((1ull << 52) - 1)) | (1ull << 52);
+      return m >> (52 - sh);
+    }
+  }
+  double q = floor(__dmul_rn(div_box(w, L, invL, pow2), 1048576.0));
+  q = q < 0.0 ? 0.0 : q;
+  q = q > 1048575.0 ? 1048575.0 : q;
+  return (uint64_t)q;
+}
+
+// Spread the low 21 bits of v to every third bit.
+__device__ __forceinline__ uint64_t spread3(uint64_t v) {
+  v &= 0x1fffffull;
+  v = (v | (v << 32)) & 0x1f00000000ffffull;
+  v = (v | (v << 16)) & 0x1f0000ff0000ffull;
+  v = (v | (v << 8)) & 0x100f00f00f00f00full;
+  v = (v | (v << 4)) & 0x10c30c30c30c30c3ull;
+  v = (v | (v << 2)) & 0x1249249249249249ull;
+  return v;
+}
+
+// The sort key of one body: (Morton(q_x, q_y, q_z) << 3) | species, x most
+// significant, q = floor((x mod L) / L * 2^20) clamped to [0, 2^20 - 1].
+__device__ __forceinline__ uint64_t sort_key(double x, double y, double z, uint8_t type, double L,
+                                             double invL, bool pow2, int ebox) {
+  const uint64_t qx = quantise20(wrap_box(x, L, invL, pow2), L, invL, pow2, ebox);
+  const uint64_t qy = quantise20(wrap_box(y, L, invL, pow2), L, invL, pow2, ebox);
+  const uint64_t qz = quantise20(wrap_box(z, L, invL, pow2), L, invL, pow2, ebox);
+  const uint64_t m = (spread3(qx) << 2) | (spread3(qy) << 1) | spread3(qz);
+  return (m << 3) | (uint64_t)(type & 7);
+}
 
 // Keys per block of the radix sort; the per-block digit histograms (and the
 // type offsets read back from the last pass's) are laid out by it.
@@ -223,6 +296,10 @@ int launch_walk_descs(ng_ctx* c, cudaStream_t stream, const WalkDesc* d_descs, i
                       uint32_t* d_prefix, uint32_t* d_work, unsigned long long* counter,
                       int64_t groups, bool rel);
 int launch_count(ng_ctx* c, int64_t* counts);  // per-particle walk counts
+// Direct mode (theta = 0, geometric opening, TreePM split): every pair within
+// r_cut summed in FP64 (ng_direct.cu).
+int launch_direct64(ng_ctx* c, float* acc, bool accumulate, bool count);
+bool direct_mode(const ng_ctx* c);
 // Pure tree mode: per-particle walk with the full laws (incl. Mahalo).
 int launch_walk_exact(ng_ctx* c, float* acc, bool accumulate, bool count);
 // The tree force of a context: the group walk, or in pure tree mode the exact walk.
@@ -240,7 +317,32 @@ int type_order(ng_ctx* c);
 
 // Host short-range law tables (double precision closed forms).
 int build_tables(ng_ctx* c);
-double short_law_factor(int law, double a, double l, double rs, double rho);
+
+// Short-range force factor T(rho) of Sec. 2.4.1 in FP64: the acceleration from
+// a source of active mass M is G M T(rho) d / rho^3. Newtonian part:
+// -rho^2 d/drho [erfc(rho / 2 r_s) / rho]. Yukawa part (Eq. (yukawa), C = 1,
+// Sec. 3.2 long-range kernel scaled by exp(-mu^2 r_s^2)): the remaining
+// real-space potential -a S(rho)/rho with
+//   S = [e^{-mu rho} erfc(v - mu r_s) + e^{mu rho} erfc(v + mu r_s)] / 2,
+// v = rho / 2 r_s, contributes a (S - rho dS/drho). The pure Yukawa law
+// (C = 0, Sec. 3.2) has that part alone. The same function fills the host
+// tables of the FP32 walk and evaluates the FP64 direct-mode sum.
+__host__ __device__ inline double short_law_factor(int law, double a, double l, double rs,
+                                                   double rho) {
+  const double v = rho / (2.0 * rs);
+  const double gauss = ::exp(-v * v);
+  double T = law == NG_YUKAWA_PURE ? 0.0 : ::erfc(v) + (2.0 / ::sqrt(M_PI)) * v * gauss;
+  if (law == NG_YUKAWA || law == NG_YUKAWA_PURE) {
+    const double mu = 1.0 / l;
+    const double lo = ::exp(-mu * rho) * ::erfc(v - mu * rs);
+    const double ec = ::erfc(v + mu * rs);
+    const double hi = ec > 0.0 ? ::exp(mu * rho + ::log(ec)) : 0.0;
+    const double S = 0.5 * (lo + hi);
+    const double dS = 0.5 * mu * (hi - lo) - gauss * ::exp(-mu * mu * rs * rs) / (rs * ::sqrt(M_PI));
+    T += a * (S - rho * dS);
+  }
+  return T;
+}
 
 // Blocks of 256 threads for a grid-stride kernel over `items` items: enough
 // to cover them, at most per_sm blocks per SM, at least one.
@@ -263,6 +365,8 @@ int alloc_bodies(ng_ctx* c, int64_t n);
 int ctx_configure(ng_ctx* c, const ng_params* p);
 // Host-only validation of a parameter block (message on c).
 int validate(ng_ctx* c, const ng_params* p);
+// Fill the defaults of a parameter block (leaf size, group size, group cell).
+void normalize_params(ng_params* p);
 int check_flags(ng_ctx* c, uint32_t flags);
 bool box_is_pow2(double L);   // L = 2^k: x / L == x * (1 / L) exactly
 

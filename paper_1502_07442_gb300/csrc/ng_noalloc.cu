@@ -12,13 +12,15 @@
 // The scratch lives in a file-scope __device__ array (kNoAllocMaxBodies
 // bodies, about 3.4 MB on every GPU that loads the library, held until the
 // process exits). Host code cannot pass the array's name to a kernel (on the
-// host it is only a stand-in symbol), so the device address is looked up with
-// cudaGetSymbolAddress once per device, with that device current, on the
-// first call made on it; make that first call before any stream capture.
+// host it is only a stand-in symbol), so every call looks up the array's
+// device address with cudaGetSymbolAddress on the current device. The first
+// call on a device may load the library's device code there; make that
+// first call before any stream capture. The address is not cached, so a
+// device reset (which can move the array) leaves no stale pointer behind.
 // Every call shares the one array: calls whose work overlaps on the GPU (two
 // streams, or two host threads) race on it. No part of the scratch has to
 // start at zero: every pass writes each word before it is read.
-#include <mutex>
+#include <cmath>
 
 #include "ng_internal.cuh"
 
@@ -39,38 +41,13 @@ struct NaScratch {
 
 static __device__ __align__(256) NaScratch g_na_scratch;
 
-// Wrap, quantise and interleave exactly as the keys of ng_build_tree: each
-// FP64 operation rounded on its own, x most significant, species low.
-__device__ __forceinline__ double na_div(double x, double L, double invL, bool pow2) {
-  return pow2 ? __dmul_rn(x, invL) : __ddiv_rn(x, L);
-}
-
-__device__ __forceinline__ uint64_t na_spread(uint64_t v) {
-  v &= 0x1fffffull;
-  v = (v | (v << 32)) & 0x1f00000000ffffull;
-  v = (v | (v << 16)) & 0x1f0000ff0000ffull;
-  v = (v | (v << 8)) & 0x100f00f00f00f00full;
-  v = (v | (v << 4)) & 0x10c30c30c30c30c3ull;
-  v = (v | (v << 2)) & 0x1249249249249249ull;
-  return v;
-}
-
-__device__ __forceinline__ uint64_t na_cell(double x, double L, double invL, bool pow2) {
-  const double w = __dsub_rn(x, __dmul_rn(L, floor(na_div(x, L, invL, pow2))));
-  double q = floor(__dmul_rn(na_div(w, L, invL, pow2), 1048576.0));
-  q = q < 0.0 ? 0.0 : (q > 1048575.0 ? 1048575.0 : q);
-  return (uint64_t)q;
-}
-
+// The keys of ng_build_tree (the same device function forms both).
 __global__ void k_na_keys(int64_t n, const double* __restrict__ pos,
                           const uint8_t* __restrict__ type, double L, double invL, bool pow2,
-                          uint64_t* __restrict__ keys, uint32_t* __restrict__ idx) {
+                          int ebox, uint64_t* __restrict__ keys, uint32_t* __restrict__ idx) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const uint64_t m = (na_spread(na_cell(pos[i], L, invL, pow2)) << 2) |
-                       (na_spread(na_cell(pos[n + i], L, invL, pow2)) << 1) |
-                       na_spread(na_cell(pos[2 * n + i], L, invL, pow2));
-    keys[i] = (m << 3) | (uint64_t)(type[i] & 7);
+    keys[i] = ng::sort_key(pos[i], pos[n + i], pos[2 * n + i], type[i], L, invL, pow2, ebox);
     idx[i] = (uint32_t)i;
   }
 }
@@ -164,29 +141,21 @@ k_na_scatter(const uint64_t* __restrict__ kin, const uint32_t* __restrict__ vin,
   }
 }
 
-// Device address of the scratch array, looked up once per device.
-constexpr int kNaMaxDevices = 64;
-std::mutex g_na_lock;
-NaScratch* g_na_addr[kNaMaxDevices] = {};
-
+// Device address of the scratch array on the current device.
 int na_scratch(NaScratch** out) {
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) {
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_na_scratch);
+  if (e != cudaSuccess || !p) {
     cudaGetLastError();
     return NG_ECUDA;
   }
-  if (dev < 0 || dev >= kNaMaxDevices) return NG_EINVAL;
-  std::lock_guard<std::mutex> g(g_na_lock);
-  if (!g_na_addr[dev]) {
-    void* p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, g_na_scratch);
-    if (e != cudaSuccess || !p) {
-      cudaGetLastError();
-      return NG_ECUDA;
-    }
-    g_na_addr[dev] = static_cast<NaScratch*>(p);
-  }
-  *out = g_na_addr[dev];
+  *out = static_cast<NaScratch*>(p);
+  return NG_OK;
+}
+
+// The launch just made failed to start: report it as this call's error.
+int na_launched() {
+  if (cudaGetLastError() != cudaSuccess) return NG_ECUDA;
   return NG_OK;
 }
 
@@ -201,8 +170,10 @@ extern "C" int ng_sort_keys_noalloc(int64_t n, const double* pos, const uint8_t*
   if (r != NG_OK) return r;
   cudaStream_t st = (cudaStream_t)stream;
   const bool pow2 = ng::box_is_pow2(box);
-  k_na_keys<<<(int)((n + 255) / 256), 256, 0, st>>>(n, pos, type, box, 1.0 / box, pow2,
+  const int ebox = pow2 ? std::ilogb(box) : 0;     // box = 2^ebox
+  k_na_keys<<<(int)((n + 255) / 256), 256, 0, st>>>(n, pos, type, box, 1.0 / box, pow2, ebox,
                                                    keys_out, perm_out);
+  if (na_launched() != NG_OK) return NG_ECUDA;
   const int nblocks = (int)((n + kNaTile - 1) / kNaTile);
   // 8 passes of 8 bits; the sorted result returns to (keys_out, perm_out)
   for (int pass = 0; pass < 8; ++pass) {
@@ -215,7 +186,7 @@ extern "C" int ng_sort_keys_noalloc(int64_t n, const double* pos, const uint8_t*
     k_na_scan<<<1, 1024, 0, st>>>(sc->hist, 256 * nblocks);
     k_na_scatter<<<nblocks, kNaThreads, 0, st>>>(kin, vin, kout, vout, n, 8 * pass, sc->hist,
                                                  nblocks);
+    if (na_launched() != NG_OK) return NG_ECUDA;
   }
-  if (cudaGetLastError() != cudaSuccess) return NG_ECUDA;
   return NG_OK;
 }

@@ -65,15 +65,18 @@ struct Req {
 // (requests live on the heap: the launch threads hold pointers to them while
 // the polling thread keeps submitting)
 
-// Device bytes a request needs in a slot (particle arrays, sort and tree
-// buffers for a node capacity of n + 1024, PM meshes).
-size_t request_bytes(const ng_request& q) {
+// Device bytes a request needs in a slot: particle arrays, sort buffers, tree
+// buffers for a capacity of `nodes` nodes, PM meshes.
+size_t request_bytes_nodes(const ng_request& q, size_t nodes) {
   const size_t n = (size_t)q.n, D = (size_t)q.params.D, N = (size_t)q.params.pm_mesh;
   const size_t body = 53 + 100;
   const size_t node = 74 + 52 * D;
   const size_t pm = N ? D * N * N * (N + 2) * 4 * 2 + D * N * N * N * 4 : 0;
-  return n * body + (n + 1024) * node + pm + (1 << 20);
+  return n * body + nodes * node + pm + (1 << 20);
 }
+
+// The admission estimate: a node capacity of n + 1024 (the slot's first try).
+size_t request_bytes(const ng_request& q) { return request_bytes_nodes(q, (size_t)q.n + 1024); }
 
 }  // namespace
 
@@ -82,6 +85,8 @@ struct ng_server {
   std::deque<int64_t> queue;
   std::vector<std::unique_ptr<Req>> reqs;
   size_t budget = 0;
+  size_t peak_held = 0;        // largest sum of slot bytes seen after an admission or a regrow
+  int64_t node_retries = 0;    // requests rerun with a larger tree capacity
   int64_t completed = 0;
   std::string err;
 };
@@ -103,7 +108,9 @@ int launch_request(ng_server* s, Slot& sl, Req& q) {
   const ng_request& r = q.r;
   const int64_t n = r.n;
   int rc = NG_OK;
-  if (std::memcmp(&c->p, &r.params, sizeof(ng_params)) != 0 || c->h_tab.empty()) {
+  ng_params want = r.params;
+  normalize_params(&want);   // compare like with like: the context holds normalised params
+  if (std::memcmp(&c->p, &want, sizeof(ng_params)) != 0 || c->h_tab.empty()) {
     rc = ctx_configure(c, &r.params);
     if (rc != NG_OK) return rc;
   }
@@ -197,6 +204,7 @@ int admit(ng_server* s) {
     Slot& sl = *s->slots[pick];
     s->queue.pop_front();
     sl.bytes = std::max(sl.bytes, need);
+    s->peak_held = std::max(s->peak_held, held_bytes(s));
     sl.req = id;
     sl.retries = 0;
     q.state = 1;
@@ -253,15 +261,25 @@ int reap(ng_server* s) {
       q.out->status = NG_ECUDA;
       sl.ctx->err = std::string("completion event: ") + cudaGetErrorString(e);
     } else if ((sl.h_status[ST_FLAGS] & SF_NODE_OVERFLOW) && sl.retries < 4) {
-      // rerun with room for the node count the build reported
+      // rerun with room for the node count the build reported, if the slot's
+      // larger holding still fits the budget beside the other slots
       ng_ctx* c = sl.ctx;
       const int64_t need = (int64_t)sl.h_status[ST_NODES_NEEDED];
-      if (alloc_nodes(c, std::max<int64_t>(2 * need, 2 * c->cap_nodes)) == NG_OK) {
+      const int64_t cap = std::max<int64_t>(2 * need, 2 * c->cap_nodes);
+      const size_t grown = std::max(sl.bytes, request_bytes_nodes(q.r, (size_t)cap));
+      if (held_bytes(s) - sl.bytes + grown > s->budget) {
+        q.out->status = NG_ENOMEM;
+        c->err = "tree capacity for the request exceeds the byte budget";
+      } else if (alloc_nodes(c, cap) == NG_OK) {
+        sl.bytes = grown;
+        s->peak_held = std::max(s->peak_held, held_bytes(s));
         sl.retries++;
+        s->node_retries++;
         hand_over(sl, &q);               // rerun on the slot's thread
         continue;
+      } else {
+        q.out->status = NG_ENOMEM;
       }
-      q.out->status = NG_ENOMEM;
     } else {
       q.out->status = sl.h_status[ST_FLAGS] ? check_flags(sl.ctx, sl.h_status[ST_FLAGS]) : NG_OK;
     }
@@ -442,5 +460,14 @@ const char* ng_serve_last_error(const ng_server* s) {
 }
 
 size_t ng_serve_request_bytes(const ng_request* r) { return r ? request_bytes(*r) : 0; }
+
+int ng_serve_stats(const ng_server* s, size_t* held_bytes_out, size_t* peak_held_bytes,
+                   int64_t* node_retries) {
+  if (!s) return NG_EINVAL;
+  if (held_bytes_out) *held_bytes_out = held_bytes(s);
+  if (peak_held_bytes) *peak_held_bytes = s->peak_held;
+  if (node_retries) *node_retries = s->node_retries;
+  return NG_OK;
+}
 
 }  // extern "C"

@@ -133,72 +133,12 @@ int scan_u32_flags(ng_ctx* c, const uint32_t* in, uint32_t* out, int64_t len, ui
 
 // --------------------------------------------------------------- keys
 
-// x / L rounded once. For a power-of-two L the product with 1/L is the same
-// number (both exact), and FP64 division costs ~10 FP64 operations here.
-__device__ __forceinline__ double div_box(double x, double L, double invL, bool pow2) {
-  return pow2 ? __dmul_rn(x, invL) : __ddiv_rn(x, L);
-}
-
-// Periodic wrap x - L floor(x / L) with each operation rounded separately
-// (no fused multiply-add), so that the host reference rounds identically.
-// FP64 issues at 1/64 of the FP32 rate here, so for a power-of-two box the
-// common case is decided on the bits: a non-negative double orders like its
-// bit pattern, and for x in [+0, L) x / L is exact and below 1, so the wrap
-// returns x itself.
-__device__ __forceinline__ double wrap_box(double x, double L, double invL, bool pow2) {
-  if (pow2) {
-    const long long b = __double_as_longlong(x);
-    if (b >= 0 && b < __double_as_longlong(L)) return x;
-  }
-  const double f = floor(div_box(x, L, invL, pow2));
-  return __dsub_rn(x, __dmul_rn(L, f));
-}
-
-// floor(w / L * 2^20) clamped to [0, 2^20 - 1]. For a box L = 2^ebox the
-// scaled value is w * 2^(20 - ebox) exactly, and its integer part is read
-// from the exponent and mantissa bits (the same number the FP64 formula
-// gives, without FP64 instructions).
-__device__ __forceinline__ uint64_t quantise20(double w, double L, double invL, bool pow2,
-                                               int ebox) {
-  if (pow2) {
-    const long long b = __double_as_longlong(w);
-    const int e = (int)((b >> 52) & 0x7ff);
-    if (b <= 0) return 0;                        // +0, -0 and negative w
-    if (e != 0x7ff) {                            // finite w > 0
-      const int sh = e - 1023 + 20 - ebox;      // w * 2^(20 - ebox) = 1.m * 2^sh
-      if (sh < 0) return 0;
-      if (sh >= 20) return 1048575;
-      const uint64_t m = ((uint64_t)b & ((1ull << 52) - 1)) | (1ull << 52);
-      return m >> (52 - sh);
-    }
-  }
-  double q = floor(__dmul_rn(div_box(w, L, invL, pow2), 1048576.0));
-  q = q < 0.0 ? 0.0 : q;
-  q = q > 1048575.0 ? 1048575.0 : q;
-  return (uint64_t)q;
-}
-
-// Spread the low 21 bits of v to every third bit.
-__device__ __forceinline__ uint64_t spread3(uint64_t v) {
-  v &= 0x1fffffull;
-  v = (v | (v << 32)) & 0x1f00000000ffffull;
-  v = (v | (v << 16)) & 0x1f0000ff0000ffull;
-  v = (v | (v << 8)) & 0x100f00f00f00f00full;
-  v = (v | (v << 4)) & 0x10c30c30c30c30c3ull;
-  v = (v | (v << 2)) & 0x1249249249249249ull;
-  return v;
-}
-
 __global__ void k_keys(int64_t n, const double* __restrict__ pos, const uint8_t* __restrict__ type,
                        double L, double invL, bool pow2, int ebox, uint64_t* __restrict__ keys,
                        uint32_t* __restrict__ idx) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const uint64_t qx = quantise20(wrap_box(pos[i], L, invL, pow2), L, invL, pow2, ebox);
-    const uint64_t qy = quantise20(wrap_box(pos[n + i], L, invL, pow2), L, invL, pow2, ebox);
-    const uint64_t qz = quantise20(wrap_box(pos[2 * n + i], L, invL, pow2), L, invL, pow2, ebox);
-    const uint64_t m = (spread3(qx) << 2) | (spread3(qy) << 1) | spread3(qz);
-    keys[i] = (m << 3) | (uint64_t)(type[i] & 7);
+    keys[i] = sort_key(pos[i], pos[n + i], pos[2 * n + i], type[i], L, invL, pow2, ebox);
     idx[i] = (uint32_t)i;
   }
 }

@@ -1,11 +1,9 @@
 """GPU parity of the forces through the C ABI against the FP64 oracle.
 
 Tolerances (FP32 on the GPU):
-* direct short-range sum (theta = 0): per particle |dF| <= 2e-5 |F|, or, where
-  the terms cancel (sum_k |F_k| > 10 |F|), |dF| <= 2e-6 sum_k |F_k|: each FP32
-  term carries <= ~1e-6 relative error (table chords <= 7e-7, rounding of
-  ~20 FP32 operations), so no FP32 evaluation can promise 2e-5 of a force
-  that is itself 10^-4 of its terms (a body at a cluster centre);
+* direct short-range sum (theta = 0): per particle |dF| <= 2e-5 |F| for every
+  body with a non-zero reference force (direct mode sums every pair in FP64
+  and rounds once to FP32, so cancellation between terms costs nothing);
 * tree mode (theta = 0.5): 99th percentile of the relative error against the
   FP64 direct sum <= 1.1x that of the oracle's per-particle tree walk;
 * PM long-range part: max error <= 1e-5 of the rms long-range acceleration
@@ -72,14 +70,11 @@ def test_direct_mode_matches_oracle(ng, name, make):
     w = make()
     prm = dict(w["params"], theta=0.0)
     got = _short_force(ng, prm, w)
-    ref, mag = oracle.direct_mag(oracle_params(prm), w["pos"], w["type"], w["mass"])
+    ref = oracle.direct(oracle_params(prm), w["pos"], w["type"], w["mass"])
     dF = np.linalg.norm(got - ref, axis=0)
     F = np.linalg.norm(ref, axis=0)
-    bound = np.maximum(2e-5 * F, 2e-6 * mag)
-    bad = dF > bound
+    bad = dF > 2e-5 * F
     assert not bad.any(), f"{bad.sum()} bodies, worst dF/F {(dF / np.maximum(F, 1e-300)).max():.3g}"
-    err, _ = rel_err(got, ref)
-    assert np.percentile(err, 99) <= 2e-5
 
 
 TREE_CASES = [
@@ -106,6 +101,29 @@ def test_tree_mode_error_within_oracle_bound(ng, name, make):
     # per-particle count still counts, so the executed count may fall a little
     # below it when groups are tight, never far
     assert nint >= 0.8 * cnt.sum()
+
+
+def test_force_is_tree_plus_pm(ng):
+    """ng_force (the library's sum) equals ng_tree_force + ng_pm_force."""
+    import torch
+    w = small_clustered(9000, 3, 63, yukawa=True, mesh=32)
+    pos, typ, mass = device_arrays(w)
+    sim = ng.Simulation(ng_params(w["params"]))
+    ng.ng_build_tree(sim.ctx, pos, typ, mass)
+    n = typ.numel()
+    tot, short, long_ = (torch.empty((3, n), dtype=torch.float32, device=pos.device)
+                         for _ in range(3))
+    ng.ng_force(sim.ctx, tot)
+    ng.ng_tree_force(sim.ctx, short)
+    ng.ng_pm_force(sim.ctx, long_)
+    torch.cuda.synchronize()
+    sim.close()
+    s64 = short.cpu().numpy().astype(np.float64)
+    l64 = long_.cpu().numpy().astype(np.float64)
+    got = tot.cpu().numpy().astype(np.float64)
+    # one FP32 rounding of the sum, and the CIC atomics' summation order
+    scale = np.linalg.norm(s64, axis=0) + np.linalg.norm(l64, axis=0)
+    assert (np.linalg.norm(got - (s64 + l64), axis=0) <= 1e-6 * scale + 1e-30).all()
 
 
 def test_single_and_two_bodies(ng):
@@ -219,20 +237,19 @@ def test_step_host_matches_device_step(ng):
 
 @pytest.mark.parametrize("D,seed", [(3, 51), (6, 52)])
 def test_fp64_accumulated_variant(ng, D, seed):
-    """The FP64-accumulated walk (each list's FP32 sum added in FP64) meets
-    the direct-mode bound and is no less accurate than FP32 accumulation; the
-    tree-mode force of both variants meets the tree bound."""
+    """The FP64-accumulated group walk (each list's FP32 sum added in FP64) is
+    no less accurate than FP32 accumulation when nearly every leaf is opened
+    (theta = 0.05, where the opening error is far below the FP32 rounding),
+    and the tree-mode force of both variants meets the tree bound."""
     w = small_clustered(12000, D, seed, yukawa=(D == 3))
-    prm = dict(w["params"], theta=0.0)
-    ref, mag = oracle.direct_mag(oracle_params(prm), w["pos"], w["type"], w["mass"])
+    prm = dict(w["params"], theta=0.05)
+    ref = oracle.direct(oracle_params(dict(prm, theta=0.0)), w["pos"], w["type"], w["mass"])
     e = {}
     for acc64 in (0, 1):
         got = _short_force(ng, dict(prm, accumulate_fp64=acc64), w)
-        dF = np.linalg.norm(got - ref, axis=0)
-        F = np.linalg.norm(ref, axis=0)
-        assert not (dF > np.maximum(2e-5 * F, 2e-6 * mag)).any()
         e[acc64] = rel_err(got, ref)[0]
     assert np.median(e[1]) <= np.median(e[0]) * 1.05, (np.median(e[1]), np.median(e[0]))
+    assert np.percentile(e[1], 99) <= 1e-4
     tree = dict(w["params"])
     direct = ref
     cpu, _ = oracle.tree_walk(oracle_params(tree), w["pos"], w["type"], w["mass"])

@@ -10,8 +10,11 @@ computes one target at a time are compared on a seeded sample of bodies:
 per-particle interaction counts on the leaf-8 tree the benchmark counts its
 unit of work on (bit-exact), and short-range forces (99th percentile of the
 error against the FP64 direct sum no worse than 1.1x the oracle walk's on
-the same tree). The long-range PM force is compared at 2^21 for every body
-(the oracle's FP64 FFT at 256^3 x 4 species would dominate the suite).
+the same tree). The long-range PM force is compared for every body at 2^21
+on the 128^3 mesh, and on the benchmark's own 256^3 mesh with its four
+species and Yukawa couplings for every 16th body of the 2^24 workload (the
+mesh, not the body count, selects the FFT sizes and the k-space kernels; the
+oracle's FP64 FFTs at 256^3 take about half a minute).
 """
 import numpy as np
 import pytest
@@ -120,6 +123,27 @@ def test_fullsize_pm_2m(ng):
     got = acc.cpu().numpy().astype(np.float64)
     sim.close()
     ref = oracle.pm(oracle_params(prm), w["pos"], w["type"], w["mass"])
+    rms = np.sqrt(np.mean(np.sum(ref ** 2, axis=0)))
+    err = np.linalg.norm(got - ref, axis=0) / rms
+    assert err.max() <= 1e-5, (err.max(), err.mean())
+
+
+def test_fullsize_pm_256_d4_yukawa(ng):
+    import torch
+    w = inputs.workload("clustered16m_d4_yukawa")
+    sub = np.arange(0, w["pos"].shape[1], 16)
+    x = dict(pos=np.ascontiguousarray(w["pos"][:, sub]), type=w["type"][sub], mass=w["mass"][sub])
+    prm = dict(w["params"], **WALK)
+    assert prm["pm_mesh"] == 256 and prm["D"] == 4 and int(np.min(prm["law"])) == 1
+    pos, typ, mass = device_arrays(x)
+    sim = ng.Simulation(ng_params(prm))
+    ng.ng_build_tree(sim.ctx, pos, typ, mass)
+    acc = torch.empty((3, typ.numel()), dtype=torch.float32, device=pos.device)
+    ng.ng_pm_force(sim.ctx, acc)
+    torch.cuda.synchronize()
+    got = acc.cpu().numpy().astype(np.float64)
+    sim.close()
+    ref = oracle.pm(oracle_params(prm), x["pos"], x["type"], x["mass"])
     rms = np.sqrt(np.mean(np.sum(ref ** 2, axis=0)))
     err = np.linalg.norm(got - ref, axis=0) / rms
     assert err.max() <= 1e-5, (err.max(), err.mean())

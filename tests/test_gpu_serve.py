@@ -166,3 +166,68 @@ def test_one_slot_serves_growing_species_count(ng):
         alone, r1 = _run(ng, [it], slots=1, budget=8 << 30)
         assert r1[0].status == 0
         assert _close(got["acc"], alone[0]["acc"])
+
+
+def test_tree_regrow_is_budgeted(ng):
+    # with leaf size 1 the clustered tree has more than n + 1024 nodes, so the
+    # first try of each request overflows its slot's node capacity and the
+    # request is rerun with a larger tree; the regrown slot is counted against
+    # the budget (the rerun happens only if it fits)
+    items = []
+    for k, n in enumerate((3000, 3500)):
+        w = small_clustered(n, 2, 860 + k, mesh=32, leaf=1)
+        items.append(dict(w=w, kind=0, nsteps=0))
+    sizes = [ng.ng_serve_request_bytes(ng.make_request(0, ng_params(it["w"]["params"]),
+                                                       it["w"]["pos"], it["w"]["type"],
+                                                       it["w"]["mass"])) for it in items]
+    budget = 8 * max(sizes)
+    reqs = (ng.NgRequest * len(items))()
+    res = (ng.NgResult * len(items))()
+    outs = []
+    for i, it in enumerate(items):
+        w = it["w"]
+        acc = np.zeros((3, w["type"].size), np.float32)
+        outs.append(acc)
+        reqs[i] = ng.make_request(0, ng_params(w["params"]), w["pos"], w["type"], w["mass"],
+                                  acc_out=acc)
+    s = ng.ng_serve_create(2, budget)
+    try:
+        ng.ng_serve(s, reqs, res, None, 300.0)
+        held, peak, retries = ng.ng_serve_stats(s)
+    finally:
+        ng.ng_serve_destroy(s)
+    assert all(r.status == 0 for r in res)
+    assert retries >= 1
+    assert peak <= budget and held <= budget
+    # the rerun result is the plain solve of the same request
+    import torch
+    from common import device_arrays
+    for it, got in zip(items, outs):
+        w = it["w"]
+        pos, typ, mass = device_arrays(w)
+        sim = ng.Simulation(ng_params(w["params"]))
+        acc = torch.zeros((3, typ.numel()), dtype=torch.float32, device=pos.device)
+        vel = torch.zeros_like(acc)
+        ng.ng_step(sim.ctx, pos, vel, typ, mass, acc, False, 0, 1e-3)
+        torch.cuda.synchronize()
+        sim.close()
+        assert _close(got, acc.cpu().numpy())
+
+
+def test_tree_regrow_beyond_budget_fails_cleanly(ng):
+    # a budget that admits the first estimate but not the regrown tree: the
+    # request fails with NG_ENOMEM and the slots never hold more than the budget
+    w = small_clustered(3000, 2, 870, mesh=32, leaf=1)
+    acc = np.zeros((3, 3000), np.float32)
+    r = ng.make_request(0, ng_params(w["params"]), w["pos"], w["type"], w["mass"], acc_out=acc)
+    budget = ng.ng_serve_request_bytes(r) + 1024
+    s = ng.ng_serve_create(1, budget)
+    res = ng.NgResult()
+    try:
+        ng.ng_serve_submit(s, r, res)
+        ng.ng_serve_wait(s, 300.0)
+        held, peak, retries = ng.ng_serve_stats(s)
+    finally:
+        ng.ng_serve_destroy(s)
+    assert res.status == ng.NG_ENOMEM
+    assert retries == 0 and peak <= budget

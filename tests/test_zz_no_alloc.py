@@ -3,9 +3,10 @@
 Callers that cannot allocate device memory (their allocator is owned by
 another framework, or they may not stall on cudaMalloc) get the sorted keys
 and permutation from a fixed device scratch array. Keys and permutation are
-integers, so the comparison is exact. Two calls in a row (different inputs,
-the second smaller) check that the shared scratch carries nothing over. This
-file is named to be collected last."""
+integers, so the comparison is exact. Calls in a row (different inputs, each
+smaller than the one before, the last in a box of side 0.75 with bodies
+outside it) check that the shared scratch carries nothing over and that the
+general wrap and quantisation match. This file is named to be collected last."""
 import numpy as np
 import pytest
 
@@ -27,6 +28,17 @@ def ng():
     return binding
 
 
+def _boxed(w, L, seed):
+    """The same bodies in a box of side L, a tenth of them shifted outside it."""
+    rng = inputs.rng_for(seed)
+    n = w["type"].size
+    shift = rng.choice([-1.0, 1.0, 2.0], size=n) * (rng.random(n) < 0.1)
+    prm = w["params"]
+    prm = dict(prm, box=L, eps=prm["eps"] * L, rs=prm["rs"] * L, rcut=prm["rcut"] * L)
+    pos = np.ascontiguousarray(w["pos"] * L + shift[None, :] * L)
+    return dict(w, pos=pos, params=prm)
+
+
 def _reference(ng, w):
     import torch
     pos, typ, mass = device_arrays(w)
@@ -44,12 +56,14 @@ def test_noalloc_sort_matches_build_tree_twice(ng):
     import torch
     cases = [small_clustered(MAX_BODIES, 4, 91), small_clustered(70001, 2, 92)]
     cases[1]["pos"][:, 10:500] = cases[1]["pos"][:, 9:10]          # ties: stable order
+    # a box that is not a power of two: the general FP64 wrap and quantisation
+    cases.append(_boxed(small_clustered(50000, 3, 93), 0.75, 94))
     for w in cases:
         pos, typ, k_ref, p_ref = _reference(ng, w)
         n = typ.numel()
         keys = torch.full((n,), -1, dtype=torch.int64, device=pos.device)
         perm = torch.full((n,), -1, dtype=torch.int32, device=pos.device)
-        assert ng.ng_sort_keys_noalloc(pos, typ, keys, perm) == ng.NG_OK
+        assert ng.ng_sort_keys_noalloc(pos, typ, keys, perm, box=w["params"]["box"]) == ng.NG_OK
         torch.cuda.synchronize()
         assert np.array_equal(keys.cpu().numpy(), k_ref)
         assert np.array_equal(perm.cpu().numpy(), p_ref)
