@@ -121,9 +121,12 @@ def test_force_is_tree_plus_pm(ng):
     s64 = short.cpu().numpy().astype(np.float64)
     l64 = long_.cpu().numpy().astype(np.float64)
     got = tot.cpu().numpy().astype(np.float64)
-    # one FP32 rounding of the sum, and the CIC atomics' summation order
+    # one FP32 rounding of the sum, and the CIC atomics' summation order,
+    # which moves the PM part by a few 1e-7 of its rms from run to run
     scale = np.linalg.norm(s64, axis=0) + np.linalg.norm(l64, axis=0)
-    assert (np.linalg.norm(got - (s64 + l64), axis=0) <= 1e-6 * scale + 1e-30).all()
+    rms_long = np.sqrt(np.mean(np.sum(l64 ** 2, axis=0)))
+    dev = np.linalg.norm(got - (s64 + l64), axis=0)
+    assert (dev <= 1e-6 * scale + 2e-6 * rms_long).all(), (dev / (scale + rms_long)).max()
 
 
 def test_single_and_two_bodies(ng):
