@@ -49,14 +49,25 @@ void release(DevBuf& b) {
 
 // ------------------------------------------------------ short-range laws
 
-// One table per distinct law; segment k (k < ncut) is the chord of T over
-// [(k - 1/2) dr, (k + 1/2) dr] (segment 0 over [0, dr/2]), c0 + t c1 with
-// t = rho/dr - k, stored as {c0 - k c1, c1}; entry ncut is zero (beyond the cut-off,
-// which sits at rho = (ncut - 1/2) dr = r_cut). The table depends on the
-// law, r_s and r_cut only, not on the softening.
+// Short-range law tables of the walk. Segment k (k < ncut) of a law is the
+// minimax line of T over [(k - 1/2) dr, (k + 1/2) dr] (segment 0 over
+// [0, dr/2]) for a locally quadratic T: the chord raised by half its
+// deviation at the segment's middle. With t = rho/dr - k it is c0 + t c1,
+// stored as {c0 - k c1, c1}; entry ncut is zero (beyond the cut-off, which
+// sits at rho = (ncut - 1/2) dr = r_cut). The table depends on the law, r_s
+// and r_cut only, not on the softening.
+//
+// Layout (walk_tab_pad): one block per active species t of the walk's lists,
+// rows k of walk_tab_pad(D) float2 entries, entry s of the row holding the law
+// of the pair (passive s, active t). A list of species t is evaluated by all
+// lanes at once, each lane with its own passive species s and segment k;
+// entry (k, s) lies in the bank pair (k * pad + s) mod 16, so lanes of
+// different species never meet in a bank, and lanes of one species only when
+// their segments differ by a multiple of 16 / pad.
 int build_tables(ng_ctx* c) {
   const ng_params& p = c->p;
   const int D = p.D;
+  const int pad = walk_tab_pad(D);
   struct Law { int kind; double a, l; };
   std::vector<Law> laws;
   for (int i = 0; i < D; ++i)
@@ -76,7 +87,7 @@ int build_tables(ng_ctx* c) {
   int ncut = p.table_size;
   if (ncut <= 0) {
     const size_t budget = 64 * 1024;
-    ncut = (int)std::min<size_t>(4096, budget / (sizeof(float) * 2 * laws.size()) - 1);
+    ncut = (int)std::min<size_t>(4096, budget / (sizeof(float) * 2 * D * pad) - 1);
   }
   if (ncut < 16) return fail(c, NG_EINVAL, "table_size %d too small", ncut);
   c->ncut = ncut;
@@ -87,23 +98,34 @@ int build_tables(ng_ctx* c) {
   if (std::sqrt(3.0) * c->L / c->dr_phys > 4.0e6)
     return fail(c, NG_EINVAL, "box too large relative to the table spacing (box/dr = %.3g)",
                 c->L / c->dr_phys);
-  std::vector<float> h((size_t)c->nlaws * (ncut + 1) * 2, 0.f);
-  for (int u = 0; u < c->nlaws; ++u) {
-    float* t = h.data() + (size_t)u * (ncut + 1) * 2;
-    if (p.pure_tree) continue;
+  // segments of every distinct law, then the walk layout
+  std::vector<double> seg((size_t)c->nlaws * (ncut + 1) * 2, 0.0);
+  for (int u = 0; u < c->nlaws && !p.pure_tree; ++u) {
+    double* t = seg.data() + (size_t)u * (ncut + 1) * 2;
     auto T = [&](double rho) { return short_law_factor(laws[u].kind, laws[u].a, laws[u].l, c->rs, rho); };
     const double dr = c->dr_phys;
-    t[0] = (float)T(0.0);
-    t[1] = (float)(2.0 * (T(0.5 * dr) - T(0.0)));
+    {
+      const double lo = T(0.0), hi = T(0.5 * dr);
+      t[0] = lo + 0.5 * (T(0.25 * dr) - 0.5 * (lo + hi));   // value at t = 0
+      t[1] = 2.0 * (hi - lo);
+    }
     for (int k = 1; k < ncut; ++k) {
       const double lo = T((k - 0.5) * dr), hi = T((k + 0.5) * dr);
+      const double c0 = 0.25 * (lo + hi) + 0.5 * T(k * dr);
       // stored shifted: the walk evaluates (c0 - k c1) + (rho / dr) c1
-      t[2 * k] = (float)(0.5 * (lo + hi) - k * (hi - lo));
-      t[2 * k + 1] = (float)(hi - lo);
+      t[2 * k] = c0 - k * (hi - lo);
+      t[2 * k + 1] = hi - lo;
     }
-    t[2 * ncut] = 0.f;
-    t[2 * ncut + 1] = 0.f;
   }
+  std::vector<float> h((size_t)D * (ncut + 1) * pad * 2, 0.f);
+  for (int tt = 0; tt < D; ++tt)
+    for (int k = 0; k <= ncut; ++k)
+      for (int ss = 0; ss < D; ++ss) {
+        const double* g = seg.data() + ((size_t)c->tabid[ss][tt] * (ncut + 1) + k) * 2;
+        float* o = h.data() + (((size_t)tt * (ncut + 1) + k) * pad + ss) * 2;
+        o[0] = (float)g[0];
+        o[1] = (float)g[1];
+      }
   c->h_tab = h;
   NG_TRY(ensure(c, c->d_tab, h.size() * sizeof(float)));
   // upload through the context's pinned staging copy: wait until the stream

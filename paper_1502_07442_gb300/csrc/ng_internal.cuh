@@ -142,6 +142,12 @@ __device__ __forceinline__ uint64_t sort_key(double x, double y, double z, uint8
 // type offsets read back from the last pass's) are laid out by it.
 constexpr int kRadixTile = 2048;
 
+// Entries per row of the walk's law table: the passive species count rounded
+// up to a power of two (a row of the table of list species t holds the law of
+// every passive species s; see build_tables).
+__host__ __device__ constexpr int walk_tab_pad(int D) { return D <= 1 ? 1 : D == 2 ? 2 : D <= 4 ? 4 : 8; }
+__host__ __device__ constexpr int walk_tab_shift(int D) { return D <= 1 ? 0 : D == 2 ? 1 : D <= 4 ? 2 : 3; }
+
 __host__ __device__ constexpr int walk_warps(int D) { return D <= 3 ? 24 : D == 4 ? 24 : D == 5 ? 20 : 16; }
 
 // Per-simulation inputs of the walk (device memory, one per simulation).
@@ -177,10 +183,10 @@ struct WalkLaunch {
   int ndesc;
   const uint32_t* gprefix;  // [ndesc + 1] group prefix
   uint32_t* work;           // work-queue counter
-  const float2* tab;        // [law][ncut + 1] segment {c0, c1}
+  const float2* tab;        // [list species t][ncut + 1][walk_tab_pad(D)] segment {c0, c1}
   int tab_entries;          // ncut + 1
   int ncut;
-  int nlaws;
+  int tab_count;            // float2 entries of the whole table
   unsigned long long* counter;  // executed interaction counter (optional)
 };
 

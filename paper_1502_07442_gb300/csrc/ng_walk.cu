@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(walk_warps(D) * 32, 1) k_walk(WalkLaunch L) {
   using Acc = typename std::conditional<ACC64, double, float>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2* tab = reinterpret_cast<float2*>(smem_raw);
-  const int ntab = L.nlaws * L.tab_entries;
+  const int ntab = L.tab_count;
   for (int i = threadIdx.x; i < ntab; i += blockDim.x) tab[i] = L.tab[i];
   const size_t tab_bytes = ((size_t)ntab * sizeof(float2) + 15) & ~(size_t)15;
   WarpSmem<D>* ws = reinterpret_cast<WarpSmem<D>*>(smem_raw + tab_bytes) + (threadIdx.x >> 5);
@@ -203,11 +203,13 @@ __global__ void __launch_bounds__(walk_warps(D) * 32, 1) k_walk(WalkLaunch L) {
 #pragma unroll
         for (int q = 0; q < D; ++q) cnt = (q == t) ? lc[q] : cnt;
         {
-          // shared address of segment k is tb + 8 * (float bits of k + 2^23), mod 2^32,
-          // so the index needs no subtraction
+          // shared address of segment k for passive species s is
+          // tb + 8 pad * (float bits of k + 2^23), mod 2^32, so the index
+          // needs no subtraction
+          constexpr int kRowShift = 3 + walk_tab_shift(D);
           const uint32_t tb =
-              (uint32_t)__cvta_generic_to_shared(tab + (int)DESC(tabid[s][t]) * L.tab_entries) -
-              ((uint32_t)kMagicBits << 3);
+              (uint32_t)__cvta_generic_to_shared(tab + (t * L.tab_entries << walk_tab_shift(D)) + s) -
+              ((uint32_t)kMagicBits << kRowShift);
           float* lt4 = reinterpret_cast<float*>(ws->list[t]);
           // pad to an even count with a massless record (zero force); full
           // quads of records, then at most one pair
@@ -229,8 +231,8 @@ __global__ void __launch_bounds__(walk_warps(D) * 32, 1) k_walk(WalkLaunch L) {
             const int b0 = min(__float_as_int(fi.x), clampbits);
             const int b1 = min(__float_as_int(fi.y), clampbits);
             const float2 rho = __fmul2_rn(qq, inv);
-            const float2 t0 = lds_f2(tb + ((uint32_t)b0 << 3));
-            const float2 t1 = lds_f2(tb + ((uint32_t)b1 << 3));
+            const float2 t0 = lds_f2(tb + ((uint32_t)b0 << kRowShift));
+            const float2 t1 = lds_f2(tb + ((uint32_t)b1 << kRowShift));
             const float2 gg = make_float2(fmaf(rho.x, t0.y, t0.x), fmaf(rho.y, t1.y, t1.x));
             const float2 inv2 = __fmul2_rn(inv, inv);
             const float2 f = __fmul2_rn(__fmul2_rn(rm, gg), __fmul2_rn(inv2, inv));
@@ -507,16 +509,16 @@ __global__ void __launch_bounds__(1024) k_walk_prep(const WalkDesc* __restrict__
 }
 
 template <int D>
-static size_t walk_smem(int nlaws, int entries, int nwarps) {
-  const size_t tab_bytes = ((size_t)nlaws * entries * sizeof(float2) + 15) & ~(size_t)15;
+static size_t walk_smem(int tab_count, int nwarps) {
+  const size_t tab_bytes = ((size_t)tab_count * sizeof(float2) + 15) & ~(size_t)15;
   return tab_bytes + (size_t)nwarps * sizeof(WarpSmem<D>);
 }
 
 template <int D, bool ACC64, bool REL>
 static int launch_walk_d(ng_ctx* c, cudaStream_t stream, const WalkLaunch& L, int64_t groups) {
   int nwarps = walk_warps(D);
-  while (nwarps > 1 && walk_smem<D>(L.nlaws, L.tab_entries, nwarps) > c->smem_optin) --nwarps;
-  const size_t smem = walk_smem<D>(L.nlaws, L.tab_entries, nwarps);
+  while (nwarps > 1 && walk_smem<D>(L.tab_count, nwarps) > c->smem_optin) --nwarps;
+  const size_t smem = walk_smem<D>(L.tab_count, nwarps);
   if (smem > c->smem_optin)
     return fail(c, NG_ENOMEM, "walk needs %zu B shared memory (max %zu)", smem, c->smem_optin);
   // the attribute is a per-function ceiling shared by every thread that
@@ -607,7 +609,7 @@ int launch_walk_descs(ng_ctx* c, cudaStream_t stream, const WalkDesc* d_descs, i
   L.tab = as<float2>(c->d_tab);
   L.tab_entries = c->ncut + 1;
   L.ncut = c->ncut;
-  L.nlaws = c->nlaws;
+  L.tab_count = c->p.D * (c->ncut + 1) * walk_tab_pad(c->p.D);
   L.counter = counter;
   return dispatch_walk(c, stream, L, groups, rel);
 }
