@@ -91,6 +91,52 @@ def walk_traffic(workload, n_override, leaf, cell):
     return None
 
 
+def measured_peaks():
+    """Measured peaks (MEASURED_PEAKS.json beside this file), else the
+    profiling recipe's fallback copy bandwidth."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            m = json.load(fh)
+        return float(m["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def stage_bytes(n, D, mesh):
+    """Algorithmic DRAM bytes of the memory-bound stages of one force
+    evaluation (reads + writes of the arrays each stage must touch once):
+    keys 24 B position + 1 B species read, 8 B key + 4 B index written; each of
+    the 8 radix passes 8 B key read by the histogram, 12 B key + index read and
+    12 B written by the scatter; gather 4 B index + 24 B position + 4 B mass +
+    1 B species read, 24 + 4 + 1 B written; type-major order 4 B index written,
+    then one 32 B radix pass; deposit 33 B per body read plus the D mesh
+    clears; FFTs and k-space one read and one write of the D real meshes or
+    half spectra; interpolation 24 B position + 1 B species + 4 B index read,
+    12 B acceleration written (mesh reads stay in cache)."""
+    real = 4 * D * mesh ** 3
+    spec = 8 * D * mesh * mesh * (mesh // 2 + 1)
+    b = {"keys": 37 * n, "radix": 8 * 32 * n, "gather": 62 * n, "type_order": 36 * n,
+         "interp": 41 * n}
+    if mesh > 0:
+        b.update(deposit=33 * n + real, fft_fwd=real + spec, kspace=2 * spec, fft_inv=spec + real)
+    return b
+
+
+def hbm_block(times, n, D, mesh):
+    peak, src = measured_peaks()
+    out = {"peak_gbs": peak, "peak_source": f"{src} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
+    for k, nbytes in stage_bytes(n, D, mesh).items():
+        ms = times.get(k, 0.0)
+        if ms > 0:
+            gbs = nbytes / (ms / 1e3) / 1e9
+            out[k] = {"ms": round(ms, 4), "bytes": int(nbytes), "gbs": round(gbs, 1),
+                      "frac": round(gbs / peak, 4)}
+    for k in ("octree", "monopoles", "groups", "walk"):
+        if times.get(k, 0.0) > 0:
+            out[k] = {"ms": round(times[k], 4), "bound": "latency / FP64" if k != "walk" else "FP32"}
+    return out
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -342,9 +388,22 @@ def main():
     nsm = torch.cuda.get_device_properties(dev).multi_processor_count
     peak = nsm * 128 * 2 * 2070e6 / 1e12
     achieved = FLOP_PER_INTERACTION * count1 / (walk / 1e3) / 1e12
+    achieved_own = FLOP_PER_INTERACTION * count_tuned_leaf / (walk / 1e3) / 1e12
     med = clocks.get("sm_mhz") or 2070.0
+    # per-stage times of one sort + tree + force evaluation (CUDA events on the
+    # context's stream), best of three, for the HBM fractions
+    best = {}
+    for _ in range(3):
+        t = ng.ng_stage_times(sim.ctx, pos, typ, mass, acc)
+        best = {k: min(v, best.get(k, v)) for k, v in t.items()}
+    hbm = hbm_block(best, n, int(w["params"]["D"]), int(w["params"]["pm_mesh"]))
     roofline = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 2),
                 "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
+                "frac_basis": f"23 flop x per-particle interactions on the leaf-{REF_LEAF} tree "
+                              "(the metric's count)",
+                "achieved_same_tree": round(achieved_own, 3),
+                "frac_same_tree": round(achieved_own / peak, 4),
+                "frac_same_tree_basis": "23 flop x per-particle interactions on the walk's own tree",
                 "traffic": walk_traffic(args.workload,
                                         args.n if args.species is None and not args.acc64 else -1,
                                         int(w["params"]["leaf_size"]),
@@ -401,7 +460,7 @@ def main():
                                f"tree with leaf size {REF_LEAF}",
                 "interactions_per_step_at_walk_leaf": int(count_tuned_leaf),
                 "particles_per_s": job_n * args.steps / (ms / 1e3),
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+                "roofline": roofline, "hbm": hbm, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
                 "gpu_launches": int(launches), "autotune": tuned}
         print(json.dumps(line))
     if ws > 1:

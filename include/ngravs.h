@@ -400,6 +400,32 @@ int ng_serve_stats(const ng_server* s, size_t* held_bytes, size_t* peak_held_byt
                    int64_t* node_retries);
 
 /*
+ * Stages of one force evaluation, in execution order (ng_stage_times):
+ * Morton+type keys, the 8 radix passes, the gather into sorted order, the
+ * octree levels, the monopoles, the walk groups, the type-major order, the
+ * PM deposit (mesh clear + CIC), forward FFTs, k-space kernels, inverse
+ * FFTs, gradient + interpolation, and the short-range tree force.
+ */
+enum {
+  NG_STAGE_KEYS = 0, NG_STAGE_RADIX, NG_STAGE_GATHER, NG_STAGE_OCTREE, NG_STAGE_MONOPOLES,
+  NG_STAGE_GROUPS, NG_STAGE_TYPE_ORDER, NG_STAGE_DEPOSIT, NG_STAGE_FFT_FWD, NG_STAGE_KSPACE,
+  NG_STAGE_FFT_INV, NG_STAGE_INTERP, NG_STAGE_WALK, NG_NSTAGES
+};
+
+/*
+ * Measurement (no paper counterpart): builds the tree of the n bodies
+ * (device arrays as in ng_build_tree) once to size every buffer, then runs
+ * one more sort, tree build and force evaluation (ng_force into acc, device
+ * float[3][n]) with a CUDA event recorded on the context's stream before each
+ * stage and after the last, and writes the milliseconds of each stage to
+ * ms_out[NG_NSTAGES] (host; 0 for stages the context's mode does not run,
+ * e.g. the PM stages when pm_mesh == 0). Synchronises the stream. Not to be
+ * called during stream capture.
+ */
+int ng_stage_times(ng_ctx* ctx, int64_t n, const double* pos, const uint8_t* type,
+                   const float* mass, float* acc, float* ms_out);
+
+/*
  * Number of CUDA kernels this context has launched so far (host-side count,
  * library kernels only; cuFFT's own kernels are not included). A captured
  * step counts once when it is captured; each replay of the step graph adds

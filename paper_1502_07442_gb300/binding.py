@@ -94,6 +94,7 @@ def lib():
         L.ng_timestep.argtypes = [vp, i64, vp, d, d, ctypes.POINTER(d), ctypes.POINTER(ctypes.c_float)]
         L.ng_pm_force.argtypes = [vp, vp]
         L.ng_force.argtypes = [vp, vp]
+        L.ng_stage_times.argtypes = [vp, i64, vp, vp, vp, vp, vp]
         L.ng_step.argtypes = [vp, i64, vp, vp, vp, vp, vp, i32, i32, d]
         L.ng_tree_export.argtypes = [vp, ctypes.POINTER(i64)] + [vp] * 9
         L.ng_type_order.argtypes = [vp, vp, vp]
@@ -128,7 +129,8 @@ def lib():
         L.ng_last_error.restype = ctypes.c_char_p
         L.ng_version.restype = ctypes.c_char_p
         for f in ("ng_create", "ng_destroy", "ng_set_stream", "ng_build_tree", "ng_tree_force",
-                  "ng_count_interactions", "ng_pm_force", "ng_force", "ng_step", "ng_tree_export",
+                  "ng_count_interactions", "ng_pm_force", "ng_force", "ng_stage_times", "ng_step",
+                  "ng_tree_export",
                   "ng_type_order", "ng_launch_count", "ng_batch_create", "ng_batch_destroy",
                   "ng_batch_step", "ng_batch_size", "ng_batch_walk_launches",
                   "ng_batch_launch_count", "ng_serve_create", "ng_serve_destroy",
@@ -142,8 +144,8 @@ def lib():
 def exported_symbols():
     """Names the header declares (used by the ABI test)."""
     return ["ng_create", "ng_destroy", "ng_set_stream", "ng_build_tree", "ng_tree_force",
-            "ng_count_interactions", "ng_pm_force", "ng_force", "ng_step", "ng_tree_export",
-            "ng_type_order",
+            "ng_count_interactions", "ng_pm_force", "ng_force", "ng_stage_times", "ng_step",
+            "ng_tree_export", "ng_type_order",
             "ng_launch_count", "ng_last_error", "ng_version", "ng_batch_create",
             "ng_batch_destroy", "ng_batch_step", "ng_batch_size", "ng_batch_walk_launches",
             "ng_batch_launch_count", "ng_batch_last_error", "ng_serve_create",
@@ -265,6 +267,18 @@ def ng_pm_force(ctx, acc_out):
 def ng_force(ctx, acc_out):
     """Short-range tree plus long-range PM acceleration, summed in the library."""
     _check(ctx, lib().ng_force(ctx, _ptr(acc_out)))
+
+
+STAGES = ("keys", "radix", "gather", "octree", "monopoles", "groups", "type_order", "deposit",
+          "fft_fwd", "kspace", "fft_inv", "interp", "walk")
+
+
+def ng_stage_times(ctx, pos, typ, mass, acc):
+    """Milliseconds of each stage of one sort + tree + force evaluation (dict)."""
+    out = (ctypes.c_float * len(STAGES))()
+    _check(ctx, lib().ng_stage_times(ctx, typ.numel(), _ptr(pos), _ptr(typ), _ptr(mass), _ptr(acc),
+                                     out))
+    return {k: float(v) for k, v in zip(STAGES, out)}
 
 
 def ng_step(ctx, pos, vel, typ, mass, acc, acc_valid, nsteps, dt):

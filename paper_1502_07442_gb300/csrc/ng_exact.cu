@@ -387,6 +387,7 @@ int build_lattice(ng_ctx* c, int nlaws, const int* kind, const double* a, const 
 // the exact-law walk in pure tree mode, the FP64 pair sum in direct mode
 // (theta = 0), the FP32 group walk otherwise.
 int launch_tree_force(ng_ctx* c, float* acc, bool accumulate, bool count) {
+  stage_mark(c, NG_STAGE_WALK);
   if (c->p.pure_tree) return launch_walk_exact(c, acc, accumulate, count);
   if (direct_mode(c)) return launch_direct64(c, acc, accumulate, count);
   return launch_walk(c, acc, accumulate, count);

@@ -142,6 +142,12 @@ __device__ __forceinline__ uint64_t sort_key(double x, double y, double z, uint8
 // type offsets read back from the last pass's) are laid out by it.
 constexpr int kRadixTile = 2048;
 
+// Packed law-table segment: the value at the segment's centre in the high
+// kTabValueBits bits and the slope in the low kTabSlopeBits bits, each a
+// fixed-point code on a power-of-two grid shared by every law of the table.
+constexpr int kTabValueBits = 21;
+constexpr int kTabSlopeBits = 11;
+
 // Entries per row of the walk's law table: the passive species count rounded
 // up to a power of two (a row of the table of list species t holds the law of
 // every passive species s; see build_tables).
@@ -183,10 +189,12 @@ struct WalkLaunch {
   int ndesc;
   const uint32_t* gprefix;  // [ndesc + 1] group prefix
   uint32_t* work;           // work-queue counter
-  const float2* tab;        // [list species t][ncut + 1][walk_tab_pad(D)] segment {c0, c1}
+  const uint32_t* tab;      // [list species t][ncut + 1][walk_tab_pad(D)] packed segment
   int tab_entries;          // ncut + 1
   int ncut;
-  int tab_count;            // float2 entries of the whole table
+  int tab_count;            // entries of the whole table
+  float vscale, voff;       // value = float(2^23 + code >> 11) * vscale + voff
+  float sscale, soff;       // slope = float(2^23 + code & 0x7ff) * sscale + soff
   unsigned long long* counter;  // executed interaction counter (optional)
 };
 
@@ -209,7 +217,8 @@ struct ng_ctx {
   int8_t tabid[ng::kMaxD][ng::kMaxD]{};
   double dr_phys = 0;                 // table spacing (physical length)
   ng::DevBuf d_tab;
-  std::vector<float> h_tab;           // host copy (tables of a batch are matched on it)
+  std::vector<uint32_t> h_tab;        // host copy of the packed segments (batches match on it)
+  float tab_dec[4] = {0.f, 0.f, 0.f, 0.f};   // decode: value scale, offset; slope scale, offset
   void* h_tab_pinned = nullptr;       // pinned staging copy of the table upload
   size_t h_tab_pinned_bytes = 0;
 
@@ -242,6 +251,11 @@ struct ng_ctx {
   cufftHandle plan_r2c = 0, plan_c2r = 0;   // the plans of the current (mesh, D)
   ng::DevBuf rho, rhok, phi;
 
+  // stage timer of ng_stage_times: when on, each stage records its start event
+  bool timing = false;
+  uint32_t stage_seen = 0;       // stages marked during the current measurement
+  cudaEvent_t stage_ev[NG_NSTAGES + 1]{};
+
   // kernels this library has launched (host-side count)
   uint64_t launches = 0;
   uint64_t graph_launches = 0;     // kernels in one captured step
@@ -257,6 +271,14 @@ struct ng_ctx {
 };
 
 namespace ng {
+
+// Stage timer: record the start of stage s on the context's stream (a no-op
+// unless ng_stage_times is measuring).
+inline void stage_mark(ng_ctx* c, int s) {
+  if (!c->timing) return;
+  cudaEventRecord(c->stage_ev[s], c->stream);
+  c->stage_seen |= 1u << s;
+}
 
 // Error helpers: record a message on ctx and return a code.
 int fail(ng_ctx* c, int code, const char* fmt, ...);

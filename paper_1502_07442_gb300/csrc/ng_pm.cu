@@ -195,6 +195,7 @@ int pm_force(ng_ctx* c, float* acc, bool accumulate) {
   NG_TRY(pm_setup(c));
   const size_t N3 = (size_t)N * N * N;
   const double L = c->L;
+  stage_mark(c, NG_STAGE_DEPOSIT);
   NG_CUDA(c, cudaMemsetAsync(c->rho.p, 0, (size_t)D * N3 * sizeof(float), c->stream));
   const int grid = work_grid(c, c->n, 8);
   const int kgrid = work_grid(c, (int64_t)N * N * (N / 2 + 1), 8);
@@ -206,6 +207,7 @@ int pm_force(ng_ctx* c, float* acc, bool accumulate) {
   if (cufftSetStream(c->plan_r2c, c->stream) != CUFFT_SUCCESS ||
       cufftSetStream(c->plan_c2r, c->stream) != CUFFT_SUCCESS)
     return fail(c, NG_ECUDA, "cufftSetStream failed");
+  stage_mark(c, NG_STAGE_FFT_FWD);
   if (cufftExecR2C(c->plan_r2c, as<cufftReal>(c->rho), as<cufftComplex>(c->rhok)) != CUFFT_SUCCESS)
     return fail(c, NG_ECUDA, "cufftExecR2C failed");
   PmLaw law{};
@@ -223,6 +225,7 @@ int pm_force(ng_ctx* c, float* acc, bool accumulate) {
   const float pref = (float)(-4.0 * M_PI / (L * L * L));
   const float rs2 = (float)(c->rs * c->rs);
   cufftComplex* mk = as<cufftComplex>(c->rhok);
+  stage_mark(c, NG_STAGE_KSPACE);
   switch (D) {
     case 1: k_kspace<1><<<kgrid, 256, 0, c->stream>>>(mk, N, kf, rs2, pref, law); break;
     case 2: k_kspace<2><<<kgrid, 256, 0, c->stream>>>(mk, N, kf, rs2, pref, law); break;
@@ -232,8 +235,10 @@ int pm_force(ng_ctx* c, float* acc, bool accumulate) {
     default: k_kspace<6><<<kgrid, 256, 0, c->stream>>>(mk, N, kf, rs2, pref, law); break;
   }
   NG_CUDA(c, cudaGetLastError());
+  stage_mark(c, NG_STAGE_FFT_INV);
   if (cufftExecC2R(c->plan_c2r, mk, as<cufftReal>(c->phi)) != CUFFT_SUCCESS)
     return fail(c, NG_ECUDA, "cufftExecC2R failed");
+  stage_mark(c, NG_STAGE_INTERP);
   k_pm_interp<<<grid, 256, 0, c->stream>>>(c->n, as<double>(c->spos), as<uint8_t>(c->stype),
                                           as<uint32_t>(c->vals_a), as<float>(c->phi), N,
                                           (double)N / L, (float)(N / L), acc, accumulate ? 1 : 0);

@@ -324,16 +324,19 @@ int sort_bodies(ng_ctx* c, int64_t n, const double* pos, const uint8_t* type, co
   uint32_t *va = as<uint32_t>(c->vals_a), *vb = as<uint32_t>(c->vals_b);
   const int grid = work_grid(c, n, 8);
   const bool pow2 = box_is_pow2(c->L);
+  stage_mark(c, NG_STAGE_KEYS);
   k_keys<<<grid, 256, 0, c->stream>>>(n, pos, type, c->L, 1.0 / c->L, pow2,
                                       pow2 ? std::ilogb(c->L) : 0, ka, va);
   c->launches += 2;   // keys + gather
   NG_CUDA(c, cudaGetLastError());
   // 8 passes of 8 bits: the result returns to (ka, va)
+  stage_mark(c, NG_STAGE_RADIX);
   for (int pass = 0; pass < 8; ++pass) {
     const bool even = (pass & 1) == 0;
     NG_TRY(radix_pass(c, even ? ka : kb, even ? va : vb, even ? kb : ka, even ? vb : va, n,
                       8 * pass, 0xffu));
   }
+  stage_mark(c, NG_STAGE_GATHER);
   k_gather<<<grid, 256, 0, c->stream>>>(n, va, pos, type, mass, c->L, 1.0 / c->L, pow2, c->p.D,
                                         as<double>(c->spos), as<float>(c->smass),
                                         as<uint8_t>(c->stype), as<uint32_t>(c->status));
@@ -348,6 +351,7 @@ int type_order(ng_ctx* c) {
   const int grid = work_grid(c, n, 8);
   uint64_t *ka = as<uint64_t>(c->keys_a), *kb = as<uint64_t>(c->keys_b);
   uint32_t* vb = as<uint32_t>(c->vals_b);
+  stage_mark(c, NG_STAGE_TYPE_ORDER);
   k_iota<<<grid, 256, 0, c->stream>>>(n, vb);
   c->launches += 1;
   NG_CUDA(c, cudaGetLastError());

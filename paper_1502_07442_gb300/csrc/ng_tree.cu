@@ -165,6 +165,7 @@ int build_octree(ng_ctx* c) {
   uint32_t* tmp = as<uint32_t>(c->n_tmp);
   const uint64_t* keys = as<uint64_t>(c->keys_a);
   const int leaf = c->p.leaf_size;
+  stage_mark(c, NG_STAGE_OCTREE);
   k_tree_init<<<1, 32, 0, c->stream>>>(st, n, level, prefix, first, count);
   c->launches += 1 + (kMaxLevel + 1) + kMaxLevel;   // init, counts, emits (scans count themselves)
   for (int l = 0; l <= kMaxLevel; ++l) {
@@ -350,6 +351,7 @@ int reduce_monopoles(ng_ctx* c) {
   a.invL = 1.0 / c->L;
   a.L = c->L;
   c->launches += kMaxLevel + 1;
+  stage_mark(c, NG_STAGE_MONOPOLES);
   for (int l = kMaxLevel; l >= 0; --l) {
     const int64_t nodes = std::min<int64_t>(c->cap_nodes, level_bound(l, c->n));
     const int grid = (int)std::max<int64_t>(
@@ -439,6 +441,7 @@ int build_groups(ng_ctx* c) {
   NG_TRY(ensure(c, c->grank, (size_t)n * sizeof(uint32_t)));
   uint32_t* gsize = as<uint32_t>(c->gsize);
   uint32_t* grank = as<uint32_t>(c->grank);
+  stage_mark(c, NG_STAGE_GROUPS);
   NG_CUDA(c, cudaMemsetAsync(gsize, 0, (size_t)n * sizeof(uint32_t), c->stream));
   c->launches += 2;   // groups, compaction (the flag scan counts itself)
   k_groups<<<work_grid(c, std::min<int64_t>(c->cap_nodes, 2 * n + 64), 4), 256, 0, c->stream>>>(

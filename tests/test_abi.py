@@ -120,3 +120,21 @@ def test_calls_reject_null_context(binding):
     assert L.ng_pm_force(None, None) == binding.NG_EINVAL
     assert L.ng_destroy(None) == binding.NG_OK
     assert "sm_103a" in binding.ng_version()
+
+
+def test_stage_names_follow_the_header(binding, tmp_path):
+    # the binding's stage names are the header's NG_STAGE_* enumerators, in order
+    text = open(HEADER).read()
+    names = re.findall(r"NG_STAGE_([A-Z_]+)", text)
+    seen = []
+    for s in names:
+        if s.lower() not in seen:
+            seen.append(s.lower())
+    assert tuple(seen) == binding.STAGES
+    src = tmp_path / "st.c"
+    src.write_text('#include <stdio.h>\n#include "ngravs.h"\n'
+                   'int main(void){printf("%d %d\\n", (int)NG_NSTAGES, (int)NG_STAGE_WALK);return 0;}\n')
+    exe = tmp_path / "st"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    n, walk = map(int, subprocess.check_output([str(exe)]).split())
+    assert n == len(binding.STAGES) and walk == n - 1
