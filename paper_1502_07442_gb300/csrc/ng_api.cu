@@ -52,21 +52,18 @@ void release(DevBuf& b) {
 // Short-range law tables of the walk. Segment k (k < ncut) of a law is the
 // minimax line of T over [(k - 1/2) dr, (k + 1/2) dr] (segment 0 over
 // [0, dr/2]) for a locally quadratic T: the chord raised by half its
-// deviation at the segment's middle, c0 + t c1 with t = rho/dr - k; entry
-// ncut is zero (beyond the cut-off, which sits at rho = (ncut - 1/2) dr =
-// r_cut). The table depends on the law, r_s and r_cut only, not on the
-// softening.
-//
-// Each segment is packed into 32 bits, c0 as a kTabValueBits-bit and c1 as a
-// kTabSlopeBits-bit fixed-point code; the two grids have power-of-two steps
-// and contain zero, so the decoded zero row is exactly 0. A 4-byte entry is
-// read by one 32-bit shared load: the 32 lanes of a warp read at
-// data-dependent segments, and 32-bit loads spread them over 32 banks, where
-// 64-bit loads would use 16 bank pairs.
+// deviation at the segment's middle. With t = rho/dr - k it is c0 + t c1,
+// stored as {c0 - k c1, c1}; entry ncut is zero (beyond the cut-off, which
+// sits at rho = (ncut - 1/2) dr = r_cut). The table depends on the law, r_s
+// and r_cut only, not on the softening.
 //
 // Layout (walk_tab_pad): one block per active species t of the walk's lists,
-// rows k of walk_tab_pad(D) entries, entry s of the row holding the law of
-// the pair (passive s, active t).
+// rows k of walk_tab_pad(D) float2 entries, entry s of the row holding the law
+// of the pair (passive s, active t). A list of species t is evaluated by all
+// lanes at once, each lane with its own passive species s and segment k;
+// entry (k, s) lies in the bank pair (k * pad + s) mod 16, so lanes of
+// different species never meet in a bank, and lanes of one species only when
+// their segments differ by a multiple of 16 / pad.
 int build_tables(ng_ctx* c) {
   const ng_params& p = c->p;
   const int D = p.D;
@@ -90,7 +87,7 @@ int build_tables(ng_ctx* c) {
   int ncut = p.table_size;
   if (ncut <= 0) {
     const size_t budget = 64 * 1024;
-    ncut = (int)std::min<size_t>(4096, budget / (sizeof(uint32_t) * D * pad) - 1);
+    ncut = (int)std::min<size_t>(4096, budget / (sizeof(float) * 2 * D * pad) - 1);
   }
   if (ncut < 16) return fail(c, NG_EINVAL, "table_size %d too small", ncut);
   c->ncut = ncut;
@@ -101,7 +98,7 @@ int build_tables(ng_ctx* c) {
   if (std::sqrt(3.0) * c->L / c->dr_phys > 4.0e6)
     return fail(c, NG_EINVAL, "box too large relative to the table spacing (box/dr = %.3g)",
                 c->L / c->dr_phys);
-  // segments {c0, c1} of every distinct law
+  // segments of every distinct law, then the walk layout
   std::vector<double> seg((size_t)c->nlaws * (ncut + 1) * 2, 0.0);
   for (int u = 0; u < c->nlaws && !p.pure_tree; ++u) {
     double* t = seg.data() + (size_t)u * (ncut + 1) * 2;
@@ -114,66 +111,35 @@ int build_tables(ng_ctx* c) {
     }
     for (int k = 1; k < ncut; ++k) {
       const double lo = T((k - 0.5) * dr), hi = T((k + 0.5) * dr);
-      t[2 * k] = 0.25 * (lo + hi) + 0.5 * T(k * dr);
+      const double c0 = 0.25 * (lo + hi) + 0.5 * T(k * dr);
+      // stored shifted: the walk evaluates (c0 - k c1) + (rho / dr) c1
+      t[2 * k] = c0 - k * (hi - lo);
       t[2 * k + 1] = hi - lo;
     }
   }
-  // fixed-point grids: the smallest power-of-two step that spans [min, max]
-  // (zero included) with the code width, codes offset so that zero is a code
-  auto grid = [](double lo, double hi, int bits, double* step, int64_t* zero) {
-    lo = std::min(lo, 0.0);
-    hi = std::max(hi, 0.0);
-    const double span = std::max(hi - lo, 1e-30);
-    int e = (int)std::ceil(std::log2(span / (double)((1 << bits) - 2)));
-    double st = std::ldexp(1.0, e);
-    while (std::ceil(-lo / st) + std::floor(hi / st) > (double)((1 << bits) - 1)) st *= 2.0;
-    *step = st;
-    *zero = (int64_t)std::ceil(-lo / st);
-  };
-  double vlo = 0, vhi = 0, slo = 0, shi = 0;
-  for (size_t i = 0; i < seg.size(); i += 2) {
-    vlo = std::min(vlo, seg[i]);
-    vhi = std::max(vhi, seg[i]);
-    slo = std::min(slo, seg[i + 1]);
-    shi = std::max(shi, seg[i + 1]);
-  }
-  double vstep, sstep;
-  int64_t vzero, szero;
-  grid(vlo, vhi, kTabValueBits, &vstep, &vzero);
-  grid(slo, shi, kTabSlopeBits, &sstep, &szero);
-  const int64_t vmax = (1 << kTabValueBits) - 1, smax = (1 << kTabSlopeBits) - 1;
-  auto code = [&](const double* g) -> uint32_t {
-    const int64_t v = std::min<int64_t>(vmax, std::max<int64_t>(0, vzero + std::llrint(g[0] / vstep)));
-    const int64_t sl = std::min<int64_t>(smax, std::max<int64_t>(0, szero + std::llrint(g[1] / sstep)));
-    return (uint32_t)(v << kTabSlopeBits) | (uint32_t)sl;
-  };
-  // decode: value = (2^23 + v) vstep - (2^23 + vzero) vstep, exact in FP32
-  c->tab_dec[0] = (float)vstep;
-  c->tab_dec[1] = (float)(-(8388608.0 + (double)vzero) * vstep);
-  c->tab_dec[2] = (float)sstep;
-  c->tab_dec[3] = (float)(-(8388608.0 + (double)szero) * sstep);
-  const double zero_row[2] = {0.0, 0.0};
-  std::vector<uint32_t> h((size_t)D * (ncut + 1) * pad, code(zero_row));
+  std::vector<float> h((size_t)D * (ncut + 1) * pad * 2, 0.f);
   for (int tt = 0; tt < D; ++tt)
     for (int k = 0; k <= ncut; ++k)
       for (int ss = 0; ss < D; ++ss) {
         const double* g = seg.data() + ((size_t)c->tabid[ss][tt] * (ncut + 1) + k) * 2;
-        h[((size_t)tt * (ncut + 1) + k) * pad + ss] = code(g);
+        float* o = h.data() + (((size_t)tt * (ncut + 1) + k) * pad + ss) * 2;
+        o[0] = (float)g[0];
+        o[1] = (float)g[1];
       }
   c->h_tab = h;
-  NG_TRY(ensure(c, c->d_tab, h.size() * sizeof(uint32_t)));
+  NG_TRY(ensure(c, c->d_tab, h.size() * sizeof(float)));
   // upload through the context's pinned staging copy: wait until the stream
   // has consumed the previous contents, then copy without a pageable stall
   NG_CUDA(c, cudaStreamSynchronize(c->stream));
-  if (c->h_tab_pinned_bytes < h.size() * sizeof(uint32_t)) {
+  if (c->h_tab_pinned_bytes < h.size() * sizeof(float)) {
     if (c->h_tab_pinned) cudaFreeHost(c->h_tab_pinned);
     c->h_tab_pinned = nullptr;
     c->h_tab_pinned_bytes = 0;
-    NG_CUDA(c, cudaHostAlloc(&c->h_tab_pinned, h.size() * sizeof(uint32_t), cudaHostAllocDefault));
-    c->h_tab_pinned_bytes = h.size() * sizeof(uint32_t);
+    NG_CUDA(c, cudaHostAlloc(&c->h_tab_pinned, h.size() * sizeof(float), cudaHostAllocDefault));
+    c->h_tab_pinned_bytes = h.size() * sizeof(float);
   }
-  std::memcpy(c->h_tab_pinned, h.data(), h.size() * sizeof(uint32_t));
-  NG_CUDA(c, cudaMemcpyAsync(c->d_tab.p, c->h_tab_pinned, h.size() * sizeof(uint32_t),
+  std::memcpy(c->h_tab_pinned, h.data(), h.size() * sizeof(float));
+  NG_CUDA(c, cudaMemcpyAsync(c->d_tab.p, c->h_tab_pinned, h.size() * sizeof(float),
                              cudaMemcpyHostToDevice, c->stream));
   c->lattice_grid = 0;
   if (p.pure_tree == 2) {

@@ -62,8 +62,7 @@ int from_sim(ng_batch* b, int i, int code) {
 bool same_table(const ng_ctx* a, const ng_ctx* c) {
   return a->p.D == c->p.D && a->p.accumulate_fp64 == c->p.accumulate_fp64 &&
          a->nlaws == c->nlaws && a->ncut == c->ncut &&
-         a->dr_phys == c->dr_phys && a->h_tab == c->h_tab &&
-         std::memcmp(a->tab_dec, c->tab_dec, sizeof(a->tab_dec)) == 0;
+         a->dr_phys == c->dr_phys && a->h_tab == c->h_tab;
 }
 
 uint64_t alloc_gen(const ng_batch* b) {

@@ -142,12 +142,6 @@ __device__ __forceinline__ uint64_t sort_key(double x, double y, double z, uint8
 // type offsets read back from the last pass's) are laid out by it.
 constexpr int kRadixTile = 2048;
 
-// Packed law-table segment: the value at the segment's centre in the high
-// kTabValueBits bits and the slope in the low kTabSlopeBits bits, each a
-// fixed-point code on a power-of-two grid shared by every law of the table.
-constexpr int kTabValueBits = 21;
-constexpr int kTabSlopeBits = 11;
-
 // Entries per row of the walk's law table: the passive species count rounded
 // up to a power of two (a row of the table of list species t holds the law of
 // every passive species s; see build_tables).
@@ -189,12 +183,10 @@ struct WalkLaunch {
   int ndesc;
   const uint32_t* gprefix;  // [ndesc + 1] group prefix
   uint32_t* work;           // work-queue counter
-  const uint32_t* tab;      // [list species t][ncut + 1][walk_tab_pad(D)] packed segment
+  const float2* tab;        // [list species t][ncut + 1][walk_tab_pad(D)] segment {c0, c1}
   int tab_entries;          // ncut + 1
   int ncut;
-  int tab_count;            // entries of the whole table
-  float vscale, voff;       // value = float(2^23 + code >> 11) * vscale + voff
-  float sscale, soff;       // slope = float(2^23 + code & 0x7ff) * sscale + soff
+  int tab_count;            // float2 entries of the whole table
   unsigned long long* counter;  // executed interaction counter (optional)
 };
 
@@ -217,8 +209,7 @@ struct ng_ctx {
   int8_t tabid[ng::kMaxD][ng::kMaxD]{};
   double dr_phys = 0;                 // table spacing (physical length)
   ng::DevBuf d_tab;
-  std::vector<uint32_t> h_tab;        // host copy of the packed segments (batches match on it)
-  float tab_dec[4] = {0.f, 0.f, 0.f, 0.f};   // decode: value scale, offset; slope scale, offset
+  std::vector<float> h_tab;           // host copy (tables of a batch are matched on it)
   void* h_tab_pinned = nullptr;       // pinned staging copy of the table upload
   size_t h_tab_pinned_bytes = 0;
 

@@ -19,10 +19,9 @@
 //
 // Inner loop per (body, record): q = |d|^2 + eps^2, inv = rsqrt(q); the
 // table index k = rint(rho), rho = q * inv, is read from the float bits of
-// q*inv + 2^23; the table holds one linear segment per index, packed in 32
-// bits as fixed-point codes of its value c0 at rho = k and its slope c1, so
-// that the factor is c0 + (rho - k) c1 (zero past the cut-off); the force is
-// m * factor * inv^3 * d, summed over one species list;
+// q*inv + 2^23; the table holds one linear segment per index, stored as
+// {c0 - k c1, c1} so that its value is (c0 - k c1) + rho c1 (zero past the
+// cut-off); the force is m * value * inv^3 * d, summed over one species list;
 // each list's sum is scaled by the coupling G[s][t] of the body's species s
 // and the list's species t and added to one accumulator per body.
 #include <type_traits>
@@ -70,10 +69,10 @@ __device__ __forceinline__ void put_rec(float4* list, int slot, float x, float y
   c[3 * kListCap + slot] = m;
 }
 
-// 4-byte shared-memory load from a 32-bit shared address
-__device__ __forceinline__ uint32_t lds_u32(uint32_t addr) {
-  uint32_t v;
-  asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(addr));
+// 8-byte shared-memory load from a 32-bit shared address
+__device__ __forceinline__ float2 lds_f2(uint32_t addr) {
+  float2 v;
+  asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(addr));
   return v;
 }
 
@@ -89,10 +88,10 @@ template <int D, bool ACC64, bool REL>
 __global__ void __launch_bounds__(walk_warps(D) * 32, 1) k_walk(WalkLaunch L) {
   using Acc = typename std::conditional<ACC64, double, float>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  uint32_t* tab = reinterpret_cast<uint32_t*>(smem_raw);
+  float2* tab = reinterpret_cast<float2*>(smem_raw);
   const int ntab = L.tab_count;
   for (int i = threadIdx.x; i < ntab; i += blockDim.x) tab[i] = L.tab[i];
-  const size_t tab_bytes = ((size_t)ntab * sizeof(uint32_t) + 15) & ~(size_t)15;
+  const size_t tab_bytes = ((size_t)ntab * sizeof(float2) + 15) & ~(size_t)15;
   WarpSmem<D>* ws = reinterpret_cast<WarpSmem<D>*>(smem_raw + tab_bytes) + (threadIdx.x >> 5);
   __syncthreads();
 
@@ -205,9 +204,9 @@ __global__ void __launch_bounds__(walk_warps(D) * 32, 1) k_walk(WalkLaunch L) {
         for (int q = 0; q < D; ++q) cnt = (q == t) ? lc[q] : cnt;
         {
           // shared address of segment k for passive species s is
-          // tb + 4 pad * (float bits of k + 2^23), mod 2^32, so the index
+          // tb + 8 pad * (float bits of k + 2^23), mod 2^32, so the index
           // needs no subtraction
-          constexpr int kRowShift = 2 + walk_tab_shift(D);
+          constexpr int kRowShift = 3 + walk_tab_shift(D);
           const uint32_t tb =
               (uint32_t)__cvta_generic_to_shared(tab + (t * L.tab_entries << walk_tab_shift(D)) + s) -
               ((uint32_t)kMagicBits << kRowShift);
@@ -222,9 +221,7 @@ __global__ void __launch_bounds__(walk_warps(D) * 32, 1) k_walk(WalkLaunch L) {
           // operations; each half rounds exactly as the scalar operation
           const float2 nx = make_float2(-xr, -xr), ny = make_float2(-yr, -yr),
                        nz = make_float2(-zr, -zr), e2 = make_float2(eps2, eps2),
-                       mg = make_float2(kMagic, kMagic),
-                       vs = make_float2(L.vscale, L.vscale), vo = make_float2(L.voff, L.voff),
-                       ss = make_float2(L.sscale, L.sscale), so = make_float2(L.soff, L.soff);
+                       mg = make_float2(kMagic, kMagic);
           float2 sx2 = make_float2(0.f, 0.f), sy2 = sx2, sz2 = sx2;
           auto pair = [&](float2 rx, float2 ry, float2 rz, float2 rm) {
             const float2 dx = __fadd2_rn(rx, nx), dy = __fadd2_rn(ry, ny), dz = __fadd2_rn(rz, nz);
@@ -234,20 +231,9 @@ __global__ void __launch_bounds__(walk_warps(D) * 32, 1) k_walk(WalkLaunch L) {
             const int b0 = min(__float_as_int(fi.x), clampbits);
             const int b1 = min(__float_as_int(fi.y), clampbits);
             const float2 rho = __fmul2_rn(qq, inv);
-            const uint32_t e0 = lds_u32(tb + ((uint32_t)b0 << kRowShift));
-            const uint32_t e1 = lds_u32(tb + ((uint32_t)b1 << kRowShift));
-            // decode (2^23 + code) exactly as floats, then scale: segment value
-            // at its centre k and slope per table unit; t = rho - k, with
-            // k = (rho + 2^23 rounded) - 2^23 exact
-            const float2 val = __ffma2_rn(
-                make_float2(__uint_as_float((e0 >> kTabSlopeBits) | (uint32_t)kMagicBits),
-                            __uint_as_float((e1 >> kTabSlopeBits) | (uint32_t)kMagicBits)), vs, vo);
-            const uint32_t smask = (1u << kTabSlopeBits) - 1u;
-            const float2 slo = __ffma2_rn(
-                make_float2(__uint_as_float((e0 & smask) | (uint32_t)kMagicBits),
-                            __uint_as_float((e1 & smask) | (uint32_t)kMagicBits)), ss, so);
-            const float2 tt = __fadd2_rn(rho, __fadd2_rn(mg, make_float2(-fi.x, -fi.y)));
-            const float2 gg = __ffma2_rn(tt, slo, val);
+            const float2 t0 = lds_f2(tb + ((uint32_t)b0 << kRowShift));
+            const float2 t1 = lds_f2(tb + ((uint32_t)b1 << kRowShift));
+            const float2 gg = make_float2(fmaf(rho.x, t0.y, t0.x), fmaf(rho.y, t1.y, t1.x));
             const float2 inv2 = __fmul2_rn(inv, inv);
             const float2 f = __fmul2_rn(__fmul2_rn(rm, gg), __fmul2_rn(inv2, inv));
             sx2 = __ffma2_rn(f, dx, sx2);
@@ -524,7 +510,7 @@ __global__ void __launch_bounds__(1024) k_walk_prep(const WalkDesc* __restrict__
 
 template <int D>
 static size_t walk_smem(int tab_count, int nwarps) {
-  const size_t tab_bytes = ((size_t)tab_count * sizeof(uint32_t) + 15) & ~(size_t)15;
+  const size_t tab_bytes = ((size_t)tab_count * sizeof(float2) + 15) & ~(size_t)15;
   return tab_bytes + (size_t)nwarps * sizeof(WarpSmem<D>);
 }
 
@@ -620,11 +606,7 @@ int launch_walk_descs(ng_ctx* c, cudaStream_t stream, const WalkDesc* d_descs, i
   L.ndesc = ndesc;
   L.gprefix = d_prefix;
   L.work = d_work;
-  L.tab = as<uint32_t>(c->d_tab);
-  L.vscale = c->tab_dec[0];
-  L.voff = c->tab_dec[1];
-  L.sscale = c->tab_dec[2];
-  L.soff = c->tab_dec[3];
+  L.tab = as<float2>(c->d_tab);
   L.tab_entries = c->ncut + 1;
   L.ncut = c->ncut;
   L.tab_count = c->p.D * (c->ncut + 1) * walk_tab_pad(c->p.D);
