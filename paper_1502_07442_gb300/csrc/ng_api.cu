@@ -260,6 +260,21 @@ int alloc_bodies(ng_ctx* c, int64_t n) {
   return NG_OK;
 }
 
+// Every device buffer and cuFFT plan that one force evaluation (and the KDK
+// steps of ng_step's stages) of n bodies needs, so that the stages that
+// follow allocate nothing.
+int reserve(ng_ctx* c, int64_t n) {
+  NG_TRY(alloc_bodies(c, n));
+  NG_TRY(alloc_nodes(c, std::max<int64_t>(c->cap_nodes, n + 1024)));
+  NG_TRY(reserve_sort(c, n));
+  NG_TRY(ensure(c, c->gsize, (size_t)n * sizeof(uint32_t)));
+  NG_TRY(ensure(c, c->grank, (size_t)n * sizeof(uint32_t)));
+  NG_TRY(ensure(c, c->walk_desc, sizeof(WalkDesc)));
+  NG_TRY(ensure(c, c->walk_prefix, 4 * sizeof(uint32_t)));
+  if (c->p.opening == NG_OPEN_RELATIVE) NG_TRY(ensure(c, c->aold, (size_t)n * sizeof(float)));
+  return pm_reserve(c);
+}
+
 // Everything after the sort; no host synchronisation.
 int tree_stages(ng_ctx* c) {
   NG_TRY(build_octree(c));

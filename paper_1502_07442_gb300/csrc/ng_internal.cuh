@@ -331,6 +331,11 @@ bool relative_active(const ng_ctx* c);
 double coupling_max(const ng_ctx* c);
 int update_aold(ng_ctx* c, const float* acc);
 int pm_force(ng_ctx* c, float* acc, bool accumulate);
+int pm_reserve(ng_ctx* c);                     // meshes and cuFFT plans of the context's mesh
+int reserve_sort(ng_ctx* c, int64_t n);        // sort buffers for n bodies
+// Every buffer and plan a force evaluation of n bodies needs (allocates on the
+// calling thread; the stages that follow then allocate nothing).
+int reserve(ng_ctx* c, int64_t n);
 extern std::mutex g_fft_plan_lock;   // see pm_setup
 int type_order(ng_ctx* c);
 

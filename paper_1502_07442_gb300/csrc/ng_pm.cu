@@ -189,6 +189,8 @@ static int pm_setup(ng_ctx* c) {
   return NG_OK;
 }
 
+int pm_reserve(ng_ctx* c) { return c->p.pm_mesh > 0 ? pm_setup(c) : NG_OK; }
+
 int pm_force(ng_ctx* c, float* acc, bool accumulate) {
   const int N = c->p.pm_mesh, D = c->p.D;
   if (N <= 0) return fail(c, NG_ESTATE, "pm_mesh is 0: no long-range step configured");

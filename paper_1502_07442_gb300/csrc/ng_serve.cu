@@ -101,28 +101,35 @@ int sfail(ng_server* s, int code, const char* msg) {
 // Message of the last failed ng_serve_create on this thread.
 thread_local std::string g_serve_create_err;
 
-// Enqueue the whole request on the slot's stream.
-int launch_request(ng_server* s, Slot& sl, Req& q) {
+// Size the slot for its request on the admitting thread while the slot is
+// idle: reconfigure the context if the parameters differ, grow the slot's
+// particle arrays and every buffer and cuFFT plan of the context. The slot's
+// launch thread then only enqueues work: no device allocation, free or plan
+// creation ever runs in a launch thread while other slots' work is in flight.
+int prepare_slot(Slot& sl, const ng_request& r) {
   ng_ctx* c = sl.ctx;
   c->stream = sl.stream;
-  const ng_request& r = q.r;
   const int64_t n = r.n;
-  int rc = NG_OK;
   ng_params want = r.params;
   normalize_params(&want);   // compare like with like: the context holds normalised params
-  if (std::memcmp(&c->p, &want, sizeof(ng_params)) != 0 || c->h_tab.empty()) {
-    rc = ctx_configure(c, &r.params);
-    if (rc != NG_OK) return rc;
-  }
+  if (std::memcmp(&c->p, &want, sizeof(ng_params)) != 0 || c->h_tab.empty())
+    NG_TRY(ctx_configure(c, &r.params));
   NG_TRY(ensure(c, sl.pos, n * 24));
   NG_TRY(ensure(c, sl.vel, n * 12));
   NG_TRY(ensure(c, sl.acc, n * 12));
   NG_TRY(ensure(c, sl.type, n));
   NG_TRY(ensure(c, sl.mass, n * 4));
-  NG_TRY(alloc_bodies(c, n));
-  // every node array, including those sized by the species count, must fit
-  // this request (a slot serves requests of different n and D)
-  NG_TRY(alloc_nodes(c, std::max<int64_t>(c->cap_nodes, n + 1024)));
+  return reserve(c, n);
+}
+
+// Enqueue the whole request on the slot's stream (launch thread; the slot
+// was prepared by prepare_slot).
+int launch_request(ng_server* s, Slot& sl, Req& q) {
+  ng_ctx* c = sl.ctx;
+  c->stream = sl.stream;
+  const uint64_t gen = c->alloc_gen;
+  const ng_request& r = q.r;
+  const int64_t n = r.n;
   double* pos = as<double>(sl.pos);
   float* vel = as<float>(sl.vel);
   float* acc = as<float>(sl.acc);
@@ -157,6 +164,7 @@ int launch_request(ng_server* s, Slot& sl, Req& q) {
   if (r.acc_out) NG_CUDA(c, cudaMemcpyAsync(r.acc_out, acc, n * 12, cudaMemcpyDeviceToHost, sl.stream));
   NG_CUDA(c, cudaMemcpyAsync(sl.h_status, c->status.p, ST_COUNT * 4, cudaMemcpyDeviceToHost, sl.stream));
   NG_CUDA(c, cudaEventRecord(sl.done, sl.stream));
+  if (c->alloc_gen != gen) return fail(c, NG_ESTATE, "a launch thread grew a device buffer");
   (void)s;
   return NG_OK;
 }
@@ -205,10 +213,19 @@ int admit(ng_server* s) {
     s->queue.pop_front();
     sl.bytes = std::max(sl.bytes, need);
     s->peak_held = std::max(s->peak_held, held_bytes(s));
+    q.out->t_admit = now_s();
+    const int rc = prepare_slot(sl, q.r);
+    if (rc != NG_OK) {
+      q.state = 3;
+      q.out->status = rc;
+      q.out->t_done = now_s();
+      if (s->err.empty()) s->err = "request " + std::to_string(id) + ": " + sl.ctx->err;
+      s->completed++;
+      continue;
+    }
     sl.req = id;
     sl.retries = 0;
     q.state = 1;
-    q.out->t_admit = now_s();
     hand_over(sl, &q);
   }
   return NG_OK;

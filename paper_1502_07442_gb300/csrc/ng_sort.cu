@@ -309,7 +309,7 @@ bool box_is_pow2(double L) {
   return std::frexp(L, &e) == 0.5;
 }
 
-int sort_bodies(ng_ctx* c, int64_t n, const double* pos, const uint8_t* type, const float* mass) {
+int reserve_sort(ng_ctx* c, int64_t n) {
   const int nblocks = (int)((n + kRsTile - 1) / kRsTile);
   NG_TRY(ensure(c, c->keys_a, n * 8));
   NG_TRY(ensure(c, c->keys_b, n * 8));
@@ -320,6 +320,13 @@ int sort_bodies(ng_ctx* c, int64_t n, const double* pos, const uint8_t* type, co
   NG_TRY(ensure(c, c->smass, n * 4));
   NG_TRY(ensure(c, c->stype, n));
   NG_TRY(ensure(c, c->tperm, n * 4));
+  NG_TRY(ensure(c, c->scan_part, kScanBlocks * sizeof(uint32_t)));
+  return NG_OK;
+}
+
+int sort_bodies(ng_ctx* c, int64_t n, const double* pos, const uint8_t* type, const float* mass) {
+  const int nblocks = (int)((n + kRsTile - 1) / kRsTile);
+  NG_TRY(reserve_sort(c, n));
   uint64_t *ka = as<uint64_t>(c->keys_a), *kb = as<uint64_t>(c->keys_b);
   uint32_t *va = as<uint32_t>(c->vals_a), *vb = as<uint32_t>(c->vals_b);
   const int grid = work_grid(c, n, 8);

@@ -231,3 +231,58 @@ def test_tree_regrow_beyond_budget_fails_cleanly(ng):
         ng.ng_serve_destroy(s)
     assert res.status == ng.NG_ENOMEM
     assert retries == 0 and peak <= budget
+
+
+def test_served_results_match_the_oracle(ng):
+    # direct mode (theta = 0: FP64 pair sums) plus the PM part, so the served
+    # force is held to the direct-mode and PM bounds against the FP64 oracle:
+    # |dF| <= 2e-5 |F| + 2e-5 rms(F); a 3-step integration's velocity and
+    # position changes within 1e-4 of the oracle's change for 99 % of bodies
+    import oracle
+    from common import oracle_params
+    items = []
+    for k, (n, D, yuk) in enumerate([(3000, 2, False), (2500, 3, True), (2000, 4, False)]):
+        w = small_clustered(n, D, 880 + k, yukawa=yuk, mesh=32)
+        w["params"] = dict(w["params"], theta=0.0)
+        items.append(dict(w=w, kind=k % 2, nsteps=3 if k % 2 else 0))
+    out, res = _run(ng, items, slots=3, budget=8 << 30)
+    assert all(r.status == 0 for r in res)
+    for it, got in zip(items, out):
+        w = it["w"]
+        op = oracle_params(w["params"])
+        if it["kind"] == 0:
+            ref = oracle.force(op, w["pos"], w["type"], w["mass"])
+            dF = np.linalg.norm(got["acc"] - ref, axis=0)
+            F = np.linalg.norm(ref, axis=0)
+            rms = np.sqrt(np.mean(F ** 2))
+            assert (dF <= 2e-5 * F + 2e-5 * rms).all(), (dF / (F + rms)).max()
+        else:
+            n = w["type"].size
+            x, v, a = oracle.kdk(op, w["pos"], np.zeros((3, n)), w["type"], w["mass"], 3, 1e-3)
+            for g, want, start in ((got["vel"], v, np.zeros((3, n))), (got["pos"], x, w["pos"])):
+                d = g - want
+                d -= np.rint(d)
+                moved = want - start
+                moved -= np.rint(moved)
+                rel = np.linalg.norm(d, axis=0) / np.maximum(np.linalg.norm(moved, axis=0), 1e-300)
+                assert np.percentile(rel, 99) <= 1e-4, np.percentile(rel, 99)
+
+
+def test_relative_and_pure_tree_requests(ng):
+    # requests that need the relative criterion's |a_old| buffer or the
+    # exact-law walk: every buffer is sized on the admitting thread, so the
+    # launch threads allocate nothing (a launch thread that did would fail its
+    # request with NG_ESTATE)
+    items = []
+    w = small_clustered(4000, 2, 890, mesh=32)
+    w["params"] = dict(w["params"], opening=1, alpha=0.005)
+    items.append(dict(w=w, kind=1, nsteps=2))
+    w = small_clustered(3000, 2, 891, mesh=32)
+    w["params"] = dict(w["params"], pure_tree=1, pm_mesh=0, rs=0.01, rcut=0.045)
+    items.append(dict(w=w, kind=0, nsteps=0))
+    mixed, res = _run(ng, items, slots=2, budget=8 << 30)
+    assert [r.status for r in res] == [0, 0]
+    for it, got in zip(items, mixed):
+        alone, r1 = _run(ng, [it], slots=1, budget=8 << 30)
+        assert r1[0].status == 0
+        assert _close(got["acc"], alone[0]["acc"])
