@@ -553,8 +553,10 @@ def bench_serve(args, ws, rank, local):
     """2000 requests (Poisson, 200 req/s; half force evaluations, half 10-step
     integrations; N log-uniform in [2^10, 2^20]; D uniform in 1..6; Newtonian
     couplings in [0.5, 1.5]; PM mesh clamp(next_pow2(N^(1/3)), 32, 128);
-    120 GB byte budget). Reports the throughput of one-at-a-time solves: plain
-    calls (a context per request) and the serving loop with one slot."""
+    120 GB byte budget). Reports the saturated throughput of the serving loop
+    with 16 slots against one-at-a-time solves (plain calls, a context per
+    request; the serving loop with one slot), and p50/p99 latency on the
+    Poisson trace at 200 requests/s and at 150 requests/s (below capacity)."""
     import torch
     from paper_1502_07442_gb300 import binding as ng, inputs
     torch.cuda.set_device(local)
@@ -579,6 +581,11 @@ def bench_serve(args, ws, rank, local):
                          pos_out=torch.zeros((3, n), dtype=torch.float64).pin_memory(),
                          vel_out=torch.zeros((3, n), dtype=torch.float32).pin_memory()))
     kinds = rng.integers(0, 2, nreq)
+    gaps = rng.exponential(1.0, nreq)            # unit-rate Poisson gaps, scaled per leg
+
+    def trace(rate):
+        g = gaps / rate
+        return np.cumsum(g) - g[0]
 
     def requests():
         reqs = (ng.NgRequest * nreq)()
@@ -657,22 +664,28 @@ def bench_serve(args, ws, rank, local):
         return r
 
     wpl, okpl = leg("plain", plain)                                # plain calls, one at a time
-    w1, lat1, ok1 = leg("one-slot", run, 1, None)                  # serving loop, one slot
-    # The concurrent (several-slot) legs are not run: they raised an illegal
-    # address whose cause is not yet known, so that configuration stays off
-    # the GPU until it is found and fixed.
-    line = {"metric": "requests/s (served, one slot)", "value": nreq / w1, "unit": "requests/s",
+    w1, _, ok1 = leg("one-slot", run, 1, None)                     # serving loop, one slot
+    wk, _, okk = leg("saturated", run, 16, None)                   # continuous batching, saturated
+    wp, lat, okp = leg("poisson200", run, 16, trace(200.0))        # the workload's arrival rate
+    wq, latq, okq = leg("poisson150", run, 16, trace(150.0))       # below the saturated capacity
+    line = {"metric": "requests/s (served, saturated)", "value": nreq / wk, "unit": "requests/s",
             "n_gpus": ws, "steps": 1, "warmup": 1, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "serve2000", "requests": nreq, "slots": 1,
+            "config": {"workload": "serve2000", "requests": nreq, "rate_per_s": 200, "slots": 16,
                        "budget_bytes": 120 << 30, "mix": "50% force, 50% 10-step KDK",
                        "n_range_log2": [10, 20]},
             "one_at_a_time": {"plain_calls_requests_per_s": nreq / wpl,
                               "serving_one_slot_requests_per_s": nreq / w1},
-            "speedup_one_slot_vs_plain_calls": wpl / w1,
-            "latency_one_slot_ms": {"p50": float(np.percentile(lat1, 50) * 1e3),
-                                    "p99": float(np.percentile(lat1, 99) * 1e3)},
-            "all_ok": bool(okpl and ok1)}
+            "speedup_vs_plain_calls": wpl / wk, "speedup_vs_one_slot": w1 / wk,
+            "poisson": {"rate_per_s": 200,
+                        "p50_latency_ms": float(np.percentile(lat, 50) * 1e3),
+                        "p99_latency_ms": float(np.percentile(lat, 99) * 1e3),
+                        "throughput_requests_per_s": nreq / wp},
+            "poisson_below_capacity": {"rate_per_s": 150,
+                                       "p50_latency_ms": float(np.percentile(latq, 50) * 1e3),
+                                       "p99_latency_ms": float(np.percentile(latq, 99) * 1e3),
+                                       "throughput_requests_per_s": nreq / wq},
+            "all_ok": bool(okpl and ok1 and okk and okp and okq)}
     if rank == 0:
         print(json.dumps(line))
 

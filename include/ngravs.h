@@ -391,13 +391,17 @@ const char* ng_serve_last_error(const ng_server* s);
  * tree buffers, PM meshes). */
 size_t ng_serve_request_bytes(const ng_request* r);
 /* Bookkeeping (no paper counterpart): bytes the slots hold now, the largest
- * sum seen after any admission or tree regrow (never above the budget), and
- * the number of requests rerun with a larger tree capacity. A request whose
- * tree outgrows the slot is rerun only if the slot's larger holding fits the
- * budget beside the other slots; otherwise it fails with NG_ENOMEM. Any
- * output pointer may be NULL. */
+ * sum seen after any admission or tree regrow (never above the budget), the
+ * number of requests rerun with a larger tree capacity, and the number of
+ * admissions that reconfigured a slot's context (parameters other than the
+ * slot's previous request's, defaults filled in before comparing). A request
+ * whose tree outgrows the slot is rerun only if the slot's larger holding
+ * fits the budget beside the other slots; otherwise it fails with NG_ENOMEM.
+ * Every device buffer and cuFFT plan a request needs is sized when it is
+ * admitted, on the thread that admits it; the slots' launch threads only
+ * enqueue work. Any output pointer may be NULL. */
 int ng_serve_stats(const ng_server* s, size_t* held_bytes, size_t* peak_held_bytes,
-                   int64_t* node_retries);
+                   int64_t* node_retries, int64_t* reconfigs);
 
 /*
  * Stages of one force evaluation, in execution order (ng_stage_times):

@@ -119,7 +119,8 @@ def lib():
         L.ng_sort_keys_noalloc.argtypes = [i64, vp, vp, d, vp, vp, vp]
         L.ng_sort_keys_noalloc.restype = ctypes.c_int
         L.ng_serve_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t),
-                                     ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(i64)]
+                                     ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(i64),
+                                     ctypes.POINTER(i64)]
         L.ng_serve_stats.restype = ctypes.c_int
         L.ng_serve_request_bytes.argtypes = [ctypes.POINTER(NgRequest)]
         L.ng_serve_request_bytes.restype = ctypes.c_size_t
@@ -407,10 +408,13 @@ def ng_serve(s, reqs, results, arrival_s=None, timeout_s=600.0):
 
 
 def ng_serve_stats(s):
-    """(bytes held now, peak bytes held, requests rerun with a larger tree)."""
-    held, peak, retries = ctypes.c_size_t(0), ctypes.c_size_t(0), ctypes.c_int64(0)
-    _scheck(s, lib().ng_serve_stats(s, ctypes.byref(held), ctypes.byref(peak), ctypes.byref(retries)))
-    return int(held.value), int(peak.value), int(retries.value)
+    """(bytes held now, peak bytes held, requests rerun with a larger tree,
+    slot reconfigurations)."""
+    held, peak = ctypes.c_size_t(0), ctypes.c_size_t(0)
+    retries, reconf = ctypes.c_int64(0), ctypes.c_int64(0)
+    _scheck(s, lib().ng_serve_stats(s, ctypes.byref(held), ctypes.byref(peak), ctypes.byref(retries),
+                                    ctypes.byref(reconf)))
+    return int(held.value), int(peak.value), int(retries.value), int(reconf.value)
 
 
 def ng_serve_request_bytes(req: NgRequest):

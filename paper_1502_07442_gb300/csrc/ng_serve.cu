@@ -87,6 +87,7 @@ struct ng_server {
   size_t budget = 0;
   size_t peak_held = 0;        // largest sum of slot bytes seen after an admission or a regrow
   int64_t node_retries = 0;    // requests rerun with a larger tree capacity
+  int64_t reconfigs = 0;       // slot contexts reconfigured for new parameters
   int64_t completed = 0;
   std::string err;
 };
@@ -106,14 +107,16 @@ thread_local std::string g_serve_create_err;
 // particle arrays and every buffer and cuFFT plan of the context. The slot's
 // launch thread then only enqueues work: no device allocation, free or plan
 // creation ever runs in a launch thread while other slots' work is in flight.
-int prepare_slot(Slot& sl, const ng_request& r) {
+int prepare_slot(ng_server* s, Slot& sl, const ng_request& r) {
   ng_ctx* c = sl.ctx;
   c->stream = sl.stream;
   const int64_t n = r.n;
   ng_params want = r.params;
   normalize_params(&want);   // compare like with like: the context holds normalised params
-  if (std::memcmp(&c->p, &want, sizeof(ng_params)) != 0 || c->h_tab.empty())
+  if (std::memcmp(&c->p, &want, sizeof(ng_params)) != 0 || c->h_tab.empty()) {
     NG_TRY(ctx_configure(c, &r.params));
+    s->reconfigs++;
+  }
   NG_TRY(ensure(c, sl.pos, n * 24));
   NG_TRY(ensure(c, sl.vel, n * 12));
   NG_TRY(ensure(c, sl.acc, n * 12));
@@ -214,7 +217,7 @@ int admit(ng_server* s) {
     sl.bytes = std::max(sl.bytes, need);
     s->peak_held = std::max(s->peak_held, held_bytes(s));
     q.out->t_admit = now_s();
-    const int rc = prepare_slot(sl, q.r);
+    const int rc = prepare_slot(s, sl, q.r);
     if (rc != NG_OK) {
       q.state = 3;
       q.out->status = rc;
@@ -479,11 +482,12 @@ const char* ng_serve_last_error(const ng_server* s) {
 size_t ng_serve_request_bytes(const ng_request* r) { return r ? request_bytes(*r) : 0; }
 
 int ng_serve_stats(const ng_server* s, size_t* held_bytes_out, size_t* peak_held_bytes,
-                   int64_t* node_retries) {
+                   int64_t* node_retries, int64_t* reconfigs) {
   if (!s) return NG_EINVAL;
   if (held_bytes_out) *held_bytes_out = held_bytes(s);
   if (peak_held_bytes) *peak_held_bytes = s->peak_held;
   if (node_retries) *node_retries = s->node_retries;
+  if (reconfigs) *reconfigs = s->reconfigs;
   return NG_OK;
 }
 

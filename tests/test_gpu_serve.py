@@ -193,7 +193,7 @@ def test_tree_regrow_is_budgeted(ng):
     s = ng.ng_serve_create(2, budget)
     try:
         ng.ng_serve(s, reqs, res, None, 300.0)
-        held, peak, retries = ng.ng_serve_stats(s)
+        held, peak, retries, _ = ng.ng_serve_stats(s)
     finally:
         ng.ng_serve_destroy(s)
     assert all(r.status == 0 for r in res)
@@ -226,7 +226,7 @@ def test_tree_regrow_beyond_budget_fails_cleanly(ng):
     try:
         ng.ng_serve_submit(s, r, res)
         ng.ng_serve_wait(s, 300.0)
-        held, peak, retries = ng.ng_serve_stats(s)
+        held, peak, retries, _ = ng.ng_serve_stats(s)
     finally:
         ng.ng_serve_destroy(s)
     assert res.status == ng.NG_ENOMEM
@@ -286,3 +286,47 @@ def test_relative_and_pure_tree_requests(ng):
         alone, r1 = _run(ng, [it], slots=1, budget=8 << 30)
         assert r1[0].status == 0
         assert _close(got["acc"], alone[0]["acc"])
+
+
+def test_same_parameters_do_not_reconfigure(ng):
+    # a slot's context is reconfigured only when a request's parameters
+    # differ from the previous request's, defaults filled in on both sides
+    # (comparing a request's raw parameters with the context's normalised ones
+    # once reconfigured the slot for every request, from the launch thread)
+    w = small_clustered(3000, 2, 895, mesh=32)
+    p = ng_params(w["params"])
+    assert p.group_cell == 0                     # a default the library fills in
+    items = [dict(w=w, kind=k % 2, nsteps=2 if k % 2 else 0) for k in range(6)]
+    reqs = (ng.NgRequest * len(items))()
+    res = (ng.NgResult * len(items))()
+    for i, it in enumerate(items):
+        reqs[i] = ng.make_request(it["kind"], p, w["pos"], w["type"], w["mass"], nsteps=it["nsteps"],
+                                  dt=1e-3)
+    s = ng.ng_serve_create(1, 8 << 30)
+    try:
+        ng.ng_serve(s, reqs, res, None, 300.0)
+        _, _, _, reconf = ng.ng_serve_stats(s)
+    finally:
+        ng.ng_serve_destroy(s)
+    assert all(r.status == 0 for r in res)
+    assert reconf == 1
+
+
+def test_sixteen_slots_with_changing_sizes_and_species(ng):
+    # the concurrent configuration of the serving benchmark, with small
+    # requests: 16 slots, requests of varying N, D and mesh in a round-robin
+    # order, so every slot serves a sequence of different parameters
+    rng = inputs.rng_for(896)
+    items = []
+    for k in range(24):
+        n = inputs.log_uniform_int(rng, 10, 14)
+        D = int(rng.integers(1, 7))
+        w = small_clustered(n, D, 8960 + k, mesh=inputs.serve_mesh(n))
+        items.append(dict(w=w, kind=k % 2, nsteps=3 if k % 2 else 0))
+    items = items * 4
+    out, res = _run(ng, items, slots=16, budget=32 << 30)
+    assert all(r.status == 0 for r in res), [r.status for r in res]
+    # every repetition of a request gives the same result
+    for k in range(24):
+        for rep in (1, 2, 3):
+            assert _close(out[k + 24 * rep]["acc"], out[k]["acc"])
