@@ -246,8 +246,11 @@ int ng_force(ng_ctx* ctx, float* acc_out);
  * pos (double[3][n]) and vel (float[3][n]) are updated in place; acc
  * (float[3][n]) must hold the acceleration at pos when acc_valid != 0,
  * otherwise it is computed first; on return it holds the acceleration at the
- * final positions. Each step after the first is replayed from a captured
- * CUDA graph. Synchronises the stream at the end to report device errors.
+ * final positions. Between steps the state stays in library buffers in the
+ * previous step's sorted order (the caller's arrays are read once at the
+ * start and written once at the end); each step after the first is replayed
+ * from a captured CUDA graph. Synchronises the stream at the end to report
+ * device errors.
  */
 int ng_step(ng_ctx* ctx, int64_t n, double* pos, float* vel, const uint8_t* type,
             const float* mass, float* acc, int acc_valid, int nsteps, double dt);
@@ -417,17 +420,19 @@ enum {
 };
 
 /*
- * Measurement (no paper counterpart): builds the tree of the n bodies
- * (device arrays as in ng_build_tree) once to size every buffer, then runs
- * one more sort, tree build and force evaluation (ng_force into acc, device
- * float[3][n]) with a CUDA event recorded on the context's stream before each
- * stage and after the last, and writes the milliseconds of each stage to
- * ms_out[NG_NSTAGES] (host; 0 for stages the context's mode does not run,
- * e.g. the PM stages when pm_mesh == 0). Synchronises the stream. Not to be
- * called during stream capture.
+ * Measurement (no paper counterpart): advances the n bodies (device arrays as
+ * in ng_step) by one ng_step step, untimed, which sizes every buffer; then by
+ * one more step exactly as ng_step runs it (resident sorted order), with a
+ * CUDA event recorded on the context's stream before each stage of its sort,
+ * tree build and force evaluation and after the last, and writes each
+ * stage's milliseconds to ms_out[NG_NSTAGES] (host; 0 for stages the
+ * context's mode does not run, e.g. the PM stages when pm_mesh == 0; the
+ * kicks and the drift are not timed). pos, vel and acc hold the state after
+ * the two steps on return. Synchronises the stream. Not to be called during
+ * stream capture.
  */
-int ng_stage_times(ng_ctx* ctx, int64_t n, const double* pos, const uint8_t* type,
-                   const float* mass, float* acc, float* ms_out);
+int ng_stage_times(ng_ctx* ctx, int64_t n, double* pos, float* vel, const uint8_t* type,
+                   const float* mass, float* acc, double dt, float* ms_out);
 
 /*
  * Number of CUDA kernels this context has launched so far (host-side count,

@@ -94,7 +94,7 @@ def lib():
         L.ng_timestep.argtypes = [vp, i64, vp, d, d, ctypes.POINTER(d), ctypes.POINTER(ctypes.c_float)]
         L.ng_pm_force.argtypes = [vp, vp]
         L.ng_force.argtypes = [vp, vp]
-        L.ng_stage_times.argtypes = [vp, i64, vp, vp, vp, vp, vp]
+        L.ng_stage_times.argtypes = [vp, i64, vp, vp, vp, vp, vp, d, vp]
         L.ng_step.argtypes = [vp, i64, vp, vp, vp, vp, vp, i32, i32, d]
         L.ng_tree_export.argtypes = [vp, ctypes.POINTER(i64)] + [vp] * 9
         L.ng_type_order.argtypes = [vp, vp, vp]
@@ -274,11 +274,12 @@ STAGES = ("keys", "radix", "gather", "octree", "monopoles", "groups", "type_orde
           "fft_fwd", "kspace", "fft_inv", "interp", "walk")
 
 
-def ng_stage_times(ctx, pos, typ, mass, acc):
-    """Milliseconds of each stage of one sort + tree + force evaluation (dict)."""
+def ng_stage_times(ctx, pos, vel, typ, mass, acc, dt):
+    """Milliseconds of each stage of one ng_step step (dict); advances the
+    state (pos, vel, acc) by two steps."""
     out = (ctypes.c_float * len(STAGES))()
-    _check(ctx, lib().ng_stage_times(ctx, typ.numel(), _ptr(pos), _ptr(typ), _ptr(mass), _ptr(acc),
-                                     out))
+    _check(ctx, lib().ng_stage_times(ctx, typ.numel(), _ptr(pos), _ptr(vel), _ptr(typ), _ptr(mass),
+                                     _ptr(acc), float(dt), out))
     return {k: float(v) for k, v in zip(STAGES, out)}
 
 

@@ -307,6 +307,14 @@ int build_checked(ng_ctx* c, int64_t n, const double* pos, const uint8_t* type,
   NG_TRY(alloc_bodies(c, n));
   NG_CUDA(c, cudaMemsetAsync(c->status.p, 0, ST_COUNT * 4, c->stream));
   NG_TRY(sort_bodies(c, n, pos, type, mass));
+  return tree_checked(c);
+}
+
+// The tree stages of the sorted bodies, with the node capacity grown until
+// the tree fits (synchronises once per attempt).
+int tree_checked(ng_ctx* c) {
+  const int64_t n = c->n;
+  c->built = false;
   if (c->cap_nodes == 0) {
     const int leaf = std::max(1, c->p.leaf_size);
     NG_TRY(alloc_nodes(c, std::max<int64_t>(4096, 3 * n / leaf + 1024)));
@@ -416,6 +424,13 @@ int validate(ng_ctx* c, const ng_params* p) {
   return NG_OK;
 }
 
+void drop_step_graphs(ng_ctx* c) {
+  if (c->step_exec) cudaGraphExecDestroy(c->step_exec);
+  if (c->step_exec_b) cudaGraphExecDestroy(c->step_exec_b);
+  c->step_exec = nullptr;
+  c->step_exec_b = nullptr;
+}
+
 void normalize_params(ng_params* p) {
   if (p->leaf_size == 0) p->leaf_size = 8;
   if (p->group_size == 0) p->group_size = 32;
@@ -430,10 +445,7 @@ int ctx_configure(ng_ctx* c, const ng_params* p) {
   c->rs = p->pm_mesh > 0 ? p->asmth * p->box / p->pm_mesh : p->asmth * p->box;
   c->rcut = p->pure_tree == 2 ? INFINITY : p->rcut_over_rs * c->rs;
   c->built = false;
-  if (c->step_exec) {
-    cudaGraphExecDestroy(c->step_exec);
-    c->step_exec = nullptr;
-  }
+  drop_step_graphs(c);
   // node arrays sized by the species count follow a change of D
   if (c->cap_nodes > 0) NG_TRY(alloc_nodes(c, c->cap_nodes));
   return build_tables(c);
@@ -495,6 +507,7 @@ int ng_destroy(ng_ctx* c) {
   if (c->stream) cudaStreamSynchronize(c->stream);
   if (c->h_tab_pinned) cudaFreeHost(c->h_tab_pinned);
   if (c->step_exec) cudaGraphExecDestroy(c->step_exec);
+  if (c->step_exec_b) cudaGraphExecDestroy(c->step_exec_b);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   for (int s = 0; s <= NG_NSTAGES; ++s)
     if (c->stage_ev[s]) cudaEventDestroy(c->stage_ev[s]);
@@ -512,7 +525,8 @@ int ng_destroy(ng_ctx* c) {
                     &c->n_cnt, &c->n_geo, &c->n_com, &c->n_link, &c->n_mono, &c->groups, &c->gsize, &c->grank,
                     &c->status, &c->counter, &c->aold, &c->io_pos, &c->io_vel, &c->io_type, &c->io_mass,
                     &c->io_acc, &c->lattice, &c->rho, &c->rhok, &c->phi,
-                    &c->walk_desc, &c->walk_prefix};
+                    &c->walk_desc, &c->walk_prefix, &c->spos_alt, &c->smass_alt, &c->stype_alt,
+                    &c->rvel, &c->rvel_alt, &c->rorig, &c->rorig_alt, &c->racc, &c->rtmp};
   for (DevBuf* b : bufs) release(*b);
   delete c;
   return NG_OK;
@@ -521,10 +535,7 @@ int ng_destroy(ng_ctx* c) {
 int ng_set_stream(ng_ctx* c, void* stream) {
   if (!c) return NG_EINVAL;
   c->stream = (cudaStream_t)stream;
-  if (c->step_exec) {
-    cudaGraphExecDestroy(c->step_exec);
-    c->step_exec = nullptr;
-  }
+  drop_step_graphs(c);
   return NG_OK;
 }
 
@@ -651,26 +662,168 @@ int ng_force(ng_ctx* c, float* acc_out) {
   return force_stages(c, acc_out);
 }
 
-int ng_stage_times(ng_ctx* c, int64_t n, const double* pos, const uint8_t* type,
-                   const float* mass, float* acc, float* ms_out) {
+// ------------------------------------------------ resident state of ng_step
+
+const uint32_t* force_out(const ng_ctx* c) {
+  return c->resident ? nullptr : as<uint32_t>(c->vals_a);
+}
+
+// Caller arrays into the resident state, caller order (the first step's sort
+// permutes them): raw positions, masses, species (checked and clamped as the
+// gather of a plain sort does), velocities, caller indices, accelerations.
+__global__ void k_resident_load(int64_t n, const double* __restrict__ pos,
+                                const float* __restrict__ vel, const uint8_t* __restrict__ type,
+                                const float* __restrict__ mass, const float* __restrict__ acc,
+                                int D, double* __restrict__ rpos, float* __restrict__ rvel,
+                                uint8_t* __restrict__ rtype, float* __restrict__ rmass,
+                                uint32_t* __restrict__ rorig, float* __restrict__ racc,
+                                uint32_t* status) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+      rpos[e * n + i] = pos[e * n + i];
+      rvel[e * n + i] = vel[e * n + i];
+      racc[e * n + i] = acc[e * n + i];
+    }
+    const uint8_t t = type[i];
+    if (t >= D) atomicOr(&status[ST_FLAGS], (uint32_t)SF_BAD_TYPE);
+    rtype[i] = t < D ? t : 0;
+    rmass[i] = mass[i];
+    rorig[i] = (uint32_t)i;
+  }
+}
+
+// The resident state back to the caller's order: positions, velocities and
+// accelerations scattered to their caller indices.
+__global__ void k_resident_store(int64_t n, const uint32_t* __restrict__ rorig,
+                                 const double* __restrict__ rpos, const float* __restrict__ rvel,
+                                 const float* __restrict__ racc, double* __restrict__ pos,
+                                 float* __restrict__ vel, float* __restrict__ acc) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t i = rorig[k];
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+      pos[e * n + i] = rpos[e * n + k];
+      vel[e * n + i] = rvel[e * n + k];
+      acc[e * n + i] = racc[e * n + k];
+    }
+  }
+}
+
+// out[idx[k]] = in[k] (a float per body).
+__global__ void k_scatter_f32(int64_t n, const uint32_t* __restrict__ idx,
+                              const float* __restrict__ in, float* __restrict__ out) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x)
+    out[idx[k]] = in[k];
+}
+
+static int reserve_resident(ng_ctx* c, int64_t n) {
+  NG_TRY(reserve(c, n));
+  NG_TRY(ensure(c, c->spos_alt, (size_t)n * 24));
+  NG_TRY(ensure(c, c->smass_alt, (size_t)n * 4));
+  NG_TRY(ensure(c, c->stype_alt, (size_t)n));
+  NG_TRY(ensure(c, c->rvel, (size_t)n * 12));
+  NG_TRY(ensure(c, c->rvel_alt, (size_t)n * 12));
+  NG_TRY(ensure(c, c->rorig, (size_t)n * 4));
+  NG_TRY(ensure(c, c->rorig_alt, (size_t)n * 4));
+  NG_TRY(ensure(c, c->racc, (size_t)n * 12));
+  NG_TRY(ensure(c, c->rtmp, (size_t)n * 4));
+  return NG_OK;
+}
+
+// Exchange the roles of the two resident sets: the current state moves to
+// the *_alt buffers, which the next step reads; the others receive the next
+// state.
+static void swap_resident(ng_ctx* c) {
+  std::swap(c->spos, c->spos_alt);
+  std::swap(c->smass, c->smass_alt);
+  std::swap(c->stype, c->stype_alt);
+  std::swap(c->rvel, c->rvel_alt);
+  std::swap(c->rorig, c->rorig_alt);
+  c->step_parity ^= 1;
+}
+
+static int resident_load(ng_ctx* c, int64_t n, const double* pos, const float* vel,
+                         const uint8_t* type, const float* mass, const float* acc) {
+  k_resident_load<<<work_grid(c, n, 8), 256, 0, c->stream>>>(
+      n, pos, vel, type, mass, acc, c->p.D, as<double>(c->spos), as<float>(c->rvel),
+      as<uint8_t>(c->stype), as<float>(c->smass), as<uint32_t>(c->rorig), as<float>(c->racc),
+      as<uint32_t>(c->status));
+  c->launches += 1;
+  NG_CUDA(c, cudaGetLastError());
+  c->resident = true;
+  return NG_OK;
+}
+
+// Back to caller order; the context's permutation then maps the sorted
+// bodies of the last step to caller indices, as after ng_build_tree, and the
+// relative criterion's |a_old| returns to caller order.
+static int resident_store(ng_ctx* c, int64_t n, double* pos, float* vel, float* acc) {
+  k_resident_store<<<work_grid(c, n, 8), 256, 0, c->stream>>>(
+      n, as<uint32_t>(c->rorig), as<double>(c->spos), as<float>(c->rvel), as<float>(c->racc), pos,
+      vel, acc);
+  c->launches += 1;
+  NG_CUDA(c, cudaGetLastError());
+  NG_CUDA(c, cudaMemcpyAsync(c->vals_a.p, c->rorig.p, (size_t)n * 4, cudaMemcpyDeviceToDevice,
+                             c->stream));
+  if (c->aold_n == n) {
+    k_scatter_f32<<<work_grid(c, n, 8), 256, 0, c->stream>>>(n, as<uint32_t>(c->rorig),
+                                                             as<float>(c->aold), as<float>(c->rtmp));
+    c->launches += 1;
+    NG_CUDA(c, cudaGetLastError());
+    NG_CUDA(c, cudaMemcpyAsync(c->aold.p, c->rtmp.p, (size_t)n * 4, cudaMemcpyDeviceToDevice,
+                               c->stream));
+  }
+  c->resident = false;
+  return NG_OK;
+}
+
+// One kick-drift-kick step on the resident state (no host synchronisation;
+// captured as a graph). The sort's gather takes the state into this step's
+// sorted order; the forces are written in that order.
+static int resident_step_once(ng_ctx* c, int64_t n, double dt, bool checked) {
+  swap_resident(c);
+  NG_TRY(launch_kick(c, n, as<float>(c->rvel_alt), as<float>(c->racc), 0.5 * dt));
+  NG_TRY(launch_drift(c, n, as<double>(c->spos_alt), as<float>(c->rvel_alt), dt));
+  NG_TRY(sort_resident(c, n));
+  if (checked) NG_TRY(tree_checked(c));
+  else NG_TRY(tree_stages(c));
+  NG_TRY(force_stages(c, as<float>(c->racc)));
+  NG_TRY(launch_kick(c, n, as<float>(c->rvel), as<float>(c->racc), 0.5 * dt));
+  return NG_OK;
+}
+
+int ng_stage_times(ng_ctx* c, int64_t n, double* pos, float* vel, const uint8_t* type,
+                   const float* mass, float* acc, double dt, float* ms_out) {
   if (!c) return NG_EINVAL;
   if (n < 1 || n >= (int64_t)1 << 31) return fail(c, NG_EINVAL, "n outside [1, 2^31)");
-  if (!pos || !type || !mass || !acc || !ms_out) return fail(c, NG_EINVAL, "NULL array");
+  if (!pos || !vel || !type || !mass || !acc || !ms_out) return fail(c, NG_EINVAL, "NULL array");
+  if (!std::isfinite(dt)) return fail(c, NG_EINVAL, "bad dt");
   for (int s = 0; s < NG_NSTAGES; ++s) ms_out[s] = 0.f;
-  // untimed: size every buffer for these bodies
-  NG_TRY(build_checked(c, n, pos, type, mass));
-  NG_TRY(force_stages(c, acc));
-  NG_CUDA(c, cudaStreamSynchronize(c->stream));
+  // untimed: one step sizes every buffer and leaves acc valid at pos
+  NG_TRY(ng_step(c, n, pos, vel, type, mass, acc, 0, 1, dt));
   for (int s = 0; s <= NG_NSTAGES; ++s)
     if (!c->stage_ev[s]) NG_CUDA(c, cudaEventCreate(&c->stage_ev[s]));
+  NG_TRY(resident_load(c, n, pos, vel, type, mass, acc));
+  swap_resident(c);
+  NG_TRY(launch_kick(c, n, as<float>(c->rvel_alt), as<float>(c->racc), 0.5 * dt));
+  NG_TRY(launch_drift(c, n, as<double>(c->spos_alt), as<float>(c->rvel_alt), dt));
   c->stage_seen = 0;
   c->timing = true;
-  int r = sort_bodies(c, n, pos, type, mass);
+  int r = sort_resident(c, n);
   if (r == NG_OK) r = tree_stages(c);
-  if (r == NG_OK) r = force_stages(c, acc);
+  if (r == NG_OK) r = force_stages(c, as<float>(c->racc));
   c->timing = false;
-  NG_TRY(r);
+  if (r != NG_OK) {
+    c->resident = false;
+    return r;
+  }
   NG_CUDA(c, cudaEventRecord(c->stage_ev[NG_NSTAGES], c->stream));
+  NG_TRY(launch_kick(c, n, as<float>(c->rvel), as<float>(c->racc), 0.5 * dt));
+  NG_TRY(resident_store(c, n, pos, vel, acc));
   NG_CUDA(c, cudaStreamSynchronize(c->stream));
   uint32_t st[ST_COUNT];
   NG_TRY(read_status(c, st));
@@ -689,21 +842,6 @@ int ng_stage_times(ng_ctx* c, int64_t n, const double* pos, const uint8_t* type,
   return NG_OK;
 }
 
-static int step_once(ng_ctx* c, int64_t n, double* pos, float* vel, const uint8_t* type,
-                     const float* mass, float* acc, double dt) {
-  const int grid = work_grid(c, 3 * n, 8);
-  c->launches += 3;   // kick, drift, kick
-  k_kick<<<grid, 256, 0, c->stream>>>(3 * n, vel, acc, (float)(0.5 * dt));
-  k_drift<<<grid, 256, 0, c->stream>>>(3 * n, pos, vel, dt, c->L, 1.0 / c->L, box_is_pow2(c->L));
-  NG_CUDA(c, cudaGetLastError());
-  NG_TRY(sort_bodies(c, n, pos, type, mass));
-  NG_TRY(tree_stages(c));
-  NG_TRY(force_stages(c, acc));
-  k_kick<<<grid, 256, 0, c->stream>>>(3 * n, vel, acc, (float)(0.5 * dt));
-  NG_CUDA(c, cudaGetLastError());
-  return NG_OK;
-}
-
 int ng_step(ng_ctx* c, int64_t n, double* pos, float* vel, const uint8_t* type,
             const float* mass, float* acc, int acc_valid, int nsteps, double dt) {
   if (!c) return NG_EINVAL;
@@ -718,71 +856,92 @@ int ng_step(ng_ctx* c, int64_t n, double* pos, float* vel, const uint8_t* type,
     NG_CUDA(c, cudaStreamSynchronize(c->stream));
     return NG_OK;
   }
-  const void* ptrs[5] = {pos, vel, type, mass, acc};
-  bool reuse = c->step_exec && c->graph_n == n && c->graph_dt == dt &&
-               c->graph_gen == c->alloc_gen && std::equal(ptrs, ptrs + 5, c->graph_ptrs);
+  // the state stays on the device in the previous step's sorted order
+  c->n = n;
+  NG_TRY(reserve_resident(c, n));
+  NG_CUDA(c, cudaMemsetAsync(c->status.p, 0, sizeof(uint32_t), c->stream));
+  NG_TRY(resident_load(c, n, pos, vel, type, mass, acc));
+  int r = NG_OK;
   int done = 0;
+  const bool reuse = c->step_exec && c->step_exec_b && c->graph_n == n && c->graph_dt == dt &&
+                     c->graph_gen == c->alloc_gen;
   if (!reuse) {
-    // one eager step sizes every buffer, then the step is captured
-    const int grid = work_grid(c, 3 * n, 8);
-    k_kick<<<grid, 256, 0, c->stream>>>(3 * n, vel, acc, (float)(0.5 * dt));
-    k_drift<<<grid, 256, 0, c->stream>>>(3 * n, pos, vel, dt, c->L, 1.0 / c->L, box_is_pow2(c->L));
-    c->launches += 3;
-    NG_CUDA(c, cudaGetLastError());
-    NG_TRY(build_checked(c, n, pos, type, mass));
-    NG_TRY(force_stages(c, acc));
-    k_kick<<<grid, 256, 0, c->stream>>>(3 * n, vel, acc, (float)(0.5 * dt));
-    NG_CUDA(c, cudaGetLastError());
+    // one eager step sizes the tree with synchronised checks, then the step
+    // is captured twice, once per assignment of the two resident sets
+    r = resident_step_once(c, n, dt, true);
     done = 1;
-    if (c->cap_nodes < c->nnodes + c->nnodes / 4 + 1024) {
+    if (r == NG_OK && c->cap_nodes < c->nnodes + c->nnodes / 4 + 1024) {
       // headroom for the replayed steps, whose trees cannot regrow; the
-      // regrow drops the node arrays, so the tree of the current positions
-      // is built again for tree queries made after this call
-      NG_CUDA(c, cudaStreamSynchronize(c->stream));
-      NG_TRY(alloc_nodes(c, c->nnodes + c->nnodes / 4 + 1024));
-      NG_TRY(build_checked(c, n, pos, type, mass));
+      // regrow drops the node arrays, so the tree of the current (sorted)
+      // bodies is built again
+      r = alloc_nodes(c, c->nnodes + c->nnodes / 4 + 1024);
+      if (r == NG_OK) r = tree_checked(c);
     }
-    NG_CUDA(c, cudaStreamSynchronize(c->stream));
-    if (c->step_exec) {
+    if (r == NG_OK && c->step_exec) {
       cudaGraphExecDestroy(c->step_exec);
       c->step_exec = nullptr;
     }
-    if (done < nsteps) {
+    if (r == NG_OK && c->step_exec_b) {
+      cudaGraphExecDestroy(c->step_exec_b);
+      c->step_exec_b = nullptr;
+    }
+    if (r == NG_OK && done < nsteps) {
       // capture needs a stream other than the legacy default one
-      if (!c->cap_stream)
-        NG_CUDA(c, cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
-      cudaStream_t user = c->stream;
-      cudaGraph_t g = nullptr;
-      NG_CUDA(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeRelaxed));
-      c->stream = c->cap_stream;
-      const uint64_t before = c->launches;
-      const int r = step_once(c, n, pos, vel, type, mass, acc, dt);
-      c->graph_launches = c->launches - before;
-      c->launches = before;
-      c->stream = user;
-      const cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
-      cudaGetLastError();
-      if (r != NG_OK) {
-        if (g) cudaGraphDestroy(g);
-        return r;
+      if (!c->cap_stream && cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        r = fail(c, NG_ECUDA, "capture stream creation failed");
       }
-      if (e != cudaSuccess) return fail(c, NG_ECUDA, "step capture failed: %s", cudaGetErrorString(e));
-      const cudaError_t ei = cudaGraphInstantiate(&c->step_exec, g, 0);
-      cudaGraphDestroy(g);
-      if (ei != cudaSuccess)
-        return fail(c, NG_ECUDA, "graph instantiate failed: %s", cudaGetErrorString(ei));
-      c->graph_n = n;
-      c->graph_dt = dt;
-      c->graph_gen = c->alloc_gen;
-      std::copy(ptrs, ptrs + 5, c->graph_ptrs);
+      cudaStream_t user = c->stream;
+      // graph k starts from step parity k (the two captures leave the
+      // assignment where it was: the captured steps do not run)
+      for (int k = 0; k < 2 && r == NG_OK; ++k) {
+        cudaGraphExec_t* slot = c->step_parity == 0 ? &c->step_exec : &c->step_exec_b;
+        cudaGraph_t g = nullptr;
+        if (cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+          cudaGetLastError();
+          r = fail(c, NG_ECUDA, "begin capture failed");
+          break;
+        }
+        c->stream = c->cap_stream;
+        const uint64_t before = c->launches;
+        r = resident_step_once(c, n, dt, false);
+        c->graph_launches = c->launches - before;
+        c->launches = before;
+        c->stream = user;
+        const cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
+        cudaGetLastError();
+        if (r != NG_OK) {
+          if (g) cudaGraphDestroy(g);
+          break;
+        }
+        if (e != cudaSuccess) {
+          r = fail(c, NG_ECUDA, "step capture failed: %s", cudaGetErrorString(e));
+          break;
+        }
+        const cudaError_t ei = cudaGraphInstantiate(slot, g, 0);
+        cudaGraphDestroy(g);
+        if (ei != cudaSuccess) r = fail(c, NG_ECUDA, "graph instantiate failed: %s", cudaGetErrorString(ei));
+      }
+      if (r == NG_OK) {
+        c->graph_n = n;
+        c->graph_dt = dt;
+        c->graph_gen = c->alloc_gen;
+      }
     }
   }
-  if (done < nsteps)
-    NG_CUDA(c, cudaMemsetAsync(c->status.p, 0, sizeof(uint32_t), c->stream));  // sticky flags
-  for (int s = done; s < nsteps; ++s) {
-    NG_CUDA(c, cudaGraphLaunch(c->step_exec, c->stream));
+  for (int s = done; s < nsteps && r == NG_OK; ++s) {
+    cudaGraphExec_t g = c->step_parity == 0 ? c->step_exec : c->step_exec_b;
+    if (cudaGraphLaunch(g, c->stream) != cudaSuccess) {
+      cudaGetLastError();
+      r = fail(c, NG_ECUDA, "graph launch failed");
+      break;
+    }
+    swap_resident(c);   // the replayed step's exchange, on the host
     c->launches += c->graph_launches;
   }
+  const int rs = resident_store(c, n, pos, vel, acc);
+  if (r == NG_OK) r = rs;
+  NG_TRY(r);
   uint32_t st[ST_COUNT];
   NG_TRY(read_status(c, st));
   NG_TRY(check_flags(c, st[ST_FLAGS]));

@@ -31,14 +31,14 @@ struct DirectArgs {
   const double* spos;      // [3][n] sorted, physical
   const float* smass;      // [n] sorted
   const uint8_t* stype;    // [n] sorted
-  const uint32_t* perm;    // sorted -> caller
+  const uint32_t* out;     // sorted -> output index (nullptr: sorted order)
   int64_t n;
   double L, invL;
   double rcut2_box;        // cut-off^2 in box units (node skipping)
   double rcut2, eps2, rs;  // physical units
   double G[kMaxD][kMaxD], ya[kMaxD][kMaxD], yl[kMaxD][kMaxD];
   int law[kMaxD][kMaxD];
-  float* acc;              // [3][n] caller order
+  float* acc;              // [3][n] output order
   int accumulate;
   unsigned long long* counter;   // terms of opened leaves (optional)
   uint32_t* status;
@@ -108,7 +108,7 @@ __global__ void __launch_bounds__(128) k_direct64(DirectArgs a) {
         for (int ch = (int)nch - 1; ch >= 0; --ch) stack[sp++] = a.child[nd] + ch;
       }
     }
-    const uint32_t i = a.perm[k];
+    const uint32_t i = a.out ? a.out[k] : (uint32_t)k;
     if (a.accumulate) {
       a.acc[i] = (float)((double)a.acc[i] + ax);
       a.acc[a.n + i] = (float)((double)a.acc[a.n + i] + ay);
@@ -143,7 +143,7 @@ int launch_direct64(ng_ctx* c, float* acc, bool accumulate, bool count) {
   a.spos = as<double>(c->spos);
   a.smass = as<float>(c->smass);
   a.stype = as<uint8_t>(c->stype);
-  a.perm = as<uint32_t>(c->vals_a);
+  a.out = force_out(c);
   a.n = c->n;
   a.L = c->L;
   a.invL = 1.0 / c->L;

@@ -41,7 +41,8 @@ struct ExactArgs {
   const double* spos;      // [3][n] sorted, physical
   const float* smass;      // [n] sorted
   const uint8_t* stype;    // [n] sorted
-  const uint32_t* perm;    // sorted -> caller
+  const uint32_t* perm;    // sorted -> caller (previous accelerations)
+  const uint32_t* out;     // sorted -> output index (nullptr: sorted order)
   int64_t n;
   int D;
   double invL, L;
@@ -61,7 +62,7 @@ struct ExactArgs {
   float lat_scale;         // 2 N / L
   float lat_inv_l2;        // 1 / L^2
   int8_t tabid[kMaxD][kMaxD];
-  float* acc;              // [3][n] caller order
+  float* acc;              // [3][n] output order
   int accumulate;
   unsigned long long* counter;   // executed terms (optional)
   uint32_t* status;
@@ -236,7 +237,7 @@ __global__ void __launch_bounds__(128) k_walk_exact(ExactArgs a) {
         for (int ch = (int)nch - 1; ch >= 0; --ch) stack[sp++] = a.child[nd] + ch;
       }
     }
-    const uint32_t i = a.perm[k];
+    const uint32_t i = a.out ? a.out[k] : (uint32_t)k;
     if (a.accumulate) {
       a.acc[i] += ax;
       a.acc[a.n + i] += ay;
@@ -270,6 +271,7 @@ int launch_walk_exact(ng_ctx* c, float* acc, bool accumulate, bool count) {
   a.smass = as<float>(c->smass);
   a.stype = as<uint8_t>(c->stype);
   a.perm = as<uint32_t>(c->vals_a);
+  a.out = force_out(c);
   a.n = c->n;
   a.D = c->p.D;
   a.L = c->L;

@@ -160,9 +160,10 @@ struct __align__(16) WalkDesc {
   const uint8_t* btype;     // [sorted body] species
   const uint32_t* bleaf;    // [sorted body] leaf node holding the body
   const int2* groups;       // [group] first body, count
-  const uint32_t* perm;     // sorted -> caller index
+  const uint32_t* perm;     // sorted -> caller index (previous accelerations are read there)
+  const uint32_t* out;      // sorted -> output index of acc (nullptr: sorted order)
   uint32_t* status;         // device status words of the simulation
-  float* acc;               // [3][n] caller order
+  float* acc;               // [3][n] output order
   int64_t n;
   int accumulate;           // add into acc instead of overwriting
   float s_tab;              // table units per box unit
@@ -235,6 +236,16 @@ struct ng_ctx {
   ng::DevBuf aold;       // float[n] |previous acceleration| per body (caller order)
   int64_t aold_n = -1;   // bodies aold holds (-1: none)
 
+  // resident state of ng_step: between steps the bodies stay in the sorted
+  // order of the previous step. (spos, smass, stype) with rvel, rorig (the
+  // caller index of each body) and racc hold the current state; each step
+  // swaps them with their *_alt partners, gathers the previous state into
+  // sorted order and writes the forces in that order.
+  bool resident = false;
+  ng::DevBuf spos_alt, smass_alt, stype_alt, rvel, rvel_alt, rorig, rorig_alt, racc, rtmp;
+  cudaGraphExec_t step_exec_b = nullptr;   // the step with the buffer roles exchanged
+  int step_parity = 0;
+
   // PM: cuFFT plans cached per (mesh, species count); a context reused for
   // requests of other sizes keeps its plans
   struct Plan { int N, D; cufftHandle r2c, c2r; };
@@ -257,7 +268,6 @@ struct ng_ctx {
   uint64_t graph_gen = 0;
   cudaGraphExec_t step_exec = nullptr;
   int64_t graph_n = -1;
-  const void* graph_ptrs[5]{};
   double graph_dt = 0;
 };
 
@@ -305,6 +315,12 @@ int scan_u32(ng_ctx* c, const uint32_t* in, uint32_t* out, int64_t len,
 // Stages of the pipeline (each enqueues on c->stream, no host sync).
 int sort_bodies(ng_ctx* c, int64_t n, const double* pos, const uint8_t* type,
                 const float* mass);
+// Resident step's sort: keys of the state in *_alt, gather of positions,
+// masses, species, velocities and caller indices into sorted order.
+int sort_resident(ng_ctx* c, int64_t n);
+// Output index of the force kernels: the caller order, or the sorted order
+// while ng_step keeps the state resident.
+const uint32_t* force_out(const ng_ctx* c);
 int build_octree(ng_ctx* c);                  // needs sorted bodies
 int reduce_monopoles(ng_ctx* c);              // needs octree
 int build_groups(ng_ctx* c);                  // needs octree
@@ -377,6 +393,7 @@ int64_t level_bound(int l, int64_t n);
 // Pipeline pieces shared by the single-simulation calls and the batch
 // runtime (ng_api.cu).
 int build_checked(ng_ctx* c, int64_t n, const double* pos, const uint8_t* type, const float* mass);
+int tree_checked(ng_ctx* c);                   // tree stages of the sorted bodies, capacity grown
 int tree_stages(ng_ctx* c);
 int force_stages(ng_ctx* c, float* acc);
 int launch_kick(ng_ctx* c, int64_t n, float* vel, const float* acc, double h);
@@ -391,6 +408,7 @@ int ctx_configure(ng_ctx* c, const ng_params* p);
 int validate(ng_ctx* c, const ng_params* p);
 // Fill the defaults of a parameter block (leaf size, group size, group cell).
 void normalize_params(ng_params* p);
+void drop_step_graphs(ng_ctx* c);   // the captured steps of ng_step
 int check_flags(ng_ctx* c, uint32_t flags);
 bool box_is_pow2(double L);   // L = 2^k: x / L == x * (1 / L) exactly
 

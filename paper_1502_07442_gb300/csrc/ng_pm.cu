@@ -107,7 +107,8 @@ __global__ void k_kspace(cufftComplex* __restrict__ mesh, int N, float kf, float
 }
 
 // -grad phi_i by 4-point central differences at the 8 CIC corners of each
-// particle of passive species i, interpolated with the CIC weights.
+// particle of passive species i, interpolated with the CIC weights; written
+// at perm[k] (caller order) or, with perm == nullptr, at k (sorted order).
 __global__ void k_pm_interp(int64_t n, const double* __restrict__ spos,
                             const uint8_t* __restrict__ stype, const uint32_t* __restrict__ perm,
                             const float* __restrict__ phi, int N, double cells_per_len,
@@ -141,7 +142,7 @@ __global__ void k_pm_interp(int64_t n, const double* __restrict__ spos,
       a[1] = fmaf(w, gy, a[1]);
       a[2] = fmaf(w, gz, a[2]);
     }
-    const uint32_t i = perm[k];
+    const uint32_t i = perm ? perm[k] : (uint32_t)k;
     const float s = -inv_h;
     if (accumulate) {
       acc[i] += s * a[0];
@@ -242,7 +243,7 @@ int pm_force(ng_ctx* c, float* acc, bool accumulate) {
     return fail(c, NG_ECUDA, "cufftExecC2R failed");
   stage_mark(c, NG_STAGE_INTERP);
   k_pm_interp<<<grid, 256, 0, c->stream>>>(c->n, as<double>(c->spos), as<uint8_t>(c->stype),
-                                          as<uint32_t>(c->vals_a), as<float>(c->phi), N,
+                                          force_out(c), as<float>(c->phi), N,
                                           (double)N / L, (float)(N / L), acc, accumulate ? 1 : 0);
   NG_CUDA(c, cudaGetLastError());
   return NG_OK;

@@ -287,6 +287,32 @@ __global__ void k_gather(int64_t n, const uint32_t* __restrict__ perm,
   }
 }
 
+// The resident step's gather: the previous state (positions already wrapped
+// by the drift, masses, species, velocities and caller indices, in the
+// previous step's sorted order) into this step's sorted order. The bodies
+// move little from step to step, so perm is close to the identity and every
+// read is close to sequential.
+__global__ void k_gather_resident(int64_t n, const uint32_t* __restrict__ perm,
+                                  const double* __restrict__ xpos, const float* __restrict__ xmass,
+                                  const uint8_t* __restrict__ xtype, const float* __restrict__ xvel,
+                                  const uint32_t* __restrict__ xorig, double* __restrict__ ypos,
+                                  float* __restrict__ ymass, uint8_t* __restrict__ ytype,
+                                  float* __restrict__ yvel, uint32_t* __restrict__ yorig) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t i = perm[k];
+    ypos[k] = xpos[i];
+    ypos[n + k] = xpos[n + i];
+    ypos[2 * n + k] = xpos[2 * n + i];
+    yvel[k] = xvel[i];
+    yvel[n + k] = xvel[n + i];
+    yvel[2 * n + k] = xvel[2 * n + i];
+    ymass[k] = xmass[i];
+    ytype[k] = xtype[i];
+    yorig[k] = xorig[i];
+  }
+}
+
 __global__ void k_iota(int64_t n, uint32_t* out) {
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
        k += (int64_t)gridDim.x * blockDim.x)
@@ -324,9 +350,9 @@ int reserve_sort(ng_ctx* c, int64_t n) {
   return NG_OK;
 }
 
-int sort_bodies(ng_ctx* c, int64_t n, const double* pos, const uint8_t* type, const float* mass) {
-  const int nblocks = (int)((n + kRsTile - 1) / kRsTile);
-  NG_TRY(reserve_sort(c, n));
+// Keys of the bodies at pos and their stable sort: sorted keys in keys_a,
+// the permutation (sorted index -> input index) in vals_a.
+static int sort_keys(ng_ctx* c, int64_t n, const double* pos, const uint8_t* type) {
   uint64_t *ka = as<uint64_t>(c->keys_a), *kb = as<uint64_t>(c->keys_b);
   uint32_t *va = as<uint32_t>(c->vals_a), *vb = as<uint32_t>(c->vals_b);
   const int grid = work_grid(c, n, 8);
@@ -334,7 +360,7 @@ int sort_bodies(ng_ctx* c, int64_t n, const double* pos, const uint8_t* type, co
   stage_mark(c, NG_STAGE_KEYS);
   k_keys<<<grid, 256, 0, c->stream>>>(n, pos, type, c->L, 1.0 / c->L, pow2,
                                       pow2 ? std::ilogb(c->L) : 0, ka, va);
-  c->launches += 2;   // keys + gather
+  c->launches += 1;
   NG_CUDA(c, cudaGetLastError());
   // 8 passes of 8 bits: the result returns to (ka, va)
   stage_mark(c, NG_STAGE_RADIX);
@@ -343,6 +369,29 @@ int sort_bodies(ng_ctx* c, int64_t n, const double* pos, const uint8_t* type, co
     NG_TRY(radix_pass(c, even ? ka : kb, even ? va : vb, even ? kb : ka, even ? vb : va, n,
                       8 * pass, 0xffu));
   }
+  return NG_OK;
+}
+
+int sort_resident(ng_ctx* c, int64_t n) {
+  NG_TRY(sort_keys(c, n, as<double>(c->spos_alt), as<uint8_t>(c->stype_alt)));
+  stage_mark(c, NG_STAGE_GATHER);
+  k_gather_resident<<<work_grid(c, n, 8), 256, 0, c->stream>>>(
+      n, as<uint32_t>(c->vals_a), as<double>(c->spos_alt), as<float>(c->smass_alt),
+      as<uint8_t>(c->stype_alt), as<float>(c->rvel_alt), as<uint32_t>(c->rorig_alt),
+      as<double>(c->spos), as<float>(c->smass), as<uint8_t>(c->stype), as<float>(c->rvel),
+      as<uint32_t>(c->rorig));
+  c->launches += 1;
+  NG_CUDA(c, cudaGetLastError());
+  return NG_OK;
+}
+
+int sort_bodies(ng_ctx* c, int64_t n, const double* pos, const uint8_t* type, const float* mass) {
+  NG_TRY(reserve_sort(c, n));
+  uint32_t* va = as<uint32_t>(c->vals_a);
+  const int grid = work_grid(c, n, 8);
+  const bool pow2 = box_is_pow2(c->L);
+  NG_TRY(sort_keys(c, n, pos, type));
+  c->launches += 1;   // gather
   stage_mark(c, NG_STAGE_GATHER);
   k_gather<<<grid, 256, 0, c->stream>>>(n, va, pos, type, mass, c->L, 1.0 / c->L, pow2, c->p.D,
                                         as<double>(c->spos), as<float>(c->smass),

@@ -450,7 +450,7 @@ __global__ void __launch_bounds__(walk_warps(D) * 32, 1) k_walk(WalkLaunch L) {
     if (active) {
       const Acc sc = (Acc)DESC(out_scale);
       const float fx = (float)(ax * sc), fy = (float)(ay * sc), fz = (float)(az * sc);
-      const uint32_t i = DESC(perm)[p];
+      const uint32_t i = DESC(out) ? DESC(out)[p] : (uint32_t)p;
       float* acc = DESC(acc);
       const int64_t nb = DESC(n);
       if (DESC(accumulate)) {
@@ -549,6 +549,7 @@ void fill_walk_desc(ng_ctx* c, float* acc, bool accumulate, WalkDesc* d) {
   d->bleaf = as<uint32_t>(c->bleaf);
   d->groups = as<int2>(c->groups);
   d->perm = as<uint32_t>(c->vals_a);
+  d->out = force_out(c);
   d->status = as<uint32_t>(c->status);
   d->acc = acc;
   d->n = c->n;
