@@ -451,6 +451,140 @@ int ctx_configure(ng_ctx* c, const ng_params* p) {
   return build_tables(c);
 }
 
+// ------------------------------------------------ resident state of ng_step
+
+const uint32_t* force_out(const ng_ctx* c) {
+  return c->resident ? nullptr : as<uint32_t>(c->vals_a);
+}
+
+// Caller arrays into the resident state, caller order (the first step's sort
+// permutes them): raw positions, masses, species (checked and clamped as the
+// gather of a plain sort does), velocities, caller indices, accelerations.
+__global__ void k_resident_load(int64_t n, const double* __restrict__ pos,
+                                const float* __restrict__ vel, const uint8_t* __restrict__ type,
+                                const float* __restrict__ mass, const float* __restrict__ acc,
+                                int D, double* __restrict__ rpos, float* __restrict__ rvel,
+                                uint8_t* __restrict__ rtype, float* __restrict__ rmass,
+                                uint32_t* __restrict__ rorig, float* __restrict__ racc,
+                                uint32_t* status) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+      rpos[e * n + i] = pos[e * n + i];
+      rvel[e * n + i] = vel[e * n + i];
+      racc[e * n + i] = acc[e * n + i];
+    }
+    const uint8_t t = type[i];
+    if (t >= D) atomicOr(&status[ST_FLAGS], (uint32_t)SF_BAD_TYPE);
+    rtype[i] = t < D ? t : 0;
+    rmass[i] = mass[i];
+    rorig[i] = (uint32_t)i;
+  }
+}
+
+// The resident state back to the caller's order: positions, velocities and
+// accelerations scattered to their caller indices.
+__global__ void k_resident_store(int64_t n, const uint32_t* __restrict__ rorig,
+                                 const double* __restrict__ rpos, const float* __restrict__ rvel,
+                                 const float* __restrict__ racc, double* __restrict__ pos,
+                                 float* __restrict__ vel, float* __restrict__ acc) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t i = rorig[k];
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+      pos[e * n + i] = rpos[e * n + k];
+      vel[e * n + i] = rvel[e * n + k];
+      acc[e * n + i] = racc[e * n + k];
+    }
+  }
+}
+
+// out[idx[k]] = in[k] (a float per body).
+__global__ void k_scatter_f32(int64_t n, const uint32_t* __restrict__ idx,
+                              const float* __restrict__ in, float* __restrict__ out) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x)
+    out[idx[k]] = in[k];
+}
+
+int reserve_resident(ng_ctx* c, int64_t n) {
+  NG_TRY(reserve(c, n));
+  NG_TRY(ensure(c, c->spos_alt, (size_t)n * 24));
+  NG_TRY(ensure(c, c->smass_alt, (size_t)n * 4));
+  NG_TRY(ensure(c, c->stype_alt, (size_t)n));
+  NG_TRY(ensure(c, c->rvel, (size_t)n * 12));
+  NG_TRY(ensure(c, c->rvel_alt, (size_t)n * 12));
+  NG_TRY(ensure(c, c->rorig, (size_t)n * 4));
+  NG_TRY(ensure(c, c->rorig_alt, (size_t)n * 4));
+  NG_TRY(ensure(c, c->racc, (size_t)n * 12));
+  NG_TRY(ensure(c, c->rtmp, (size_t)n * 4));
+  return NG_OK;
+}
+
+// Exchange the roles of the two resident sets: the current state moves to
+// the *_alt buffers, which the next step reads; the others receive the next
+// state.
+void swap_resident(ng_ctx* c) {
+  std::swap(c->spos, c->spos_alt);
+  std::swap(c->smass, c->smass_alt);
+  std::swap(c->stype, c->stype_alt);
+  std::swap(c->rvel, c->rvel_alt);
+  std::swap(c->rorig, c->rorig_alt);
+  c->step_parity ^= 1;
+}
+
+int resident_load(ng_ctx* c, int64_t n, const double* pos, const float* vel,
+                         const uint8_t* type, const float* mass, const float* acc) {
+  k_resident_load<<<work_grid(c, n, 8), 256, 0, c->stream>>>(
+      n, pos, vel, type, mass, acc, c->p.D, as<double>(c->spos), as<float>(c->rvel),
+      as<uint8_t>(c->stype), as<float>(c->smass), as<uint32_t>(c->rorig), as<float>(c->racc),
+      as<uint32_t>(c->status));
+  c->launches += 1;
+  NG_CUDA(c, cudaGetLastError());
+  c->resident = true;
+  return NG_OK;
+}
+
+// Back to caller order; the context's permutation then maps the sorted
+// bodies of the last step to caller indices, as after ng_build_tree, and the
+// relative criterion's |a_old| returns to caller order.
+int resident_store(ng_ctx* c, int64_t n, double* pos, float* vel, float* acc) {
+  k_resident_store<<<work_grid(c, n, 8), 256, 0, c->stream>>>(
+      n, as<uint32_t>(c->rorig), as<double>(c->spos), as<float>(c->rvel), as<float>(c->racc), pos,
+      vel, acc);
+  c->launches += 1;
+  NG_CUDA(c, cudaGetLastError());
+  NG_CUDA(c, cudaMemcpyAsync(c->vals_a.p, c->rorig.p, (size_t)n * 4, cudaMemcpyDeviceToDevice,
+                             c->stream));
+  if (c->aold_n == n) {
+    k_scatter_f32<<<work_grid(c, n, 8), 256, 0, c->stream>>>(n, as<uint32_t>(c->rorig),
+                                                             as<float>(c->aold), as<float>(c->rtmp));
+    c->launches += 1;
+    NG_CUDA(c, cudaGetLastError());
+    NG_CUDA(c, cudaMemcpyAsync(c->aold.p, c->rtmp.p, (size_t)n * 4, cudaMemcpyDeviceToDevice,
+                               c->stream));
+  }
+  c->resident = false;
+  return NG_OK;
+}
+
+// One kick-drift-kick step on the resident state (no host synchronisation;
+// captured as a graph). The sort's gather takes the state into this step's
+// sorted order; the forces are written in that order.
+int resident_step_once(ng_ctx* c, int64_t n, double dt, bool checked) {
+  swap_resident(c);
+  NG_TRY(launch_kick(c, n, as<float>(c->rvel_alt), as<float>(c->racc), 0.5 * dt));
+  NG_TRY(launch_drift(c, n, as<double>(c->spos_alt), as<float>(c->rvel_alt), dt));
+  NG_TRY(sort_resident(c, n));
+  if (checked) NG_TRY(tree_checked(c));
+  else NG_TRY(tree_stages(c));
+  NG_TRY(force_stages(c, as<float>(c->racc)));
+  NG_TRY(launch_kick(c, n, as<float>(c->rvel), as<float>(c->racc), 0.5 * dt));
+  return NG_OK;
+}
+
 }  // namespace ng
 
 using namespace ng;
@@ -660,140 +794,6 @@ int ng_force(ng_ctx* c, float* acc_out) {
   if (!c->built) return fail(c, NG_ESTATE, "ng_force before ng_build_tree");
   if (!acc_out) return fail(c, NG_EINVAL, "acc_out is NULL");
   return force_stages(c, acc_out);
-}
-
-// ------------------------------------------------ resident state of ng_step
-
-const uint32_t* force_out(const ng_ctx* c) {
-  return c->resident ? nullptr : as<uint32_t>(c->vals_a);
-}
-
-// Caller arrays into the resident state, caller order (the first step's sort
-// permutes them): raw positions, masses, species (checked and clamped as the
-// gather of a plain sort does), velocities, caller indices, accelerations.
-__global__ void k_resident_load(int64_t n, const double* __restrict__ pos,
-                                const float* __restrict__ vel, const uint8_t* __restrict__ type,
-                                const float* __restrict__ mass, const float* __restrict__ acc,
-                                int D, double* __restrict__ rpos, float* __restrict__ rvel,
-                                uint8_t* __restrict__ rtype, float* __restrict__ rmass,
-                                uint32_t* __restrict__ rorig, float* __restrict__ racc,
-                                uint32_t* status) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-#pragma unroll
-    for (int e = 0; e < 3; ++e) {
-      rpos[e * n + i] = pos[e * n + i];
-      rvel[e * n + i] = vel[e * n + i];
-      racc[e * n + i] = acc[e * n + i];
-    }
-    const uint8_t t = type[i];
-    if (t >= D) atomicOr(&status[ST_FLAGS], (uint32_t)SF_BAD_TYPE);
-    rtype[i] = t < D ? t : 0;
-    rmass[i] = mass[i];
-    rorig[i] = (uint32_t)i;
-  }
-}
-
-// The resident state back to the caller's order: positions, velocities and
-// accelerations scattered to their caller indices.
-__global__ void k_resident_store(int64_t n, const uint32_t* __restrict__ rorig,
-                                 const double* __restrict__ rpos, const float* __restrict__ rvel,
-                                 const float* __restrict__ racc, double* __restrict__ pos,
-                                 float* __restrict__ vel, float* __restrict__ acc) {
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
-       k += (int64_t)gridDim.x * blockDim.x) {
-    const uint32_t i = rorig[k];
-#pragma unroll
-    for (int e = 0; e < 3; ++e) {
-      pos[e * n + i] = rpos[e * n + k];
-      vel[e * n + i] = rvel[e * n + k];
-      acc[e * n + i] = racc[e * n + k];
-    }
-  }
-}
-
-// out[idx[k]] = in[k] (a float per body).
-__global__ void k_scatter_f32(int64_t n, const uint32_t* __restrict__ idx,
-                              const float* __restrict__ in, float* __restrict__ out) {
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
-       k += (int64_t)gridDim.x * blockDim.x)
-    out[idx[k]] = in[k];
-}
-
-static int reserve_resident(ng_ctx* c, int64_t n) {
-  NG_TRY(reserve(c, n));
-  NG_TRY(ensure(c, c->spos_alt, (size_t)n * 24));
-  NG_TRY(ensure(c, c->smass_alt, (size_t)n * 4));
-  NG_TRY(ensure(c, c->stype_alt, (size_t)n));
-  NG_TRY(ensure(c, c->rvel, (size_t)n * 12));
-  NG_TRY(ensure(c, c->rvel_alt, (size_t)n * 12));
-  NG_TRY(ensure(c, c->rorig, (size_t)n * 4));
-  NG_TRY(ensure(c, c->rorig_alt, (size_t)n * 4));
-  NG_TRY(ensure(c, c->racc, (size_t)n * 12));
-  NG_TRY(ensure(c, c->rtmp, (size_t)n * 4));
-  return NG_OK;
-}
-
-// Exchange the roles of the two resident sets: the current state moves to
-// the *_alt buffers, which the next step reads; the others receive the next
-// state.
-static void swap_resident(ng_ctx* c) {
-  std::swap(c->spos, c->spos_alt);
-  std::swap(c->smass, c->smass_alt);
-  std::swap(c->stype, c->stype_alt);
-  std::swap(c->rvel, c->rvel_alt);
-  std::swap(c->rorig, c->rorig_alt);
-  c->step_parity ^= 1;
-}
-
-static int resident_load(ng_ctx* c, int64_t n, const double* pos, const float* vel,
-                         const uint8_t* type, const float* mass, const float* acc) {
-  k_resident_load<<<work_grid(c, n, 8), 256, 0, c->stream>>>(
-      n, pos, vel, type, mass, acc, c->p.D, as<double>(c->spos), as<float>(c->rvel),
-      as<uint8_t>(c->stype), as<float>(c->smass), as<uint32_t>(c->rorig), as<float>(c->racc),
-      as<uint32_t>(c->status));
-  c->launches += 1;
-  NG_CUDA(c, cudaGetLastError());
-  c->resident = true;
-  return NG_OK;
-}
-
-// Back to caller order; the context's permutation then maps the sorted
-// bodies of the last step to caller indices, as after ng_build_tree, and the
-// relative criterion's |a_old| returns to caller order.
-static int resident_store(ng_ctx* c, int64_t n, double* pos, float* vel, float* acc) {
-  k_resident_store<<<work_grid(c, n, 8), 256, 0, c->stream>>>(
-      n, as<uint32_t>(c->rorig), as<double>(c->spos), as<float>(c->rvel), as<float>(c->racc), pos,
-      vel, acc);
-  c->launches += 1;
-  NG_CUDA(c, cudaGetLastError());
-  NG_CUDA(c, cudaMemcpyAsync(c->vals_a.p, c->rorig.p, (size_t)n * 4, cudaMemcpyDeviceToDevice,
-                             c->stream));
-  if (c->aold_n == n) {
-    k_scatter_f32<<<work_grid(c, n, 8), 256, 0, c->stream>>>(n, as<uint32_t>(c->rorig),
-                                                             as<float>(c->aold), as<float>(c->rtmp));
-    c->launches += 1;
-    NG_CUDA(c, cudaGetLastError());
-    NG_CUDA(c, cudaMemcpyAsync(c->aold.p, c->rtmp.p, (size_t)n * 4, cudaMemcpyDeviceToDevice,
-                               c->stream));
-  }
-  c->resident = false;
-  return NG_OK;
-}
-
-// One kick-drift-kick step on the resident state (no host synchronisation;
-// captured as a graph). The sort's gather takes the state into this step's
-// sorted order; the forces are written in that order.
-static int resident_step_once(ng_ctx* c, int64_t n, double dt, bool checked) {
-  swap_resident(c);
-  NG_TRY(launch_kick(c, n, as<float>(c->rvel_alt), as<float>(c->racc), 0.5 * dt));
-  NG_TRY(launch_drift(c, n, as<double>(c->spos_alt), as<float>(c->rvel_alt), dt));
-  NG_TRY(sort_resident(c, n));
-  if (checked) NG_TRY(tree_checked(c));
-  else NG_TRY(tree_stages(c));
-  NG_TRY(force_stages(c, as<float>(c->racc)));
-  NG_TRY(launch_kick(c, n, as<float>(c->rvel), as<float>(c->racc), 0.5 * dt));
-  return NG_OK;
 }
 
 int ng_stage_times(ng_ctx* c, int64_t n, double* pos, float* vel, const uint8_t* type,

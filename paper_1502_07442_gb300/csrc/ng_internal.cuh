@@ -321,6 +321,13 @@ int sort_resident(ng_ctx* c, int64_t n);
 // Output index of the force kernels: the caller order, or the sorted order
 // while ng_step keeps the state resident.
 const uint32_t* force_out(const ng_ctx* c);
+// Resident state of ng_step (ng_api.cu).
+int reserve_resident(ng_ctx* c, int64_t n);
+void swap_resident(ng_ctx* c);
+int resident_load(ng_ctx* c, int64_t n, const double* pos, const float* vel, const uint8_t* type,
+                  const float* mass, const float* acc);
+int resident_store(ng_ctx* c, int64_t n, double* pos, float* vel, float* acc);
+int resident_step_once(ng_ctx* c, int64_t n, double dt, bool checked);
 int build_octree(ng_ctx* c);                  // needs sorted bodies
 int reduce_monopoles(ng_ctx* c);              // needs octree
 int build_groups(ng_ctx* c);                  // needs octree
