@@ -421,14 +421,15 @@ enum {
 
 /*
  * Measurement (no paper counterpart): advances the n bodies (device arrays as
- * in ng_step) by one ng_step step, untimed, which sizes every buffer; then by
- * one more step exactly as ng_step runs it (resident sorted order), with a
+ * in ng_step) by two ng_step steps, untimed, which size every buffer and
+ * bring the state into sorted order; then by one more step exactly as a
+ * replayed ng_step step runs (resident sorted order), with a
  * CUDA event recorded on the context's stream before each stage of its sort,
  * tree build and force evaluation and after the last, and writes each
  * stage's milliseconds to ms_out[NG_NSTAGES] (host; 0 for stages the
  * context's mode does not run, e.g. the PM stages when pm_mesh == 0; the
  * kicks and the drift are not timed). pos, vel and acc hold the state after
- * the two steps on return. Synchronises the stream. Not to be called during
+ * the three steps on return. Synchronises the stream. Not to be called during
  * stream capture.
  */
 int ng_stage_times(ng_ctx* ctx, int64_t n, double* pos, float* vel, const uint8_t* type,

@@ -276,7 +276,7 @@ STAGES = ("keys", "radix", "gather", "octree", "monopoles", "groups", "type_orde
 
 def ng_stage_times(ctx, pos, vel, typ, mass, acc, dt):
     """Milliseconds of each stage of one ng_step step (dict); advances the
-    state (pos, vel, acc) by two steps."""
+    state (pos, vel, acc) by three steps."""
     out = (ctypes.c_float * len(STAGES))()
     _check(ctx, lib().ng_stage_times(ctx, typ.numel(), _ptr(pos), _ptr(vel), _ptr(typ), _ptr(mass),
                                      _ptr(acc), float(dt), out))

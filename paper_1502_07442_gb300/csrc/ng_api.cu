@@ -808,6 +808,9 @@ int ng_stage_times(ng_ctx* c, int64_t n, double* pos, float* vel, const uint8_t*
   for (int s = 0; s <= NG_NSTAGES; ++s)
     if (!c->stage_ev[s]) NG_CUDA(c, cudaEventCreate(&c->stage_ev[s]));
   NG_TRY(resident_load(c, n, pos, vel, type, mass, acc));
+  // one untimed resident step: the timed one then starts, as every replayed
+  // step does, from the previous step's sorted order
+  NG_TRY(resident_step_once(c, n, dt, false));
   swap_resident(c);
   NG_TRY(launch_kick(c, n, as<float>(c->rvel_alt), as<float>(c->racc), 0.5 * dt));
   NG_TRY(launch_drift(c, n, as<double>(c->spos_alt), as<float>(c->rvel_alt), dt));
