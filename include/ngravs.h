@@ -319,8 +319,10 @@ int ng_batch_step(ng_batch* b, const int64_t* n, double* const* pos, float* cons
                   const uint8_t* const* type, const float* const* mass, float* const* acc,
                   int acc_valid, int nsteps, double dt);
 
-/* Number of simulations; number of walk launches per step (one per class of
- * simulations sharing D and the law table). */
+/* Number of simulations; number of walk launches per step: one per class of
+ * simulations whose laws fit one law table laid out for 6 species (any
+ * species counts; simulations whose laws agree on their species pairs, cut-off
+ * and table spacing share a class). */
 int ng_batch_size(const ng_batch* b);
 int ng_batch_walk_launches(const ng_batch* b);
 /* Kernels launched by all member contexts so far (see ng_launch_count). */

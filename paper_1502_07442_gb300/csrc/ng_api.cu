@@ -64,10 +64,56 @@ void release(DevBuf& b) {
 // entry (k, s) lies in the bank pair (k * pad + s) mod 16, so lanes of
 // different species never meet in a bank, and lanes of one species only when
 // their segments differ by a multiple of 16 / pad.
+std::vector<float> walk_table(const ng_ctx* c, int Dl, int ncut, double dr) {
+  const ng_params& p = c->p;
+  const int D = p.D;
+  const int pad = walk_tab_pad(Dl);
+  // segments of every distinct law (c->tabid), then the walk layout
+  std::vector<double> seg((size_t)c->nlaws * (ncut + 1) * 2, 0.0);
+  for (int u = 0; u < c->nlaws && !p.pure_tree; ++u) {
+    int si = 0, ti = 0;
+    for (int i = 0; i < D; ++i)
+      for (int j = 0; j < D; ++j)
+        if (c->tabid[i][j] == u) si = i, ti = j;
+    const int kind = p.law[si][ti];
+    const bool yk = kind == NG_YUKAWA || kind == NG_YUKAWA_PURE;
+    const double ya = yk ? p.yuk_a[si][ti] : 0.0, yl = yk ? p.yuk_l[si][ti] : 0.0;
+    double* t = seg.data() + (size_t)u * (ncut + 1) * 2;
+    auto T = [&](double rho) { return short_law_factor(kind, ya, yl, c->rs, rho); };
+    {
+      const double lo = T(0.0), hi = T(0.5 * dr);
+      t[0] = lo + 0.5 * (T(0.25 * dr) - 0.5 * (lo + hi));   // value at t = 0
+      t[1] = 2.0 * (hi - lo);
+    }
+    for (int k = 1; k < ncut; ++k) {
+      const double lo = T((k - 0.5) * dr), hi = T((k + 0.5) * dr);
+      const double c0 = 0.25 * (lo + hi) + 0.5 * T(k * dr);
+      // stored shifted: the walk evaluates (c0 - k c1) + (rho / dr) c1
+      t[2 * k] = c0 - k * (hi - lo);
+      t[2 * k + 1] = hi - lo;
+    }
+  }
+  std::vector<float> h((size_t)Dl * (ncut + 1) * pad * 2, 0.f);
+  for (int tt = 0; tt < D; ++tt)
+    for (int k = 0; k <= ncut; ++k)
+      for (int ss = 0; ss < D; ++ss) {
+        const double* g = seg.data() + ((size_t)c->tabid[ss][tt] * (ncut + 1) + k) * 2;
+        float* o = h.data() + (((size_t)tt * (ncut + 1) + k) * pad + ss) * 2;
+        o[0] = (float)g[0];
+        o[1] = (float)g[1];
+      }
+  return h;
+}
+
+int walk_table_entries(int Dl, int table_size) {
+  if (table_size > 0) return table_size;
+  const size_t budget = 64 * 1024;
+  return (int)std::min<size_t>(4096, budget / (sizeof(float) * 2 * Dl * walk_tab_pad(Dl)) - 1);
+}
+
 int build_tables(ng_ctx* c) {
   const ng_params& p = c->p;
   const int D = p.D;
-  const int pad = walk_tab_pad(D);
   struct Law { int kind; double a, l; };
   std::vector<Law> laws;
   for (int i = 0; i < D; ++i)
@@ -84,11 +130,7 @@ int build_tables(ng_ctx* c) {
       c->tabid[i][j] = (int8_t)id;
     }
   c->nlaws = (int)laws.size();
-  int ncut = p.table_size;
-  if (ncut <= 0) {
-    const size_t budget = 64 * 1024;
-    ncut = (int)std::min<size_t>(4096, budget / (sizeof(float) * 2 * D * pad) - 1);
-  }
+  const int ncut = walk_table_entries(D, p.table_size);
   if (ncut < 16) return fail(c, NG_EINVAL, "table_size %d too small", ncut);
   c->ncut = ncut;
   // pure tree mode evaluates the laws directly: the table is kept (zero) only
@@ -98,34 +140,7 @@ int build_tables(ng_ctx* c) {
   if (std::sqrt(3.0) * c->L / c->dr_phys > 4.0e6)
     return fail(c, NG_EINVAL, "box too large relative to the table spacing (box/dr = %.3g)",
                 c->L / c->dr_phys);
-  // segments of every distinct law, then the walk layout
-  std::vector<double> seg((size_t)c->nlaws * (ncut + 1) * 2, 0.0);
-  for (int u = 0; u < c->nlaws && !p.pure_tree; ++u) {
-    double* t = seg.data() + (size_t)u * (ncut + 1) * 2;
-    auto T = [&](double rho) { return short_law_factor(laws[u].kind, laws[u].a, laws[u].l, c->rs, rho); };
-    const double dr = c->dr_phys;
-    {
-      const double lo = T(0.0), hi = T(0.5 * dr);
-      t[0] = lo + 0.5 * (T(0.25 * dr) - 0.5 * (lo + hi));   // value at t = 0
-      t[1] = 2.0 * (hi - lo);
-    }
-    for (int k = 1; k < ncut; ++k) {
-      const double lo = T((k - 0.5) * dr), hi = T((k + 0.5) * dr);
-      const double c0 = 0.25 * (lo + hi) + 0.5 * T(k * dr);
-      // stored shifted: the walk evaluates (c0 - k c1) + (rho / dr) c1
-      t[2 * k] = c0 - k * (hi - lo);
-      t[2 * k + 1] = hi - lo;
-    }
-  }
-  std::vector<float> h((size_t)D * (ncut + 1) * pad * 2, 0.f);
-  for (int tt = 0; tt < D; ++tt)
-    for (int k = 0; k <= ncut; ++k)
-      for (int ss = 0; ss < D; ++ss) {
-        const double* g = seg.data() + ((size_t)c->tabid[ss][tt] * (ncut + 1) + k) * 2;
-        float* o = h.data() + (((size_t)tt * (ncut + 1) + k) * pad + ss) * 2;
-        o[0] = (float)g[0];
-        o[1] = (float)g[1];
-      }
+  std::vector<float> h = walk_table(c, D, ncut, c->dr_phys);
   c->h_tab = h;
   NG_TRY(ensure(c, c->d_tab, h.size() * sizeof(float)));
   // upload through the context's pinned staging copy: wait until the stream

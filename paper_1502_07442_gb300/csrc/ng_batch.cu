@@ -5,9 +5,10 @@
 // Each simulation's sort, tree and PM stages run on one of several worker
 // streams (fork/join inside one captured CUDA graph, so small simulations
 // overlap on the device); the short-range walk of all simulations that share
-// the species count and the law table is ONE persistent launch whose warps
-// pull (simulation, group) items from a single work queue; the closing kick
-// runs per simulation. The step is captured once and replayed.
+// one law table (laid out for 6 species; simulations of any species count
+// whose laws agree on their species pairs share it) is ONE persistent launch
+// whose warps pull (simulation, group) items from a single work queue; the
+// closing kick runs per simulation. The step is captured once and replayed.
 #include <algorithm>
 #include <cstdarg>
 #include <cstdio>
@@ -19,10 +20,15 @@
 using namespace ng;
 
 struct WalkClass {
-  int D = 0;
+  int D = 0;                         // the largest species count of the members
   std::vector<int> members;          // simulation indices
   std::vector<WalkDesc> h;           // host descriptors (kept alive for the graph)
   DevBuf d, pre;                     // device descriptors, group prefix + work counter
+  // the class's law table, laid out for kMaxD lists (variable-D launches)
+  std::vector<float> htab;
+  int ncut = 0;
+  double dr = 0;
+  DevBuf tab;
 };
 
 struct ng_batch {
@@ -59,10 +65,23 @@ int from_sim(ng_batch* b, int i, int code) {
   return bfail(b, code, "simulation %d: %s", i, ng_last_error(b->sims[i]));
 }
 
-bool same_table(const ng_ctx* a, const ng_ctx* c) {
-  return a->p.D == c->p.D && a->p.accumulate_fp64 == c->p.accumulate_fp64 &&
-         a->nlaws == c->nlaws && a->ncut == c->ncut &&
-         a->dr_phys == c->dr_phys && a->h_tab == c->h_tab;
+// A simulation can join a walk class when the class's table (laid out for
+// kMaxD lists) holds its laws on its own D x D block and the table spacing,
+// cut-off and accumulation agree; the first member, of the largest species
+// count, defines the table.
+bool fits_class(const WalkClass& k, const ng_ctx* rep, const ng_ctx* c,
+                const std::vector<float>& h, int ncut, double dr) {
+  if (c->p.accumulate_fp64 != rep->p.accumulate_fp64 || c->rcut != rep->rcut ||
+      ncut != k.ncut || dr != k.dr || h.size() != k.htab.size())
+    return false;
+  const int D = c->p.D, pad = walk_tab_pad(kMaxD);
+  for (int t = 0; t < D; ++t)
+    for (int r = 0; r <= ncut; ++r)
+      for (int sp = 0; sp < D; ++sp) {
+        const size_t o = (((size_t)t * (ncut + 1) + r) * pad + sp) * 2;
+        if (h[o] != k.htab[o] || h[o + 1] != k.htab[o + 1]) return false;
+      }
+  return true;
 }
 
 uint64_t alloc_gen(const ng_batch* b) {
@@ -111,11 +130,21 @@ int ng_batch_create(ng_batch** out, int nsim, const ng_params* params, void* str
     ng_batch_destroy(b);
     return NG_ECUDA;
   }
-  // walk classes: same species count and identical law table
-  for (int i = 0; i < nsim; ++i) {
+  // walk classes: simulations whose laws fit one table laid out for kMaxD
+  // lists (largest species counts first, so each class's first member
+  // defines its table); one persistent walk launch per class
+  std::vector<int> order(nsim);
+  for (int i = 0; i < nsim; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int x, int y) { return b->sims[x]->p.D > b->sims[y]->p.D; });
+  for (int i : order) {
+    ng_ctx* c = b->sims[i];
+    const int ncut = walk_table_entries(kMaxD, c->p.table_size);
+    const double dr = c->rcut / (ncut - 0.5);
+    std::vector<float> h = walk_table(c, kMaxD, ncut, dr);
     bool placed = false;
     for (WalkClass& k : b->classes) {
-      if (same_table(b->sims[k.members[0]], b->sims[i])) {
+      if (fits_class(k, b->sims[k.members[0]], c, h, ncut, dr)) {
         k.members.push_back(i);
         placed = true;
         break;
@@ -123,8 +152,27 @@ int ng_batch_create(ng_batch** out, int nsim, const ng_params* params, void* str
     }
     if (!placed) {
       b->classes.emplace_back();
-      b->classes.back().D = b->sims[i]->p.D;
-      b->classes.back().members.push_back(i);
+      WalkClass& k = b->classes.back();
+      k.D = c->p.D;
+      k.members.push_back(i);
+      k.htab = std::move(h);
+      k.ncut = ncut;
+      k.dr = dr;
+    }
+  }
+  for (WalkClass& k : b->classes) {
+    std::sort(k.members.begin(), k.members.end());
+    ng_ctx* rep = b->sims[k.members[0]];
+    int r = ensure(rep, k.tab, k.htab.size() * sizeof(float));
+    if (r == NG_OK &&
+        cudaMemcpy(k.tab.p, k.htab.data(), k.htab.size() * sizeof(float), cudaMemcpyHostToDevice) !=
+            cudaSuccess) {
+      cudaGetLastError();
+      r = NG_ECUDA;
+    }
+    if (r != NG_OK) {
+      ng_batch_destroy(b);
+      return r;
     }
   }
   *out = b;
@@ -137,6 +185,7 @@ int ng_batch_destroy(ng_batch* b) {
   for (WalkClass& k : b->classes) {
     release(k.d);
     release(k.pre);
+    release(k.tab);
   }
   for (cudaStream_t s : b->workers) cudaStreamDestroy(s);
   for (cudaEvent_t e : b->joins) cudaEventDestroy(e);
@@ -212,9 +261,10 @@ int batch_step_once(ng_batch* b, const int64_t* n, double* const* pos, float* co
     for (int m : k.members) groups += walk_groups_hint(b->sims[m]);
     bool rel = false;   // some member uses the relative criterion
     for (const WalkDesc& h : k.h) rel = rel || h.aold != nullptr;
+    WalkTable tab{as<float2>(k.tab), k.ncut, (int)(k.htab.size() / 2)};
     if (r == NG_OK)
       r = launch_walk_descs(rep, origin, as<WalkDesc>(k.d), nd, pre, pre + nd + 1, nullptr, groups,
-                            rel);
+                            rel, &tab, true);
     rep->stream = keep;
     if (r != NG_OK) return from_sim(b, k.members[0], r);
   }
@@ -294,7 +344,7 @@ int ng_batch_step(ng_batch* b, const int64_t* n, double* const* pos, float* cons
       k.h.resize(k.members.size());
       for (size_t j = 0; j < k.members.size(); ++j) {
         ng_ctx* c = b->sims[k.members[j]];
-        fill_walk_desc(c, acc[k.members[j]], c->p.pm_mesh > 0, &k.h[j]);
+        fill_walk_desc_dr(c, acc[k.members[j]], c->p.pm_mesh > 0, k.dr, &k.h[j]);
       }
       ng_ctx* rep = b->sims[k.members[0]];
       int r = ensure(rep, k.d, k.h.size() * sizeof(WalkDesc));

@@ -151,6 +151,13 @@ __host__ __device__ constexpr int walk_tab_shift(int D) { return D <= 1 ? 0 : D 
 __host__ __device__ constexpr int walk_warps(int D) { return D <= 3 ? 24 : D == 4 ? 24 : D == 5 ? 20 : 16; }
 
 // Per-simulation inputs of the walk (device memory, one per simulation).
+// The law table of a walk launch (device copy).
+struct WalkTable {
+  const float2* tab;        // [list species t][ncut + 1][walk_tab_pad(D)]
+  int ncut;
+  int count;                // float2 entries
+};
+
 struct __align__(16) WalkDesc {
   const float4* geo;        // [node] centre (box units), half side
   const float4* com;        // [node] all-species centre of mass - centre, total mass
@@ -175,6 +182,7 @@ struct __align__(16) WalkDesc {
   float G[kMaxD][kMaxD];
   const float* aold;        // relative criterion: |a_old| per caller index (nullptr: geometric)
   float rel_scale;          // alpha L^2 / G_max (box units)
+  int D;                    // species of the simulation (launches over several species counts)
 };
 
 // Kernel parameters of one walk launch over one or more simulations that
@@ -334,9 +342,14 @@ int build_groups(ng_ctx* c);                  // needs octree
 int launch_walk(ng_ctx* c, float* acc, bool accumulate, bool count);
 void fill_walk_desc(ng_ctx* c, float* acc, bool accumulate, WalkDesc* d);
 int64_t walk_groups_hint(const ng_ctx* c);
+// One walk launch over ndesc simulations sharing the law table `tab` (the
+// context's own when nullptr); vard: their species counts differ (the
+// variable-D instance with lists and table for 6 species).
 int launch_walk_descs(ng_ctx* c, cudaStream_t stream, const WalkDesc* d_descs, int ndesc,
                       uint32_t* d_prefix, uint32_t* d_work, unsigned long long* counter,
-                      int64_t groups, bool rel);
+                      int64_t groups, bool rel, const WalkTable* tab = nullptr, bool vard = false);
+// Walk descriptor with the table spacing of another table (batch classes).
+void fill_walk_desc_dr(ng_ctx* c, float* acc, bool accumulate, double dr, WalkDesc* d);
 int launch_count(ng_ctx* c, int64_t* counts);  // per-particle walk counts
 // Direct mode (theta = 0, geometric opening, TreePM split): every pair within
 // r_cut summed in FP64 (ng_direct.cu).
@@ -364,6 +377,10 @@ int type_order(ng_ctx* c);
 
 // Host short-range law tables (double precision closed forms).
 int build_tables(ng_ctx* c);
+// The walk's law table of a context laid out for Dl >= D lists (rows of
+// walk_tab_pad(Dl) entries; pairs outside D x D zero), ncut segments of dr.
+std::vector<float> walk_table(const ng_ctx* c, int Dl, int ncut, double dr);
+int walk_table_entries(int Dl, int table_size);   // default segment count for Dl lists
 
 // Short-range force factor T(rho) of Sec. 2.4.1 in FP64: the acceleration from
 // a source of active mass M is G M T(rho) d / rho^3. Newtonian part:

@@ -84,7 +84,10 @@ __device__ __forceinline__ float2 lds_f2(uint32_t addr) {
 // added into an FP64 per-body accumulator); otherwise FP32 throughout.
 // REL: some simulation of the launch may use the relative criterion (an
 // instance without it carries none of that code).
-template <int D, bool ACC64, bool REL>
+// VARD: the simulations of the launch may have different species counts; D
+// is then the largest (lists for D species, the law table laid out for D),
+// and each work item uses its simulation's own count DESC(D) <= D.
+template <int D, bool ACC64, bool REL, bool VARD>
 __global__ void __launch_bounds__(walk_warps(D) * 32, 1) k_walk(WalkLaunch L) {
   using Acc = typename std::conditional<ACC64, double, float>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -121,6 +124,7 @@ __global__ void __launch_bounds__(walk_warps(D) * 32, 1) k_walk(WalkLaunch L) {
     }
     __syncwarp();
     const uint32_t nnodes = DESC(status)[ST_LEVELS + kMaxLevel + 1];
+    const int DR = VARD ? DESC(D) : D;   // species of this item's simulation
     const float rc2 = DESC(rcut_box) * DESC(rcut_box);
     const float rc2_keep = rc2 * 1.0001f;   // margin for FP32 rounding of the offsets
     const float s_tab = DESC(s_tab);
@@ -308,6 +312,7 @@ __global__ void __launch_bounds__(walk_warps(D) * 32, 1) k_walk(WalkLaunch L) {
         int slot = 0;
 #pragma unroll
         for (int t = 0; t < D; ++t) {
+          if (VARD && t >= DR) break;
           const uint32_t m = __ballot_sync(0xffffffffu, bt == t);
           if (bt == t) slot = lc[t] + __popc(m & lt);
           lc[t] += __popc(m);
@@ -348,9 +353,9 @@ __global__ void __launch_bounds__(walk_warps(D) * 32, 1) k_walk(WalkLaunch L) {
         lk = DESC(link)[node];
         // the species monopoles are read only if the node is accepted;
         // start moving them into L1 now
-        const char* mp = reinterpret_cast<const char*>(DESC(mono) + (size_t)node * D);
+        const char* mp = reinterpret_cast<const char*>(DESC(mono) + (size_t)node * DR);
         asm volatile("prefetch.global.L1 [%0];" ::"l"(mp));
-        asm volatile("prefetch.global.L1 [%0];" ::"l"(mp + D * 16 - 1));
+        asm volatile("prefetch.global.L1 [%0];" ::"l"(mp + DR * 16 - 1));
         dcx = wrap_unit(ge.x - ox);
         dcy = wrap_unit(ge.y - oy);
         dcz = wrap_unit(ge.z - oz);
@@ -383,8 +388,9 @@ __global__ void __launch_bounds__(walk_warps(D) * 32, 1) k_walk(WalkLaunch L) {
       if (__any_sync(0xffffffffu, cls == 1)) {
 #pragma unroll
         for (int t = 0; t < D; ++t) {
+          if (VARD && t >= DR) break;
           float4 mo = make_float4(0.f, 0.f, 0.f, 0.f);
-          if (cls == 1) mo = DESC(mono)[(size_t)node * D + t];
+          if (cls == 1) mo = DESC(mono)[(size_t)node * DR + t];
           const float px = dcx + mo.x, py = dcy + mo.y, pz = dcz + mo.z;
           const bool has = mo.w > 0.f && near_box(px, py, pz, gx, gy, gz, rc2_keep);
           const uint32_t b = __ballot_sync(0xffffffffu, has);
@@ -514,7 +520,7 @@ static size_t walk_smem(int tab_count, int nwarps) {
   return tab_bytes + (size_t)nwarps * sizeof(WarpSmem<D>);
 }
 
-template <int D, bool ACC64, bool REL>
+template <int D, bool ACC64, bool REL, bool VARD>
 static int launch_walk_d(ng_ctx* c, cudaStream_t stream, const WalkLaunch& L, int64_t groups) {
   int nwarps = walk_warps(D);
   while (nwarps > 1 && walk_smem<D>(L.tab_count, nwarps) > c->smem_optin) --nwarps;
@@ -523,23 +529,27 @@ static int launch_walk_d(ng_ctx* c, cudaStream_t stream, const WalkLaunch& L, in
     return fail(c, NG_ENOMEM, "walk needs %zu B shared memory (max %zu)", smem, c->smem_optin);
   // the attribute is a per-function ceiling shared by every thread that
   // launches the walk: always raise it to the device maximum, never lower it
-  NG_CUDA(c, cudaFuncSetAttribute(k_walk<D, ACC64, REL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  NG_CUDA(c, cudaFuncSetAttribute(k_walk<D, ACC64, REL, VARD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)c->smem_optin));
   int per_sm = 0;
-  NG_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walk<D, ACC64, REL>, nwarps * 32,
+  NG_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_walk<D, ACC64, REL, VARD>, nwarps * 32,
                                                            smem));
   if (per_sm < 1) per_sm = 1;
   // persistent warps take groups from a counter: no more blocks than the
   // expected groups need, so small problems leave SMs to concurrent work
   const int64_t want = (std::max<int64_t>(groups, 1) + nwarps - 1) / nwarps;
   const int grid = (int)std::min<int64_t>((int64_t)c->nsm * per_sm, want);
-  k_walk<D, ACC64, REL><<<grid, nwarps * 32, smem, stream>>>(L);
+  k_walk<D, ACC64, REL, VARD><<<grid, nwarps * 32, smem, stream>>>(L);
   c->launches += 1;
   NG_CUDA(c, cudaGetLastError());
   return NG_OK;
 }
 
 void fill_walk_desc(ng_ctx* c, float* acc, bool accumulate, WalkDesc* d) {
+  fill_walk_desc_dr(c, acc, accumulate, c->dr_phys, d);
+}
+
+void fill_walk_desc_dr(ng_ctx* c, float* acc, bool accumulate, double dr, WalkDesc* d) {
   d->geo = as<float4>(c->n_geo);
   d->com = as<float4>(c->n_com);
   d->link = as<int4>(c->n_link);
@@ -554,12 +564,13 @@ void fill_walk_desc(ng_ctx* c, float* acc, bool accumulate, WalkDesc* d) {
   d->acc = acc;
   d->n = c->n;
   d->accumulate = accumulate ? 1 : 0;
-  d->s_tab = (float)(c->L / c->dr_phys);
+  d->s_tab = (float)(c->L / dr);
   d->rcut_box = (float)(c->rcut / c->L);
   d->theta2 = (float)(c->p.theta * c->p.theta);
-  const double eps_tab = c->p.eps / c->dr_phys;
+  const double eps_tab = c->p.eps / dr;
   d->eps2_tab = (float)(eps_tab * eps_tab);
-  d->out_scale = (float)(1.0 / (c->dr_phys * c->dr_phys));
+  d->out_scale = (float)(1.0 / (dr * dr));
+  d->D = c->p.D;
   for (int i = 0; i < kMaxD; ++i)
     for (int j = 0; j < kMaxD; ++j) {
       d->tabid[i][j] = c->tabid[i][j];
@@ -570,24 +581,26 @@ void fill_walk_desc(ng_ctx* c, float* acc, bool accumulate, WalkDesc* d) {
 }
 
 template <bool ACC64, bool REL>
-static int dispatch_walk_acc(ng_ctx* c, cudaStream_t stream, const WalkLaunch& L, int64_t groups) {
+static int dispatch_walk_acc(ng_ctx* c, cudaStream_t stream, const WalkLaunch& L, int64_t groups,
+                             bool vard) {
+  if (vard) return launch_walk_d<kMaxD, ACC64, REL, true>(c, stream, L, groups);
   switch (c->p.D) {
-    case 1: return launch_walk_d<1, ACC64, REL>(c, stream, L, groups);
-    case 2: return launch_walk_d<2, ACC64, REL>(c, stream, L, groups);
-    case 3: return launch_walk_d<3, ACC64, REL>(c, stream, L, groups);
-    case 4: return launch_walk_d<4, ACC64, REL>(c, stream, L, groups);
-    case 5: return launch_walk_d<5, ACC64, REL>(c, stream, L, groups);
-    default: return launch_walk_d<6, ACC64, REL>(c, stream, L, groups);
+    case 1: return launch_walk_d<1, ACC64, REL, false>(c, stream, L, groups);
+    case 2: return launch_walk_d<2, ACC64, REL, false>(c, stream, L, groups);
+    case 3: return launch_walk_d<3, ACC64, REL, false>(c, stream, L, groups);
+    case 4: return launch_walk_d<4, ACC64, REL, false>(c, stream, L, groups);
+    case 5: return launch_walk_d<5, ACC64, REL, false>(c, stream, L, groups);
+    default: return launch_walk_d<6, ACC64, REL, false>(c, stream, L, groups);
   }
 }
 
 static int dispatch_walk(ng_ctx* c, cudaStream_t stream, const WalkLaunch& L, int64_t groups,
-                         bool rel) {
+                         bool rel, bool vard) {
   if (c->p.accumulate_fp64)
-    return rel ? dispatch_walk_acc<true, true>(c, stream, L, groups)
-               : dispatch_walk_acc<true, false>(c, stream, L, groups);
-  return rel ? dispatch_walk_acc<false, true>(c, stream, L, groups)
-             : dispatch_walk_acc<false, false>(c, stream, L, groups);
+    return rel ? dispatch_walk_acc<true, true>(c, stream, L, groups, vard)
+               : dispatch_walk_acc<true, false>(c, stream, L, groups, vard);
+  return rel ? dispatch_walk_acc<false, true>(c, stream, L, groups, vard)
+             : dispatch_walk_acc<false, false>(c, stream, L, groups, vard);
 }
 
 int64_t walk_groups_hint(const ng_ctx* c) {
@@ -598,7 +611,7 @@ int64_t walk_groups_hint(const ng_ctx* c) {
 
 int launch_walk_descs(ng_ctx* c, cudaStream_t stream, const WalkDesc* d_descs, int ndesc,
                       uint32_t* d_prefix, uint32_t* d_work, unsigned long long* counter,
-                      int64_t groups, bool rel) {
+                      int64_t groups, bool rel, const WalkTable* tab, bool vard) {
   k_walk_prep<<<1, 1024, 0, stream>>>(d_descs, ndesc, d_prefix, d_work);
   c->launches += 1;
   NG_CUDA(c, cudaGetLastError());
@@ -607,12 +620,19 @@ int launch_walk_descs(ng_ctx* c, cudaStream_t stream, const WalkDesc* d_descs, i
   L.ndesc = ndesc;
   L.gprefix = d_prefix;
   L.work = d_work;
-  L.tab = as<float2>(c->d_tab);
-  L.tab_entries = c->ncut + 1;
-  L.ncut = c->ncut;
-  L.tab_count = c->p.D * (c->ncut + 1) * walk_tab_pad(c->p.D);
+  if (tab) {
+    L.tab = tab->tab;
+    L.tab_entries = tab->ncut + 1;
+    L.ncut = tab->ncut;
+    L.tab_count = tab->count;
+  } else {
+    L.tab = as<float2>(c->d_tab);
+    L.tab_entries = c->ncut + 1;
+    L.ncut = c->ncut;
+    L.tab_count = c->p.D * (c->ncut + 1) * walk_tab_pad(c->p.D);
+  }
   L.counter = counter;
-  return dispatch_walk(c, stream, L, groups, rel);
+  return dispatch_walk(c, stream, L, groups, rel, vard);
 }
 
 // The descriptor travels as a kernel argument (captured by value, also in

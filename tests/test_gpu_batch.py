@@ -1,9 +1,10 @@
 """Batched independent simulations: every simulation advanced inside a batch
-(sort/tree/PM on worker streams, one walk launch per species-count class)
-matches the same simulation advanced alone through ng_step. The walk is
-deterministic; the CIC deposit's FP32 atomics may add in another order, so
-the comparison allows FP32-level differences (99 % of bodies within 1e-5 of
-their displacement / velocity change, all within 1e-3)."""
+(sort/tree/PM on worker streams, one walk launch for all species counts)
+matches the same simulation advanced alone through ng_step, and, in direct
+summation, the FP64 oracle's integration. The batch's walk reads the class's
+law table (laid out for six species, its own segment count), so batch and
+alone differ at the table's accuracy (~1e-5 of a force): 99 % of bodies
+within 1e-4 of their displacement / velocity change, all within 1e-2."""
 import numpy as np
 import pytest
 
@@ -24,7 +25,7 @@ def ng():
 
 
 def _sims():
-    # uneven N and D; two simulations share D = 2 (one walk launch serves both)
+    # uneven N and D, one law and one mesh: one walk launch serves them all
     specs = [(5000, 2, 71), (20000, 2, 72), (3000, 1, 73), (12000, 4, 74), (1500, 6, 75),
              (777, 3, 76)]
     out = []
@@ -71,7 +72,7 @@ def test_batch_matches_each_simulation_alone(ng, variant):
         alone.append({k: v.cpu().numpy() for k, v in a.items()})
         s.close()
     b = ng.ng_batch_create([ng_params(w["params"]) for w in sims])
-    assert ng.ng_batch_walk_launches(b) == 5           # D = 2 shared
+    assert ng.ng_batch_walk_launches(b) == 1           # every species count in one launch
     m = [_dev(w) for w in sims]
     ng.ng_batch_step(b, [x["pos"] for x in m], [x["vel"] for x in m], [x["typ"] for x in m],
                      [x["mass"] for x in m], [x["acc"] for x in m], False, steps, dt)
@@ -80,8 +81,8 @@ def test_batch_matches_each_simulation_alone(ng, variant):
         rx = _rel_change(x["pos"].cpu().numpy(), ref["pos"], w["pos"])
         rv = _rel_change(x["vel"].cpu().numpy().astype(np.float64), ref["vel"].astype(np.float64),
                          w["vel"].astype(np.float64))
-        assert np.percentile(rx, 99) <= 1e-5 and rx.max() <= 1e-3, (np.percentile(rx, 99), rx.max())
-        assert np.percentile(rv, 99) <= 1e-5 and rv.max() <= 1e-3, (np.percentile(rv, 99), rv.max())
+        assert np.percentile(rx, 99) <= 1e-4 and rx.max() <= 1e-2, (np.percentile(rx, 99), rx.max())
+        assert np.percentile(rv, 99) <= 1e-4 and rv.max() <= 1e-2, (np.percentile(rv, 99), rv.max())
     # a second call replays the captured batch step
     ng.ng_batch_step(b, [x["pos"] for x in m], [x["vel"] for x in m], [x["typ"] for x in m],
                      [x["mass"] for x in m], [x["acc"] for x in m], True, 2, dt)
@@ -99,3 +100,34 @@ def test_batch_rejects_bad_arguments(ng):
     with pytest.raises(ng.NgError):
         ng.ng_batch_step(b, [x["pos"]], [x["vel"]], [x["typ"]], [x["mass"]], [x["acc"]], False, -1, 1e-3)
     ng.ng_batch_destroy(b)
+
+
+def test_batch_members_match_the_oracle(ng):
+    """Three simulations of D = 1, 3 and 6 in one batch, direct summation
+    (theta = 0: the batch's group walk opens every leaf) plus PM, three KDK
+    steps against the FP64 oracle's integration of each: velocity and
+    position changes within 1e-4 of the oracle's for 99 % of bodies."""
+    import torch
+    import oracle
+    from common import oracle_params
+    sims = []
+    for n, D, seed in [(3000, 1, 81), (2500, 3, 82), (2000, 6, 83)]:
+        w = small_clustered(n, D, seed, mesh=32)
+        w["params"] = dict(w["params"], theta=0.0)
+        rng = inputs.rng_for(seed + 100)
+        w["vel"] = (0.01 * rng.standard_normal((3, n))).astype(np.float32)
+        sims.append(w)
+    b = ng.ng_batch_create([ng_params(w["params"]) for w in sims])
+    assert ng.ng_batch_walk_launches(b) == 1
+    m = [_dev(w) for w in sims]
+    ng.ng_batch_step(b, [x["pos"] for x in m], [x["vel"] for x in m], [x["typ"] for x in m],
+                     [x["mass"] for x in m], [x["acc"] for x in m], False, 3, 1e-3)
+    torch.cuda.synchronize()
+    ng.ng_batch_destroy(b)
+    for w, x in zip(sims, m):
+        xo, vo, _ = oracle.kdk(oracle_params(w["params"]), w["pos"], w["vel"].astype(np.float64),
+                               w["type"], w["mass"], 3, 1e-3)
+        rx = _rel_change(x["pos"].cpu().numpy(), xo, w["pos"])
+        rv = _rel_change(x["vel"].cpu().numpy().astype(np.float64), vo, w["vel"].astype(np.float64))
+        assert np.percentile(rx, 99) <= 1e-4, np.percentile(rx, 99)
+        assert np.percentile(rv, 99) <= 1e-4, np.percentile(rv, 99)
