@@ -112,16 +112,18 @@ def stage_bytes(n, D, mesh):
     evaluation (reads + writes of the arrays each stage must touch once):
     keys 24 B position + 1 B species read, 8 B key + 4 B index written; each of
     the 8 radix passes 8 B key read by the histogram, 12 B key + index read and
-    12 B written by the scatter; gather 4 B index + 24 B position + 4 B mass +
-    1 B species read, 24 + 4 + 1 B written; type-major order 4 B index written,
+    12 B written by the scatter; type-major order 4 B index written,
     then one 32 B radix pass; deposit 33 B per body read plus the D mesh
     clears; FFTs and k-space one read and one write of the D real meshes or
     half spectra; interpolation 24 B position + 1 B species + 4 B index read,
-    12 B acceleration written (mesh reads stay in cache)."""
+    12 B acceleration written, and one read of the D potential meshes. The
+    gather of a step (ng_step keeps the state in the previous step's sorted
+    order) reads and writes 24 B position, 12 B velocity, 4 B mass, 1 B
+    species, 4 B caller index and reads the 4 B permutation."""
     real = 4 * D * mesh ** 3
     spec = 8 * D * mesh * mesh * (mesh // 2 + 1)
-    b = {"keys": 37 * n, "radix": 8 * 32 * n, "gather": 62 * n, "type_order": 36 * n,
-         "interp": 41 * n}
+    b = {"keys": 37 * n, "radix": 8 * 32 * n, "gather": (2 * 45 + 4) * n, "type_order": 36 * n,
+         "interp": 41 * n + real}
     if mesh > 0:
         b.update(deposit=33 * n + real, fft_fwd=real + spec, kspace=2 * spec, fft_inv=spec + real)
     return b

@@ -109,6 +109,10 @@ __global__ void k_kspace(cufftComplex* __restrict__ mesh, int N, float kf, float
 // -grad phi_i by 4-point central differences at the 8 CIC corners of each
 // particle of passive species i, interpolated with the CIC weights; written
 // at perm[k] (caller order) or, with perm == nullptr, at k (sorted order).
+// The three stencils of the 8 corners touch 56 distinct mesh points: along
+// each axis, for each of the 4 corner lines, the 6 points from -2 to +3
+// around the cell, the 2x2x2 corner block shared by the three axes. Each is
+// loaded once (56 loads instead of 96).
 __global__ void k_pm_interp(int64_t n, const double* __restrict__ spos,
                             const uint8_t* __restrict__ stype, const uint32_t* __restrict__ perm,
                             const float* __restrict__ phi, int N, double cells_per_len,
@@ -123,35 +127,68 @@ __global__ void k_pm_interp(int64_t n, const double* __restrict__ spos,
     const float f[3] = {(float)(ux - fx0), (float)(uy - fy0), (float)(uz - fz0)};
     const int i0[3] = {(int)fx0, (int)fy0, (int)fz0};
     const float* P = phi + (size_t)stype[k] * N3;
-    auto at = [&](int x, int y, int z) {
-      return __ldg(P + ((size_t)(x & mask) * N + (y & mask)) * N + (z & mask));
-    };
-    float a[3] = {0.f, 0.f, 0.f};
+    // wrapped offsets of the mesh points -2..+3 along each axis
+    size_t ox[6], oy[6];
+    int oz[6];
 #pragma unroll
-    for (int c = 0; c < 8; ++c) {
-      const int dx = c >> 2, dy = (c >> 1) & 1, dz = c & 1;
-      const float w = (dx ? f[0] : 1.f - f[0]) * (dy ? f[1] : 1.f - f[1]) * (dz ? f[2] : 1.f - f[2]);
-      const int x = i0[0] + dx, y = i0[1] + dy, z = i0[2] + dz;
-      const float gx = (2.f / 3.f) * (at(x + 1, y, z) - at(x - 1, y, z)) -
-                       (1.f / 12.f) * (at(x + 2, y, z) - at(x - 2, y, z));
-      const float gy = (2.f / 3.f) * (at(x, y + 1, z) - at(x, y - 1, z)) -
-                       (1.f / 12.f) * (at(x, y + 2, z) - at(x, y - 2, z));
-      const float gz = (2.f / 3.f) * (at(x, y, z + 1) - at(x, y, z - 1)) -
-                       (1.f / 12.f) * (at(x, y, z + 2) - at(x, y, z - 2));
-      a[0] = fmaf(w, gx, a[0]);
-      a[1] = fmaf(w, gy, a[1]);
-      a[2] = fmaf(w, gz, a[2]);
+    for (int d = 0; d < 6; ++d) {
+      ox[d] = (size_t)((i0[0] + d - 2) & mask) * N * N;
+      oy[d] = (size_t)((i0[1] + d - 2) & mask) * N;
+      oz[d] = (i0[2] + d - 2) & mask;
     }
+    // X[b][e][j]: the x line at y offset b, z offset e (j = x offset + 2);
+    // Y[a][e][j], Z[a][b][j] likewise; indices 2 and 3 are the corner block
+    float X[2][2][6], Y[2][2][6], Z[2][2][6];
+#pragma unroll
+    for (int b = 0; b < 2; ++b)
+#pragma unroll
+      for (int e = 0; e < 2; ++e)
+#pragma unroll
+        for (int j = 0; j < 6; ++j) X[b][e][j] = __ldg(P + ox[j] + oy[2 + b] + oz[2 + e]);
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+      for (int e = 0; e < 2; ++e)
+#pragma unroll
+        for (int j = 0; j < 6; ++j)
+          Y[a][e][j] = (j == 2 || j == 3) ? X[j - 2][e][2 + a]
+                                          : __ldg(P + ox[2 + a] + oy[j] + oz[2 + e]);
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+      for (int b = 0; b < 2; ++b)
+#pragma unroll
+        for (int j = 0; j < 6; ++j)
+          Z[a][b][j] = (j == 2 || j == 3) ? X[b][j - 2][2 + a]
+                                          : __ldg(P + ox[2 + a] + oy[2 + b] + oz[j]);
+    float g[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+      for (int b = 0; b < 2; ++b)
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          const float w = (a ? f[0] : 1.f - f[0]) * (b ? f[1] : 1.f - f[1]) * (e ? f[2] : 1.f - f[2]);
+          const float* x = X[b][e];
+          const float* y = Y[a][e];
+          const float* z = Z[a][b];
+          const float gx = (2.f / 3.f) * (x[a + 3] - x[a + 1]) - (1.f / 12.f) * (x[a + 4] - x[a]);
+          const float gy = (2.f / 3.f) * (y[b + 3] - y[b + 1]) - (1.f / 12.f) * (y[b + 4] - y[b]);
+          const float gz = (2.f / 3.f) * (z[e + 3] - z[e + 1]) - (1.f / 12.f) * (z[e + 4] - z[e]);
+          g[0] = fmaf(w, gx, g[0]);
+          g[1] = fmaf(w, gy, g[1]);
+          g[2] = fmaf(w, gz, g[2]);
+        }
     const uint32_t i = perm ? perm[k] : (uint32_t)k;
     const float s = -inv_h;
     if (accumulate) {
-      acc[i] += s * a[0];
-      acc[n + i] += s * a[1];
-      acc[2 * n + i] += s * a[2];
+      acc[i] += s * g[0];
+      acc[n + i] += s * g[1];
+      acc[2 * n + i] += s * g[2];
     } else {
-      acc[i] = s * a[0];
-      acc[n + i] = s * a[1];
-      acc[2 * n + i] = s * a[2];
+      acc[i] = s * g[0];
+      acc[n + i] = s * g[1];
+      acc[2 * n + i] = s * g[2];
     }
   }
 }
