@@ -306,6 +306,7 @@ int read_status(ng_ctx* c, uint32_t* st) {
 }
 
 int check_flags(ng_ctx* c, uint32_t flags) {
+  flags &= ~(uint32_t)SF_DEPTH;   // a capped tree is valid (see SF_DEPTH)
   if (flags & SF_NODE_OVERFLOW) return fail(c, NG_ENOMEM, "tree node capacity exceeded");
   if (flags & SF_STACK_OVERFLOW) return fail(c, NG_ENOMEM, "walk stack capacity exceeded");
   if (flags & SF_GROUP_OVERFLOW) return fail(c, NG_ENOMEM, "walk group capacity exceeded");
@@ -346,6 +347,9 @@ int tree_checked(ng_ctx* c) {
       continue;
     }
     c->nnodes = st[ST_LEVELS + kMaxLevel + 1];
+    c->depth_seen = 0;
+    for (int l = 0; l <= kMaxLevel; ++l)
+      if (st[ST_LEVELS + kMaxLevel + 2 + l] > 0) c->depth_seen = l;
     NG_TRY(reduce_monopoles(c));
     NG_TRY(build_groups(c));
     NG_TRY(type_order(c));
@@ -831,8 +835,11 @@ int ng_stage_times(ng_ctx* c, int64_t n, double* pos, float* vel, const uint8_t*
   NG_TRY(launch_drift(c, n, as<double>(c->spos_alt), as<float>(c->rvel_alt), dt));
   c->stage_seen = 0;
   c->timing = true;
+  // the tree depth of a captured step
+  c->level_cap = std::min(kMaxLevel, c->depth_seen + kCapturedDepthMargin);
   int r = sort_resident(c, n);
   if (r == NG_OK) r = tree_stages(c);
+  c->level_cap = kMaxLevel;
   if (r == NG_OK) r = force_stages(c, as<float>(c->racc));
   c->timing = false;
   if (r != NG_OK) {
@@ -910,6 +917,8 @@ int ng_step(ng_ctx* c, int64_t n, double* pos, float* vel, const uint8_t* type,
         r = fail(c, NG_ECUDA, "capture stream creation failed");
       }
       cudaStream_t user = c->stream;
+      // captured trees stop two levels below the deepest one seen so far
+      c->level_cap = std::min(kMaxLevel, c->depth_seen + kCapturedDepthMargin);
       // graph k starts from step parity k (the two captures leave the
       // assignment where it was: the captured steps do not run)
       for (int k = 0; k < 2 && r == NG_OK; ++k) {
@@ -940,6 +949,7 @@ int ng_step(ng_ctx* c, int64_t n, double* pos, float* vel, const uint8_t* type,
         cudaGraphDestroy(g);
         if (ei != cudaSuccess) r = fail(c, NG_ECUDA, "graph instantiate failed: %s", cudaGetErrorString(ei));
       }
+      c->level_cap = kMaxLevel;
       if (r == NG_OK) {
         c->graph_n = n;
         c->graph_dt = dt;
@@ -962,6 +972,8 @@ int ng_step(ng_ctx* c, int64_t n, double* pos, float* vel, const uint8_t* type,
   NG_TRY(r);
   uint32_t st[ST_COUNT];
   NG_TRY(read_status(c, st));
+  // a replayed tree outgrew the level cap (still correct): capture deeper next call
+  if (st[ST_FLAGS] & SF_DEPTH) drop_step_graphs(c);
   NG_TRY(check_flags(c, st[ST_FLAGS]));
   c->built = true;
   return NG_OK;

@@ -49,6 +49,11 @@ struct ng_batch {
 
 namespace {
 
+// Worker streams of a batch step: the per-simulation stages are chains of
+// small kernels, so more chains keep more SMs busy (batch64: 13.9 ms per
+// step with 8 workers, 11.8 with 16, 11.3 with 32).
+constexpr int kBatchWorkers = 32;
+
 int bfail(ng_batch* b, int code, const char* fmt, ...) {
   char buf[512];
   va_list ap;
@@ -111,7 +116,7 @@ int ng_batch_create(ng_batch** out, int nsim, const ng_params* params, void* str
     }
     b->sims.push_back(c);
   }
-  const int nw = std::min(nsim, 8);
+  const int nw = std::min(nsim, kBatchWorkers);
   for (int w = 0; w < nw; ++w) {
     cudaStream_t s = nullptr;
     cudaEvent_t e = nullptr;
@@ -363,10 +368,17 @@ int ng_batch_step(ng_batch* b, const int64_t* n, double* const* pos, float* cons
         return bfail(b, NG_ECUDA, "begin capture failed");
       }
       uint64_t before = 0;
-      for (const ng_ctx* c : b->sims) before += c->launches;
+      for (ng_ctx* c : b->sims) {
+        before += c->launches;
+        // captured trees stop two levels below the deepest one seen so far
+        c->level_cap = std::min(kMaxLevel, c->depth_seen + kCapturedDepthMargin);
+      }
       const int r = batch_step_once(b, n, pos, vel, type, mass, acc, dt, b->cap);
       uint64_t after = 0;
-      for (const ng_ctx* c : b->sims) after += c->launches;
+      for (ng_ctx* c : b->sims) {
+        after += c->launches;
+        c->level_cap = kMaxLevel;
+      }
       b->graph_launches = after - before;
       const cudaError_t e = cudaStreamEndCapture(b->cap, &g);
       cudaGetLastError();
@@ -392,14 +404,21 @@ int ng_batch_step(ng_batch* b, const int64_t* n, double* const* pos, float* cons
     }
     b->replay_launches += b->graph_launches;
   }
+  bool deeper = false;
   for (int i = 0; i < S; ++i) {
     ng_ctx* c = b->sims[i];
     c->stream = b->stream;
     uint32_t st[ST_COUNT];
     int r = read_status(c, st);
+    if (r == NG_OK && (st[ST_FLAGS] & SF_DEPTH)) deeper = true;
     if (r == NG_OK) r = check_flags(c, st[ST_FLAGS]);
     if (r != NG_OK) return from_sim(b, i, r);
     c->built = true;
+  }
+  // a replayed tree outgrew its level cap (still correct): capture deeper next call
+  if (deeper && b->exec) {
+    cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
   }
   return NG_OK;
 }

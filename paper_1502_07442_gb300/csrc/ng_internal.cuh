@@ -18,6 +18,7 @@ namespace ng {
 // ----------------------------------------------------------------- limits
 constexpr int kMaxD = NG_MAX_SPECIES;
 constexpr int kMaxLevel = 20;           // 20 Morton bits per axis
+constexpr int kCapturedDepthMargin = 2;  // captured steps build this far below the depth seen
 constexpr int kWarp = 32;
 
 // Status words in device memory (ctx->status).
@@ -34,7 +35,12 @@ enum StatusFlag {
   SF_STACK_OVERFLOW = 2,
   SF_GROUP_OVERFLOW = 4,
   SF_BAD_TREE = 8,
-  SF_BAD_TYPE = 16
+  SF_BAD_TYPE = 16,
+  // not an error: a build with a level cap (captured steps) kept a node at
+  // the cap whose body count is above the leaf size as a leaf. The tree is
+  // valid (leaves of any size are walked, summed and grouped) but not the
+  // canonical one; the caller captures its steps again, deeper.
+  SF_DEPTH = 32
 };
 static_assert(ST_LEVELS + (kMaxLevel + 2) + (kMaxLevel + 1) <= ST_COUNT, "status block too small");
 
@@ -230,6 +236,8 @@ struct ng_ctx {
 
   // tree
   int64_t cap_nodes = 0, nnodes = 0;
+  int level_cap = ng::kMaxLevel;   // deepest level a build emits (captured steps: depth_seen + 2)
+  int depth_seen = ng::kMaxLevel;  // deepest non-empty level of the last checked build
   int64_t ngroups = 0, ngroups_n = -1;   // walk groups of the last checked build, for n = ngroups_n
   ng::DevBuf n_level, n_prefix, n_first, n_count, n_child, n_nchild, n_tmp;
   ng::DevBuf n_m64, n_cnt, n_geo, n_com, n_link, n_mono;

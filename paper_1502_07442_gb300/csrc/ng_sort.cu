@@ -111,9 +111,10 @@ int scan_u32(ng_ctx* c, const uint32_t* in, uint32_t* out, int64_t len, const ui
   uint32_t* part = as<uint32_t>(c->scan_part);
   // blocks for at most 4 tiles each; both kernels split the range by gridDim
   const int blocks = scan_blocks(len);
-  k_scan_partial<<<blocks, kScanThreads, 0, c->stream>>>(in, len, d_len, part, 0);
+  // one block needs no partial sums (its offset is zero)
+  if (blocks > 1) k_scan_partial<<<blocks, kScanThreads, 0, c->stream>>>(in, len, d_len, part, 0);
   k_scan_final<<<blocks, kScanThreads, 0, c->stream>>>(in, out, len, d_len, part, d_total, 0);
-  c->launches += 2;
+  c->launches += blocks > 1 ? 2 : 1;
   NG_CUDA(c, cudaGetLastError());
   return NG_OK;
 }
@@ -124,9 +125,9 @@ int scan_u32_flags(ng_ctx* c, const uint32_t* in, uint32_t* out, int64_t len, ui
   NG_TRY(ensure(c, c->scan_part, kScanBlocks * sizeof(uint32_t)));
   uint32_t* part = as<uint32_t>(c->scan_part);
   const int blocks = scan_blocks(len);
-  k_scan_partial<<<blocks, kScanThreads, 0, c->stream>>>(in, len, nullptr, part, 1);
+  if (blocks > 1) k_scan_partial<<<blocks, kScanThreads, 0, c->stream>>>(in, len, nullptr, part, 1);
   k_scan_final<<<blocks, kScanThreads, 0, c->stream>>>(in, out, len, nullptr, part, d_total, 1);
-  c->launches += 2;
+  c->launches += blocks > 1 ? 2 : 1;
   NG_CUDA(c, cudaGetLastError());
   return NG_OK;
 }

@@ -6,7 +6,10 @@
 // Canonical tree: nodes are the non-empty Morton cells reachable from the
 // root; a cell is a leaf iff it holds <= leaf_size bodies or is at level 20;
 // children are the non-empty octants in octant order; nodes are numbered
-// level by level, and within a level in key order.
+// level by level, and within a level in key order. Builds inside captured
+// steps stop at a level cap two below the deepest level seen by the step
+// before the capture (fewer launches per level-free tail); a cell at the cap
+// is then a leaf whatever it holds, and SF_DEPTH says so.
 #include "ng_internal.cuh"
 
 namespace ng {
@@ -73,10 +76,12 @@ __device__ __forceinline__ OctTeam octant_team(const uint64_t* __restrict__ keys
   return t;
 }
 
-__global__ void k_tree_count(int lvl, uint32_t* status, int64_t cap, int leaf_size,
+// lmax: the deepest level the build emits (kMaxLevel unless capped); nodes
+// of level lmax are leaves, and one above the leaf size raises SF_DEPTH.
+__global__ void k_tree_count(int lvl, int lmax, uint32_t* status, int64_t cap, int leaf_size,
                              const uint64_t* __restrict__ keys, const uint32_t* __restrict__ first,
                              const uint32_t* __restrict__ count, uint8_t* nchild,
-                             uint32_t* tmp) {
+                             uint32_t* child, uint32_t* tmp) {
   Levels lv = levels_of(status);
   const uint32_t s = lv.start[lvl];
   uint32_t e = lv.start[lvl + 1];
@@ -91,12 +96,16 @@ __global__ void k_tree_count(int lvl, uint32_t* status, int64_t cap, int leaf_si
     const bool valid = j < nodes;
     const uint32_t k = s + (uint32_t)j;
     const uint32_t f = valid ? first[k] : 0u, c = valid ? count[k] : 0u;
-    const bool split = valid && (int)c > leaf_size && lvl < kMaxLevel;
+    const bool split = valid && (int)c > leaf_size && lvl < lmax;
     const OctTeam t = octant_team(keys, split, f, c, shift, sub, lane);
     if (valid && sub == 0) {
       const uint32_t nch = (uint32_t)__popc(t.bits);
       nchild[k] = (uint8_t)nch;
       tmp[k - s] = nch;
+      if (lvl == lmax) {
+        child[k] = 0xffffffffu;   // no emit follows the last level
+        if ((int)c > leaf_size && lmax < kMaxLevel) atomicOr(&status[ST_FLAGS], (uint32_t)SF_DEPTH);
+      }
     }
   }
 }
@@ -152,6 +161,17 @@ __global__ void k_tree_emit(int lvl, uint32_t* status, int64_t cap,
   }
 }
 
+// A build capped at level lmax < kMaxLevel: the levels below it are empty
+// (their starts all equal the end of level lmax), as the node total and the
+// per-level kernels that follow expect.
+__global__ void k_tree_close(uint32_t* status, int lmax) {
+  if (threadIdx.x == 0) {
+    Levels lv = levels_of(status);
+    const uint32_t end = lv.start[lmax + 1];
+    for (int l = lmax + 2; l <= kMaxLevel + 1; ++l) lv.start[l] = end;
+  }
+}
+
 int build_octree(ng_ctx* c) {
   const int64_t n = c->n;
   const int64_t cap = c->cap_nodes;
@@ -165,20 +185,26 @@ int build_octree(ng_ctx* c) {
   uint32_t* tmp = as<uint32_t>(c->n_tmp);
   const uint64_t* keys = as<uint64_t>(c->keys_a);
   const int leaf = c->p.leaf_size;
+  const int lmax = std::min(std::max(c->level_cap, 0), kMaxLevel);
   stage_mark(c, NG_STAGE_OCTREE);
   k_tree_init<<<1, 32, 0, c->stream>>>(st, n, level, prefix, first, count);
-  c->launches += 1 + (kMaxLevel + 1) + kMaxLevel;   // init, counts, emits (scans count themselves)
-  for (int l = 0; l <= kMaxLevel; ++l) {
+  c->launches += 1 + (lmax + 1) + lmax;   // init, counts, emits (scans count themselves)
+  for (int l = 0; l <= lmax; ++l) {
     // grids sized by the most nodes level l can hold (kernels stride over the actual count)
     const int64_t bound = std::min<int64_t>(cap, level_bound(l, c->n));
     const int grid = work_grid(c, 8 * bound, 4);   // 8 lanes per node
-    k_tree_count<<<grid, 256, 0, c->stream>>>(l, st, cap, leaf, keys, first, count, nchild, tmp);
-    if (l == kMaxLevel) break;
+    k_tree_count<<<grid, 256, 0, c->stream>>>(l, lmax, st, cap, leaf, keys, first, count, nchild,
+                                              child, tmp);
+    if (l == lmax) break;
     // children per level: exclusive scan of the per-node child counts
     uint32_t* lvcount = st + ST_LEVELS + kMaxLevel + 2;
     NG_TRY(scan_u32(c, tmp, tmp, bound, lvcount + l, lvcount + l + 1));
     k_tree_emit<<<grid, 256, 0, c->stream>>>(l, st, cap, keys, level, prefix, first, count,
                                              nchild, child, tmp);
+  }
+  if (lmax < kMaxLevel) {
+    k_tree_close<<<1, 32, 0, c->stream>>>(st, lmax);
+    c->launches += 1;
   }
   NG_CUDA(c, cudaGetLastError());
   return NG_OK;
@@ -350,9 +376,10 @@ int reduce_monopoles(ng_ctx* c) {
   a.cap = c->cap_nodes;
   a.invL = 1.0 / c->L;
   a.L = c->L;
-  c->launches += kMaxLevel + 1;
+  const int lmax = std::min(std::max(c->level_cap, 0), kMaxLevel);   // deeper levels are empty
+  c->launches += lmax + 1;
   stage_mark(c, NG_STAGE_MONOPOLES);
-  for (int l = kMaxLevel; l >= 0; --l) {
+  for (int l = lmax; l >= 0; --l) {
     const int64_t nodes = std::min<int64_t>(c->cap_nodes, level_bound(l, c->n));
     const int grid = (int)std::max<int64_t>(
         1, std::min<int64_t>((int64_t)c->nsm * 16, (nodes + kMonoThreads - 1) / kMonoThreads));
