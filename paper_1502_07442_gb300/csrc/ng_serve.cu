@@ -42,6 +42,7 @@ struct Slot {
   ng_ctx* ctx = nullptr;
   cudaStream_t stream = nullptr;
   cudaEvent_t done = nullptr;
+  cudaEvent_t first_tree = nullptr;   // the request's first tree is built
   DevBuf pos, vel, acc, type, mass;
   uint32_t* h_status = nullptr;       // pinned copy of the status words
   int64_t req = -1;                   // request in flight (-1: free)
@@ -125,11 +126,24 @@ int prepare_slot(ng_server* s, Slot& sl, const ng_request& r) {
   return reserve(c, n);
 }
 
+// Restores the full tree depth of a slot's context on every exit path.
+struct LevelCapReset {
+  ng_ctx* c;
+  ~LevelCapReset() { c->level_cap = kMaxLevel; }
+};
+
+// Seconds a launch thread waits for its request's first tree.
+constexpr double kFirstTreeWait = 120.0;
+
 // Enqueue the whole request on the slot's stream (launch thread; the slot
-// was prepared by prepare_slot).
+// was prepared by prepare_slot). For an integration the thread waits (bounded)
+// for the first tree only, while the first force runs: the trees of the steps
+// then stop two levels below its depth (cells at the cap stay leaves, a valid
+// tree; see SF_DEPTH), which saves the launches of the empty deeper levels.
 int launch_request(ng_server* s, Slot& sl, Req& q) {
   ng_ctx* c = sl.ctx;
   c->stream = sl.stream;
+  LevelCapReset reset_cap{c};
   const uint64_t gen = c->alloc_gen;
   const ng_request& r = q.r;
   const int64_t n = r.n;
@@ -151,8 +165,29 @@ int launch_request(ng_server* s, Slot& sl, Req& q) {
   // force at the input positions
   NG_TRY(sort_bodies(c, n, pos, type, mass));
   NG_TRY(tree_stages(c));
+  const bool steps = r.kind == NG_REQ_STEPS && r.nsteps > 0;
+  if (steps) {
+    // the first tree's level counts (read back before the final status copy
+    // reuses the buffer)
+    NG_CUDA(c, cudaMemcpyAsync(sl.h_status, c->status.p, ST_COUNT * 4, cudaMemcpyDeviceToHost,
+                               sl.stream));
+    NG_CUDA(c, cudaEventRecord(sl.first_tree, sl.stream));
+  }
   NG_TRY(force_stages(c, acc));
   if (r.kind == NG_REQ_STEPS) {
+    if (steps) {
+      const double t0 = now_s();
+      cudaError_t e;
+      while ((e = cudaEventQuery(sl.first_tree)) == cudaErrorNotReady) {
+        if (now_s() - t0 > kFirstTreeWait) return fail(c, NG_ETIMEOUT, "first tree not built in time");
+        std::this_thread::sleep_for(std::chrono::microseconds(20));
+      }
+      NG_CUDA(c, e);
+      int depth = 0;
+      for (int l = 0; l <= kMaxLevel; ++l)
+        if (sl.h_status[ST_LEVELS + kMaxLevel + 2 + l] > 0) depth = l;
+      c->level_cap = std::min(kMaxLevel, depth + kCapturedDepthMargin);
+    }
     for (int st = 0; st < r.nsteps; ++st) {
       NG_TRY(launch_kick(c, n, vel, acc, 0.5 * r.dt));
       NG_TRY(launch_drift(c, n, pos, vel, r.dt));
@@ -340,6 +375,7 @@ int ng_serve_create(ng_server** out, int slots, size_t hbm_budget) {
     Slot& sl = *s->slots.back();
     cudaError_t e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.first_tree, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaHostAlloc((void**)&sl.h_status, ST_COUNT * 4, cudaHostAllocDefault);
     int rc = e == cudaSuccess ? NG_OK : NG_ECUDA;
     if (e != cudaSuccess) {
@@ -389,6 +425,7 @@ int ng_serve_destroy(ng_server* s) {
     }
     if (sl.h_status) cudaFreeHost(sl.h_status);
     if (sl.done) cudaEventDestroy(sl.done);
+    if (sl.first_tree) cudaEventDestroy(sl.first_tree);
     if (sl.stream) cudaStreamDestroy(sl.stream);
   }
   delete s;
