@@ -107,12 +107,13 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
-def stage_bytes(n, D, mesh):
+def stage_bytes(n, D, mesh, passes=8):
     """Algorithmic DRAM bytes of the memory-bound stages of one force
     evaluation (reads + writes of the arrays each stage must touch once):
-    keys 24 B position + 1 B species read, 8 B key + 4 B index written; each of
-    the 8 radix passes 8 B key read by the histogram, 12 B key + index read and
-    12 B written by the scatter; type-major order 4 B index written,
+    keys 24 B position + 1 B species read, 8 B key + 4 B index written; each
+    radix pass (8 for a full sort, fewer when the step's tree stops at a level
+    cap) 8 B key read by the histogram, 12 B key + index read and 12 B written
+    by the scatter; type-major order 4 B index written,
     then one 32 B radix pass; deposit 33 B per body read plus the D mesh
     clears; FFTs and k-space one read and one write of the D real meshes or
     half spectra; interpolation 24 B position + 1 B species + 4 B index read,
@@ -122,17 +123,18 @@ def stage_bytes(n, D, mesh):
     species, 4 B caller index and reads the 4 B permutation."""
     real = 4 * D * mesh ** 3
     spec = 8 * D * mesh * mesh * (mesh // 2 + 1)
-    b = {"keys": 37 * n, "radix": 8 * 32 * n, "gather": (2 * 45 + 4) * n, "type_order": 36 * n,
+    b = {"keys": 37 * n, "radix": passes * 32 * n, "gather": (2 * 45 + 4) * n, "type_order": 36 * n,
          "interp": 41 * n + real}
     if mesh > 0:
         b.update(deposit=33 * n + real, fft_fwd=real + spec, kspace=2 * spec, fft_inv=spec + real)
     return b
 
 
-def hbm_block(times, n, D, mesh):
+def hbm_block(times, n, D, mesh, passes=8):
     peak, src = measured_peaks()
-    out = {"peak_gbs": peak, "peak_source": f"{src} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
-    for k, nbytes in stage_bytes(n, D, mesh).items():
+    out = {"peak_gbs": peak, "peak_source": f"{src} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+           "radix_passes": passes}
+    for k, nbytes in stage_bytes(n, D, mesh, passes).items():
         ms = times.get(k, 0.0)
         if ms > 0:
             gbs = nbytes / (ms / 1e3) / 1e9
@@ -403,7 +405,8 @@ def main():
     for _ in range(3):
         t = ng.ng_stage_times(sim.ctx, pos, vel, typ, mass, acc, dt)
         best = {k: min(v, best.get(k, v)) for k, v in t.items()}
-    hbm = hbm_block(best, n, int(w["params"]["D"]), int(w["params"]["pm_mesh"]))
+    hbm = hbm_block(best, n, int(w["params"]["D"]), int(w["params"]["pm_mesh"]),
+                    ng.ng_sort_passes(sim.ctx))
     roofline = {"bound": "alu", "achieved": round(achieved_own, 3), "peak": round(peak, 2),
                 "unit": "TFLOP/s", "frac": round(achieved_own / peak, 4),
                 "frac_basis": "23 flop x per-particle walk interactions on the walk's own tree "
@@ -540,7 +543,7 @@ def bench_batch(args, ws, rank, local):
                        "n_range": [int(min(x["typ"].numel() for x in state)),
                                    int(max(x["typ"].numel() for x in state))],
                        "pm_mesh": 64, "walk_launches_per_step": ng.ng_batch_walk_launches(b),
-                       "step": "one graph: per-simulation sort/tree/PM on 8 streams, one walk per D class",
+                       "step": "one graph: per-simulation sort/tree/PM on 32 worker streams, one walk launch",
                        "autotune": tuned},
             "particles_per_s": nbodies * args.steps / (ms / 1e3), "clocks": clk.summary(),
             "gpu_launches": int(ng.ng_batch_launch_count(b) - l0)}

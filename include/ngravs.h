@@ -446,6 +446,14 @@ int ng_stage_times(ng_ctx* ctx, int64_t n, double* pos, float* vel, const uint8_
 int ng_launch_count(const ng_ctx* ctx, uint64_t* out);
 
 /*
+ * Radix passes (8 key bits each) of the context's last key sort: 8 for a
+ * canonical build; fewer in steps whose trees stop at a level cap (captured
+ * steps, served integrations), which sort only the Morton bits of their
+ * levels. Sizes the sort's bytes in per-stage bandwidth figures.
+ */
+int ng_sort_passes(const ng_ctx* ctx, int32_t* out);
+
+/*
  * Sorted keys and permutation without any allocation (the paper has no
  * counterpart: this is for callers that cannot call cudaMalloc, e.g. code
  * running while another framework holds the memory pool, or a host that

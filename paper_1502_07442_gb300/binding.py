@@ -99,6 +99,7 @@ def lib():
         L.ng_tree_export.argtypes = [vp, ctypes.POINTER(i64)] + [vp] * 9
         L.ng_type_order.argtypes = [vp, vp, vp]
         L.ng_launch_count.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64)]
+        L.ng_sort_passes.argtypes = [vp, ctypes.POINTER(i32)]
         L.ng_batch_create.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(NgParams), vp]
         L.ng_batch_destroy.argtypes = [vp]
         L.ng_batch_step.argtypes = [vp, vp, vp, vp, vp, vp, vp, i32, i32, d]
@@ -132,7 +133,8 @@ def lib():
         for f in ("ng_create", "ng_destroy", "ng_set_stream", "ng_build_tree", "ng_tree_force",
                   "ng_count_interactions", "ng_pm_force", "ng_force", "ng_stage_times", "ng_step",
                   "ng_tree_export",
-                  "ng_type_order", "ng_launch_count", "ng_batch_create", "ng_batch_destroy",
+                  "ng_type_order", "ng_launch_count", "ng_sort_passes", "ng_batch_create",
+                  "ng_batch_destroy",
                   "ng_batch_step", "ng_batch_size", "ng_batch_walk_launches",
                   "ng_batch_launch_count", "ng_serve_create", "ng_serve_destroy",
                   "ng_serve_submit", "ng_serve_cancel", "ng_serve_poll", "ng_serve_pending",
@@ -147,7 +149,7 @@ def exported_symbols():
     return ["ng_create", "ng_destroy", "ng_set_stream", "ng_build_tree", "ng_tree_force",
             "ng_count_interactions", "ng_pm_force", "ng_force", "ng_stage_times", "ng_step",
             "ng_tree_export", "ng_type_order",
-            "ng_launch_count", "ng_last_error", "ng_version", "ng_batch_create",
+            "ng_launch_count", "ng_sort_passes", "ng_last_error", "ng_version", "ng_batch_create",
             "ng_batch_destroy", "ng_batch_step", "ng_batch_size", "ng_batch_walk_launches",
             "ng_batch_launch_count", "ng_batch_last_error", "ng_serve_create",
             "ng_serve_destroy", "ng_serve_submit", "ng_serve_cancel", "ng_serve_poll",
@@ -321,6 +323,12 @@ def ng_type_order(ctx, D, order_out=None):
 def ng_launch_count(ctx):
     v = ctypes.c_uint64(0)
     _check(ctx, lib().ng_launch_count(ctx, ctypes.byref(v)))
+    return int(v.value)
+
+
+def ng_sort_passes(ctx):
+    v = ctypes.c_int32(0)
+    _check(ctx, lib().ng_sort_passes(ctx, ctypes.byref(v)))
     return int(v.value)
 
 

@@ -178,15 +178,34 @@ __global__ void k_kick(int64_t m, float* __restrict__ vel, const float* __restri
     vel[i] = fmaf(acc[i], h, vel[i]);
 }
 
-__global__ void k_drift(int64_t m, double* __restrict__ pos, const float* __restrict__ vel,
-                        double dt, double L, double invL, bool pow2) {
+
+// Per element: nkick kicks v += a h (each rounded as k_kick), then the FP64
+// drift x += v dt with the periodic wrap (in a power-of-two box, x in [+0, L)
+// wraps to itself, decided on the bits). One launch for the opening kick and
+// drift of a step, or (nkick = 2) for the closing kick of a step with the
+// opening kick and drift of the next.
+__global__ void k_kick_drift(int64_t m, float* __restrict__ vel, const float* __restrict__ acc,
+                             float h, int nkick, double* __restrict__ pos, double dt, double L,
+                             double invL, bool pow2) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const double x = fma((double)vel[i], dt, pos[i]);
-    // in a power-of-two box, x in [+0, L) wraps to itself (decided on the bits)
+    const float a = acc[i];
+    float v = fmaf(a, h, vel[i]);
+    if (nkick == 2) v = fmaf(a, h, v);
+    vel[i] = v;
+    const double x = fma((double)v, dt, pos[i]);
     const long long b = __double_as_longlong(x);
     pos[i] = pow2 && b >= 0 && b < __double_as_longlong(L) ? x : x - L * floor(pow2 ? x * invL : x / L);
   }
+}
+
+int launch_kick_drift(ng_ctx* c, int64_t n, float* vel, const float* acc, double h, int nkick,
+                      double* pos, double dt) {
+  k_kick_drift<<<work_grid(c, 3 * n, 8), 256, 0, c->stream>>>(3 * n, vel, acc, (float)h, nkick, pos,
+                                                          dt, c->L, 1.0 / c->L, box_is_pow2(c->L));
+  c->launches += 1;
+  NG_CUDA(c, cudaGetLastError());
+  return NG_OK;
 }
 
 int launch_kick(ng_ctx* c, int64_t n, float* vel, const float* acc, double h) {
@@ -196,13 +215,6 @@ int launch_kick(ng_ctx* c, int64_t n, float* vel, const float* acc, double h) {
   return NG_OK;
 }
 
-int launch_drift(ng_ctx* c, int64_t n, double* pos, const float* vel, double dt) {
-  k_drift<<<work_grid(c, 3 * n, 8), 256, 0, c->stream>>>(3 * n, pos, vel, dt, c->L, 1.0 / c->L,
-                                                    box_is_pow2(c->L));
-  c->launches += 1;
-  NG_CUDA(c, cudaGetLastError());
-  return NG_OK;
-}
 
 // ------------------------------------------- relative opening criterion
 
@@ -594,8 +606,8 @@ int resident_store(ng_ctx* c, int64_t n, double* pos, float* vel, float* acc) {
 // sorted order; the forces are written in that order.
 int resident_step_once(ng_ctx* c, int64_t n, double dt, bool checked) {
   swap_resident(c);
-  NG_TRY(launch_kick(c, n, as<float>(c->rvel_alt), as<float>(c->racc), 0.5 * dt));
-  NG_TRY(launch_drift(c, n, as<double>(c->spos_alt), as<float>(c->rvel_alt), dt));
+  NG_TRY(launch_kick_drift(c, n, as<float>(c->rvel_alt), as<float>(c->racc), 0.5 * dt, 1,
+                           as<double>(c->spos_alt), dt));
   NG_TRY(sort_resident(c, n));
   if (checked) NG_TRY(tree_checked(c));
   else NG_TRY(tree_stages(c));
@@ -831,8 +843,8 @@ int ng_stage_times(ng_ctx* c, int64_t n, double* pos, float* vel, const uint8_t*
   // step does, from the previous step's sorted order
   NG_TRY(resident_step_once(c, n, dt, false));
   swap_resident(c);
-  NG_TRY(launch_kick(c, n, as<float>(c->rvel_alt), as<float>(c->racc), 0.5 * dt));
-  NG_TRY(launch_drift(c, n, as<double>(c->spos_alt), as<float>(c->rvel_alt), dt));
+  NG_TRY(launch_kick_drift(c, n, as<float>(c->rvel_alt), as<float>(c->racc), 0.5 * dt, 1,
+                           as<double>(c->spos_alt), dt));
   c->stage_seen = 0;
   c->timing = true;
   // the tree depth of a captured step
@@ -1083,6 +1095,12 @@ int ng_type_order(ng_ctx* c, int64_t* type_offsets, uint32_t* order_out) {
 int ng_launch_count(const ng_ctx* c, uint64_t* out) {
   if (!c || !out) return NG_EINVAL;
   *out = c->launches;
+  return NG_OK;
+}
+
+int ng_sort_passes(const ng_ctx* c, int32_t* out) {
+  if (!c || !out) return NG_EINVAL;
+  *out = c->sort_passes;
   return NG_OK;
 }
 

@@ -234,8 +234,7 @@ int batch_step_once(ng_batch* b, const int64_t* n, double* const* pos, float* co
     ng_ctx* c = b->sims[i];
     cudaStream_t keep = c->stream;
     c->stream = b->workers[i % W];
-    int r = launch_kick(c, n[i], vel[i], acc[i], 0.5 * dt);
-    if (r == NG_OK) r = launch_drift(c, n[i], pos[i], vel[i], dt);
+    int r = launch_kick_drift(c, n[i], vel[i], acc[i], 0.5 * dt, 1, pos[i], dt);
     if (r == NG_OK) r = sort_bodies(c, n[i], pos[i], type[i], mass[i]);
     if (r == NG_OK) r = tree_stages(c);
     if (r == NG_OK) {
@@ -333,8 +332,7 @@ int ng_batch_step(ng_batch* b, const int64_t* n, double* const* pos, float* cons
     for (int i = 0; i < S; ++i) {
       ng_ctx* c = b->sims[i];
       c->stream = b->stream;
-      int r = launch_kick(c, n[i], vel[i], acc[i], 0.5 * dt);
-      if (r == NG_OK) r = launch_drift(c, n[i], pos[i], vel[i], dt);
+      int r = launch_kick_drift(c, n[i], vel[i], acc[i], 0.5 * dt, 1, pos[i], dt);
       if (r == NG_OK) r = build_checked(c, n[i], pos[i], type[i], mass[i]);
       if (r == NG_OK) r = force_stages(c, acc[i]);
       if (r == NG_OK) r = launch_kick(c, n[i], vel[i], acc[i], 0.5 * dt);

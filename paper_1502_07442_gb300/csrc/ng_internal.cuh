@@ -238,6 +238,7 @@ struct ng_ctx {
   int64_t cap_nodes = 0, nnodes = 0;
   int level_cap = ng::kMaxLevel;   // deepest level a build emits (captured steps: depth_seen + 2)
   int depth_seen = ng::kMaxLevel;  // deepest non-empty level of the last checked build
+  int sort_passes = 0;             // radix passes of the last key sort
   int64_t ngroups = 0, ngroups_n = -1;   // walk groups of the last checked build, for n = ngroups_n
   ng::DevBuf n_level, n_prefix, n_first, n_count, n_child, n_nchild, n_tmp;
   ng::DevBuf n_m64, n_cnt, n_geo, n_com, n_link, n_mono;
@@ -429,7 +430,9 @@ int tree_checked(ng_ctx* c);                   // tree stages of the sorted bodi
 int tree_stages(ng_ctx* c);
 int force_stages(ng_ctx* c, float* acc);
 int launch_kick(ng_ctx* c, int64_t n, float* vel, const float* acc, double h);
-int launch_drift(ng_ctx* c, int64_t n, double* pos, const float* vel, double dt);
+// nkick (1 or 2) kicks of h, then the drift (one launch, same rounding as the two)
+int launch_kick_drift(ng_ctx* c, int64_t n, float* vel, const float* acc, double h, int nkick,
+                      double* pos, double dt);
 int alloc_nodes(ng_ctx* c, int64_t cap);
 int read_status(ng_ctx* c, uint32_t* st);      // synchronises c->stream
 int alloc_bodies(ng_ctx* c, int64_t n);

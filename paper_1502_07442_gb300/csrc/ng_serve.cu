@@ -188,14 +188,14 @@ int launch_request(ng_server* s, Slot& sl, Req& q) {
         if (sl.h_status[ST_LEVELS + kMaxLevel + 2 + l] > 0) depth = l;
       c->level_cap = std::min(kMaxLevel, depth + kCapturedDepthMargin);
     }
+    // a step's closing kick goes with the next step's opening kick and drift
     for (int st = 0; st < r.nsteps; ++st) {
-      NG_TRY(launch_kick(c, n, vel, acc, 0.5 * r.dt));
-      NG_TRY(launch_drift(c, n, pos, vel, r.dt));
+      NG_TRY(launch_kick_drift(c, n, vel, acc, 0.5 * r.dt, st == 0 ? 1 : 2, pos, r.dt));
       NG_TRY(sort_bodies(c, n, pos, type, mass));
       NG_TRY(tree_stages(c));
       NG_TRY(force_stages(c, acc));
-      NG_TRY(launch_kick(c, n, vel, acc, 0.5 * r.dt));
     }
+    if (r.nsteps > 0) NG_TRY(launch_kick(c, n, vel, acc, 0.5 * r.dt));
     if (r.pos_out) NG_CUDA(c, cudaMemcpyAsync(r.pos_out, pos, n * 24, cudaMemcpyDeviceToHost, sl.stream));
     if (r.vel_out) NG_CUDA(c, cudaMemcpyAsync(r.vel_out, vel, n * 12, cudaMemcpyDeviceToHost, sl.stream));
   }

@@ -363,10 +363,20 @@ static int sort_keys(ng_ctx* c, int64_t n, const double* pos, const uint8_t* typ
                                       pow2 ? std::ilogb(c->L) : 0, ka, va);
   c->launches += 1;
   NG_CUDA(c, cudaGetLastError());
-  // 8 passes of 8 bits: the result returns to (ka, va)
+  // 8 passes of 8 bits: the result returns to (ka, va). A tree capped at
+  // level_cap reads the Morton bits of its levels only (bits >= 3 + 3 (20 -
+  // cap)), so the passes below them are skipped, keeping an even number of
+  // passes: bodies that share those bits keep their previous relative order,
+  // and every cell down to the cap is still one contiguous range.
+  int first = 0;
+  if (c->level_cap < kMaxLevel) {
+    first = (3 + 3 * (kMaxLevel - std::max(c->level_cap, 0))) / 8;
+    if ((8 - first) & 1) --first;
+  }
+  c->sort_passes = 8 - first;
   stage_mark(c, NG_STAGE_RADIX);
-  for (int pass = 0; pass < 8; ++pass) {
-    const bool even = (pass & 1) == 0;
+  for (int pass = first; pass < 8; ++pass) {
+    const bool even = ((pass - first) & 1) == 0;
     NG_TRY(radix_pass(c, even ? ka : kb, even ? va : vb, even ? kb : ka, even ? vb : va, n,
                       8 * pass, 0xffu));
   }

@@ -609,12 +609,11 @@ int64_t walk_groups_hint(const ng_ctx* c) {
   return c->ngroups_n == c->n && c->ngroups > 0 ? c->ngroups : (c->n + 15) / 16;
 }
 
-int launch_walk_descs(ng_ctx* c, cudaStream_t stream, const WalkDesc* d_descs, int ndesc,
-                      uint32_t* d_prefix, uint32_t* d_work, unsigned long long* counter,
-                      int64_t groups, bool rel, const WalkTable* tab, bool vard) {
-  k_walk_prep<<<1, 1024, 0, stream>>>(d_descs, ndesc, d_prefix, d_work);
-  c->launches += 1;
-  NG_CUDA(c, cudaGetLastError());
+// The walk of one launch over descriptors already in device memory (their
+// group prefix and the work counter ready).
+static int launch_walk_ready(ng_ctx* c, cudaStream_t stream, const WalkDesc* d_descs, int ndesc,
+                             uint32_t* d_prefix, uint32_t* d_work, unsigned long long* counter,
+                             int64_t groups, bool rel, const WalkTable* tab, bool vard) {
   WalkLaunch L;
   L.descs = d_descs;
   L.ndesc = ndesc;
@@ -635,11 +634,30 @@ int launch_walk_descs(ng_ctx* c, cudaStream_t stream, const WalkDesc* d_descs, i
   return dispatch_walk(c, stream, L, groups, rel, vard);
 }
 
-// The descriptor travels as a kernel argument (captured by value, also in
-// graphs) and is stored to device memory by one thread: no host buffer has
-// to outlive the launch and no pageable copy stalls the stream.
-__global__ void k_put_desc(const WalkDesc d, WalkDesc* out) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) *out = d;
+int launch_walk_descs(ng_ctx* c, cudaStream_t stream, const WalkDesc* d_descs, int ndesc,
+                      uint32_t* d_prefix, uint32_t* d_work, unsigned long long* counter,
+                      int64_t groups, bool rel, const WalkTable* tab, bool vard) {
+  k_walk_prep<<<1, 1024, 0, stream>>>(d_descs, ndesc, d_prefix, d_work);
+  c->launches += 1;
+  NG_CUDA(c, cudaGetLastError());
+  return launch_walk_ready(c, stream, d_descs, ndesc, d_prefix, d_work, counter, groups, rel, tab,
+                           vard);
+}
+
+// One simulation: the descriptor travels as a kernel argument (captured by
+// value, also in graphs) and one thread stores it to device memory with the
+// group prefix and the zeroed work counter, so no host buffer has to outlive
+// the launch and no pageable copy stalls the stream.
+__global__ void k_walk_prep1(const WalkDesc d, WalkDesc* out, uint32_t* gprefix, uint32_t* work) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    *out = d;
+    uint32_t ng = d.status[ST_NGROUPS];
+    if (ng > (uint64_t)d.n) ng = (uint32_t)d.n;
+    if (d.status[ST_FLAGS] & SF_NODE_OVERFLOW) ng = 0;
+    gprefix[0] = 0;
+    gprefix[1] = ng;
+    *work = 0;
+  }
 }
 
 int launch_walk(ng_ctx* c, float* acc, bool accumulate, bool count) {
@@ -647,13 +665,13 @@ int launch_walk(ng_ctx* c, float* acc, bool accumulate, bool count) {
   NG_TRY(ensure(c, c->walk_prefix, 4 * sizeof(uint32_t)));
   WalkDesc d;
   fill_walk_desc(c, acc, accumulate, &d);
-  k_put_desc<<<1, 32, 0, c->stream>>>(d, as<WalkDesc>(c->walk_desc));
+  uint32_t* pre = as<uint32_t>(c->walk_prefix);
+  k_walk_prep1<<<1, 32, 0, c->stream>>>(d, as<WalkDesc>(c->walk_desc), pre, pre + 2);
   c->launches += 1;
   NG_CUDA(c, cudaGetLastError());
-  uint32_t* pre = as<uint32_t>(c->walk_prefix);
-  return launch_walk_descs(c, c->stream, as<WalkDesc>(c->walk_desc), 1, pre, pre + 2,
+  return launch_walk_ready(c, c->stream, as<WalkDesc>(c->walk_desc), 1, pre, pre + 2,
                            count ? as<unsigned long long>(c->counter) : nullptr,
-                           walk_groups_hint(c), d.aold != nullptr);
+                           walk_groups_hint(c), d.aold != nullptr, nullptr, false);
 }
 
 // ------------------------------------------------ per-particle count walk
