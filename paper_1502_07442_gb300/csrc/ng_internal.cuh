@@ -19,6 +19,12 @@ namespace ng {
 constexpr int kMaxD = NG_MAX_SPECIES;
 constexpr int kMaxLevel = 20;           // 20 Morton bits per axis
 constexpr int kCapturedDepthMargin = 2;  // captured steps build this far below the depth seen
+// Trees of at most kClusterMaxBodies bodies are built, and their monopoles
+// reduced, by one launch each: a cluster of kClusterBlocks blocks that runs
+// every level with the hardware cluster barrier between levels (larger trees:
+// one launch per level and phase, over the whole GPU).
+constexpr int kClusterBlocks = 8;
+constexpr int64_t kClusterMaxBodies = 32768;
 constexpr int kWarp = 32;
 
 // Status words in device memory (ctx->status).
@@ -415,6 +421,35 @@ __host__ __device__ inline double short_law_factor(int law, double a, double l, 
     T += a * (S - rho * dS);
   }
   return T;
+}
+
+// Inclusive scan of one value per thread over a block of THREADS threads
+// (warp shuffles, then the warp totals); *total receives the block's sum.
+
+template <int THREADS>
+__device__ __forceinline__ uint32_t block_inclusive_scan(uint32_t v, uint32_t* warp_tot,
+                                                         uint32_t* total) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t t = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += t;
+  }
+  if (lane == 31) warp_tot[wid] = v;
+  __syncthreads();
+  if (wid == 0) {
+    uint32_t w = lane < THREADS / 32 ? warp_tot[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t t = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += t;
+    }
+    if (lane < THREADS / 32) warp_tot[lane] = w;
+    if (lane == THREADS / 32 - 1) *total = w;
+  }
+  __syncthreads();
+  if (wid > 0) v += warp_tot[wid - 1];
+  return v;
 }
 
 // Blocks of 256 threads for a grid-stride kernel over `items` items: enough

@@ -9,34 +9,6 @@
 
 namespace ng {
 
-// ------------------------------------------------------------ block scan
-
-template <int THREADS>
-__device__ __forceinline__ uint32_t block_inclusive_scan(uint32_t v, uint32_t* warp_tot,
-                                                         uint32_t* total) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    uint32_t t = __shfl_up_sync(0xffffffffu, v, o);
-    if (lane >= o) v += t;
-  }
-  if (lane == 31) warp_tot[wid] = v;
-  __syncthreads();
-  if (wid == 0) {
-    uint32_t w = lane < THREADS / 32 ? warp_tot[lane] : 0;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      uint32_t t = __shfl_up_sync(0xffffffffu, w, o);
-      if (lane >= o) w += t;
-    }
-    if (lane < THREADS / 32) warp_tot[lane] = w;
-    if (lane == THREADS / 32 - 1) *total = w;
-  }
-  __syncthreads();
-  if (wid > 0) v += warp_tot[wid - 1];
-  return v;
-}
-
 constexpr int kScanThreads = 1024;
 constexpr int kScanBlocks = 256;
 

@@ -10,6 +10,8 @@
 // steps stop at a level cap two below the deepest level seen by the step
 // before the capture (fewer launches per level-free tail); a cell at the cap
 // is then a leaf whatever it holds, and SF_DEPTH says so.
+#include <cooperative_groups.h>
+
 #include "ng_internal.cuh"
 
 namespace ng {
@@ -76,12 +78,17 @@ __device__ __forceinline__ OctTeam octant_team(const uint64_t* __restrict__ keys
   return t;
 }
 
-// lmax: the deepest level the build emits (kMaxLevel unless capped); nodes
-// of level lmax are leaves, and one above the leaf size raises SF_DEPTH.
-__global__ void k_tree_count(int lvl, int lmax, uint32_t* status, int64_t cap, int leaf_size,
-                             const uint64_t* __restrict__ keys, const uint32_t* __restrict__ first,
-                             const uint32_t* __restrict__ count, uint8_t* nchild,
-                             uint32_t* child, uint32_t* tmp) {
+// Count phase of level lvl: each team of 8 lanes (team of teams, warps'
+// teams looping together) takes nodes of the level and records their child
+// counts in nchild and tmp. lmax: the deepest level the build emits
+// (kMaxLevel unless capped); nodes of level lmax are leaves, and one above
+// the leaf size raises SF_DEPTH.
+__device__ __forceinline__ void tree_count_nodes(int lvl, int lmax, uint32_t* status, int64_t cap,
+                                                 int leaf_size, const uint64_t* __restrict__ keys,
+                                                 const uint32_t* __restrict__ first,
+                                                 const uint32_t* __restrict__ count,
+                                                 uint8_t* nchild, uint32_t* child, uint32_t* tmp,
+                                                 int64_t team, int64_t teams) {
   Levels lv = levels_of(status);
   const uint32_t s = lv.start[lvl];
   uint32_t e = lv.start[lvl + 1];
@@ -89,8 +96,6 @@ __global__ void k_tree_count(int lvl, int lmax, uint32_t* status, int64_t cap, i
   const int nodes = e > s ? (int)(e - s) : 0;
   const int shift = 3 * (kMaxLevel - (lvl + 1));
   const int lane = threadIdx.x & 31, sub = lane & 7;
-  const int64_t team = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 3;
-  const int64_t teams = ((int64_t)gridDim.x * blockDim.x) >> 3;   // a multiple of 4
   for (int64_t base = team & ~(int64_t)3; base < nodes; base += teams) {
     const int64_t j = base + (team & 3);
     const bool valid = j < nodes;
@@ -110,31 +115,35 @@ __global__ void k_tree_count(int lvl, int lmax, uint32_t* status, int64_t cap, i
   }
 }
 
-__global__ void k_tree_emit(int lvl, uint32_t* status, int64_t cap,
-                            const uint64_t* __restrict__ keys, uint8_t* level, uint64_t* prefix,
-                            uint32_t* first, uint32_t* count, const uint8_t* __restrict__ nchild,
-                            uint32_t* child, const uint32_t* __restrict__ off) {
+// The start of level lvl + 2 from the child total of level lvl (one thread);
+// a node count beyond the capacity raises SF_NODE_OVERFLOW.
+__device__ __forceinline__ void tree_level_close(int lvl, uint32_t* status, int64_t cap) {
+  Levels lv = levels_of(status);
+  const uint64_t end = (uint64_t)lv.start[lvl + 1] + lv.count[lvl + 1];
+  lv.start[lvl + 2] = (uint32_t)(end < 0xffffffffull ? end : 0xffffffffull);
+  // only levels up to the first overflow are counted correctly: the node
+  // estimate is taken there and never from the truncated levels below it
+  if (!(status[ST_FLAGS] & SF_NODE_OVERFLOW)) {
+    status[ST_NODES_NEEDED] = (uint32_t)(end < 0xffffffffull ? end : 0xffffffffull);
+    if (end > (uint64_t)cap) status[ST_FLAGS] |= (uint32_t)SF_NODE_OVERFLOW;
+  }
+}
+
+// Emit phase of level lvl: the children of each split node, numbered from the
+// level's end (next0) by the exclusive scan of the child counts (off).
+__device__ __forceinline__ void tree_emit_nodes(int lvl, uint32_t next0, uint32_t* status, int64_t cap,
+                                                const uint64_t* __restrict__ keys, uint8_t* level,
+                                                uint64_t* prefix, uint32_t* first, uint32_t* count,
+                                                const uint8_t* __restrict__ nchild, uint32_t* child,
+                                                const uint32_t* __restrict__ off, int64_t team,
+                                                int64_t teams) {
   Levels lv = levels_of(status);
   const uint32_t s = lv.start[lvl];
-  uint32_t e = lv.start[lvl + 1];
+  uint32_t e = next0;
   if (e > cap) e = (uint32_t)cap;
-  const uint32_t next0 = lv.start[lvl + 1];
-  const uint32_t total = lv.count[lvl + 1];
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    const uint64_t end = (uint64_t)next0 + total;
-    lv.start[lvl + 2] = (uint32_t)(end < 0xffffffffull ? end : 0xffffffffull);
-    // only levels up to the first overflow are counted correctly: the node
-    // estimate is taken there and never from the truncated levels below it
-    if (!(status[ST_FLAGS] & SF_NODE_OVERFLOW)) {
-      status[ST_NODES_NEEDED] = (uint32_t)(end < 0xffffffffull ? end : 0xffffffffull);
-      if (end > (uint64_t)cap) status[ST_FLAGS] |= (uint32_t)SF_NODE_OVERFLOW;
-    }
-  }
   const int nodes = e > s ? (int)(e - s) : 0;
   const int shift = 3 * (kMaxLevel - (lvl + 1));
   const int lane = threadIdx.x & 31, sub = lane & 7;
-  const int64_t team = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 3;
-  const int64_t teams = ((int64_t)gridDim.x * blockDim.x) >> 3;
   for (int64_t base = team & ~(int64_t)3; base < nodes; base += teams) {
     const int64_t j = base + (team & 3);
     const bool valid = j < nodes;
@@ -158,6 +167,104 @@ __global__ void k_tree_emit(int lvl, uint32_t* status, int64_t cap,
         count[id] = t.end - t.start;
       }
     }
+  }
+}
+
+__global__ void k_tree_count(int lvl, int lmax, uint32_t* status, int64_t cap, int leaf_size,
+                             const uint64_t* __restrict__ keys, const uint32_t* __restrict__ first,
+                             const uint32_t* __restrict__ count, uint8_t* nchild,
+                             uint32_t* child, uint32_t* tmp) {
+  const int64_t team = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 3;
+  const int64_t teams = ((int64_t)gridDim.x * blockDim.x) >> 3;   // a multiple of 4
+  tree_count_nodes(lvl, lmax, status, cap, leaf_size, keys, first, count, nchild, child, tmp, team,
+                   teams);
+}
+
+__global__ void k_tree_emit(int lvl, uint32_t* status, int64_t cap,
+                            const uint64_t* __restrict__ keys, uint8_t* level, uint64_t* prefix,
+                            uint32_t* first, uint32_t* count, const uint8_t* __restrict__ nchild,
+                            uint32_t* child, const uint32_t* __restrict__ off) {
+  const uint32_t next0 = levels_of(status).start[lvl + 1];
+  if (blockIdx.x == 0 && threadIdx.x == 0) tree_level_close(lvl, status, cap);
+  const int64_t team = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 3;
+  const int64_t teams = ((int64_t)gridDim.x * blockDim.x) >> 3;
+  tree_emit_nodes(lvl, next0, status, cap, keys, level, prefix, first, count, nchild, child, off,
+                  team, teams);
+}
+
+// The whole build of a small tree in one launch: one cluster of
+// kClusterBlocks blocks (co-scheduled; its barrier is the hardware cluster
+// barrier, so no block waits on a flag) runs every level's count, scan and
+// emit phases, each the same code as the per-level kernels, with a cluster
+// barrier between phases. The child-count scan of a level: each block sums
+// its contiguous chunk, the sums go to every block's shared memory, and
+// each block scans its chunk from the sum of the chunks before it.
+__global__ void __cluster_dims__(kClusterBlocks, 1, 1) __launch_bounds__(1024, 1)
+k_tree_cluster(int lmax, uint32_t* status, int64_t n, int64_t cap, int leaf_size,
+               const uint64_t* __restrict__ keys, uint8_t* level, uint64_t* prefix, uint32_t* first,
+               uint32_t* count, uint8_t* nchild, uint32_t* child, uint32_t* tmp) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  __shared__ uint32_t sums[kClusterBlocks];
+  __shared__ uint32_t warp_tot[32];
+  __shared__ uint32_t tile_total;
+  const int tid = threadIdx.x, nb = (int)gridDim.x, b = (int)blockIdx.x;
+  Levels lv = levels_of(status);
+  if (b == 0 && tid == 0) {
+    for (int l = 0; l <= kMaxLevel + 1; ++l) lv.start[l] = 1;
+    for (int l = 0; l <= kMaxLevel; ++l) lv.count[l] = 0;
+    lv.start[0] = 0;
+    lv.start[1] = 1;
+    lv.count[0] = 1;
+    status[ST_NODES_NEEDED] = 1;
+    status[ST_NGROUPS] = 0;
+    level[0] = 0;
+    prefix[0] = 0;
+    first[0] = 0;
+    count[0] = (uint32_t)n;
+  }
+  cluster.sync();
+  const int64_t team = ((int64_t)b * blockDim.x + tid) >> 3;
+  const int64_t teams = ((int64_t)nb * blockDim.x) >> 3;
+  for (int l = 0; l <= lmax; ++l) {
+    tree_count_nodes(l, lmax, status, cap, leaf_size, keys, first, count, nchild, child, tmp, team,
+                     teams);
+    cluster.sync();
+    if (l == lmax) break;
+    // exclusive scan of the level's child counts (tmp, in place)
+    const uint32_t s = lv.start[l];
+    uint32_t e = lv.start[l + 1];
+    if (e > cap) e = (uint32_t)cap;
+    const int nodes = e > s ? (int)(e - s) : 0;
+    const int chunk = (nodes + nb - 1) / nb;
+    const int c0 = min(nodes, b * chunk), c1 = min(nodes, c0 + chunk);
+    uint32_t part = 0;
+    for (int i = c0 + tid; i < c1; i += blockDim.x) part += tmp[i];
+    block_inclusive_scan<1024>(part, warp_tot, &tile_total);
+    if (tid < nb) *cluster.map_shared_rank(&sums[b], tid) = tile_total;
+    cluster.sync();
+    uint32_t carry = 0;
+    for (int r = 0; r < b; ++r) carry += sums[r];
+    for (int base = c0; base < c1; base += blockDim.x) {
+      const int i = base + tid;
+      const uint32_t v = i < c1 ? tmp[i] : 0u;
+      const uint32_t inc = block_inclusive_scan<1024>(v, warp_tot, &tile_total);
+      if (i < c1) tmp[i] = carry + inc - v;
+      __syncthreads();
+      carry += tile_total;
+      __syncthreads();
+    }
+    if (b == nb - 1 && tid == 0) lv.count[l + 1] = carry;
+    cluster.sync();
+    const uint32_t next0 = lv.start[l + 1];
+    if (b == 0 && tid == 0) tree_level_close(l, status, cap);
+    tree_emit_nodes(l, next0, status, cap, keys, level, prefix, first, count, nchild, child, tmp,
+                    team, teams);
+    cluster.sync();
+  }
+  if (lmax < kMaxLevel && b == 0 && tid == 0) {
+    const uint32_t end = lv.start[lmax + 1];
+    for (int l = lmax + 2; l <= kMaxLevel + 1; ++l) lv.start[l] = end;
   }
 }
 
@@ -187,6 +294,13 @@ int build_octree(ng_ctx* c) {
   const int leaf = c->p.leaf_size;
   const int lmax = std::min(std::max(c->level_cap, 0), kMaxLevel);
   stage_mark(c, NG_STAGE_OCTREE);
+  if (n <= kClusterMaxBodies) {
+    k_tree_cluster<<<kClusterBlocks, 1024, 0, c->stream>>>(lmax, st, n, cap, leaf, keys, level,
+                                                          prefix, first, count, nchild, child, tmp);
+    c->launches += 1;
+    NG_CUDA(c, cudaGetLastError());
+    return NG_OK;
+  }
   k_tree_init<<<1, 32, 0, c->stream>>>(st, n, level, prefix, first, count);
   c->launches += 1 + (lmax + 1) + lmax;   // init, counts, emits (scans count themselves)
   for (int l = 0; l <= lmax; ++l) {
@@ -254,101 +368,128 @@ struct MonoArgs {
 // by M in FP32.
 constexpr int kMonoThreads = 128;
 
+// Sums of node k of level lvl (leaf: its bodies; internal node: its <= 8
+// children) into the node's FP64 monopoles and FP32 walk records. lacc: the
+// calling thread's per-species leaf sums {m, m x, m y, m z} (physical units),
+// addressed by the body's species: no FP64 instruction is spent on the
+// species a body does not have (predicated per-species sums would issue D
+// times as many, and FP64 issues at 1/64 of the FP32 rate here).
+template <int D>
+__device__ __forceinline__ void mono_node(int lvl, uint32_t k, const MonoArgs& a,
+                                          double (*lacc)[4][kMonoThreads], int tid) {
+  double cen[3], side;
+  node_centre(lvl, a.prefix[k], cen, &side);
+  double sm[D], sx[D], sy[D], sz[D];
+  uint32_t sc[D];
+#pragma unroll
+  for (int t = 0; t < D; ++t) { sm[t] = sx[t] = sy[t] = sz[t] = 0.0; sc[t] = 0; }
+  const uint32_t nch = a.nchild[k];
+  const uint32_t f = a.first[k], c = a.count[k];
+  if (nch == 0) {
+#pragma unroll
+    for (int q = 0; q < D; ++q)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) lacc[q][j][tid] = 0.0;
+    // leaf centre in physical units; body records are offsets from it in box units
+    const double cxL = cen[0] * a.L, cyL = cen[1] * a.L, czL = cen[2] * a.L;
+    const float invLf = (float)a.invL;
+    for (uint32_t b = f; b < f + c; ++b) {
+      const double xp = a.spos[b], yp = a.spos[a.n + b], zp = a.spos[2 * a.n + b];
+      const float m = a.smass[b];
+      const int t = a.stype[b];
+      a.body[b] = make_float4((float)(xp - cxL) * invLf, (float)(yp - cyL) * invLf,
+                              (float)(zp - czL) * invLf, m);
+      a.bleaf[b] = k;
+      const double md = (double)m;
+      lacc[t][0][tid] += md;
+      lacc[t][1][tid] = fma(md, xp, lacc[t][1][tid]);
+      lacc[t][2][tid] = fma(md, yp, lacc[t][2][tid]);
+      lacc[t][3][tid] = fma(md, zp, lacc[t][3][tid]);
+#pragma unroll
+      for (int q = 0; q < D; ++q) sc[q] += t == q ? 1u : 0u;
+    }
+    // to box units (exact when the box is a power of two)
+#pragma unroll
+    for (int q = 0; q < D; ++q) {
+      sm[q] = lacc[q][0][tid];
+      sx[q] = lacc[q][1][tid] * a.invL;
+      sy[q] = lacc[q][2][tid] * a.invL;
+      sz[q] = lacc[q][3][tid] * a.invL;
+    }
+  } else {
+    const uint32_t c0 = a.child[k];
+    for (uint32_t j = 0; j < nch; ++j) {
+      const uint32_t ch = c0 + j;
+#pragma unroll
+      for (int q = 0; q < D; ++q) {
+        const double4 v = *reinterpret_cast<const double4*>(a.m64 + ((size_t)ch * D + q) * 4);
+        sm[q] += v.x;
+        sx[q] += v.y;
+        sy[q] += v.z;
+        sz[q] += v.w;
+        sc[q] += a.cnt[(size_t)ch * D + q];
+      }
+    }
+  }
+  double mt = 0, xt = 0, yt = 0, zt = 0;
+#pragma unroll
+  for (int q = 0; q < D; ++q) {
+    *reinterpret_cast<double4*>(a.m64 + ((size_t)k * D + q) * 4) = make_double4(sm[q], sx[q], sy[q], sz[q]);
+    a.cnt[(size_t)k * D + q] = sc[q];
+    float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (sm[q] > 0.0) {
+      const float im = 1.0f / (float)sm[q];
+      r = make_float4((float)fma(-sm[q], cen[0], sx[q]) * im, (float)fma(-sm[q], cen[1], sy[q]) * im,
+                      (float)fma(-sm[q], cen[2], sz[q]) * im, (float)sm[q]);
+    }
+    a.mono[(size_t)k * D + q] = r;
+    mt += sm[q];
+    xt += sx[q];
+    yt += sy[q];
+    zt += sz[q];
+  }
+  a.geo[k] = make_float4((float)cen[0], (float)cen[1], (float)cen[2], (float)(0.5 * side));
+  float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (mt > 0.0) {
+    const float im = 1.0f / (float)mt;
+    r = make_float4((float)fma(-mt, cen[0], xt) * im, (float)fma(-mt, cen[1], yt) * im,
+                    (float)fma(-mt, cen[2], zt) * im, (float)mt);
+  }
+  a.com[k] = r;
+  a.link[k] = make_int4(nch ? (int)a.child[k] : -1, (int)nch, (int)f, (int)c);
+}
+
 template <int D>
 __global__ void __launch_bounds__(kMonoThreads) k_monopoles(int lvl, MonoArgs a) {
-  // per-thread leaf sums per species {m, m x, m y, m z} (physical units),
-  // addressed by the body's species: no FP64 instruction is spent on the
-  // species a body does not have (predicated per-species sums would issue D
-  // times as many, and FP64 issues at 1/64 of the FP32 rate here)
   __shared__ double lacc[D][4][kMonoThreads];
   if (a.status[ST_FLAGS] & SF_NODE_OVERFLOW) return;   // truncated tree: do not read it
-  const int tid = threadIdx.x;
   Levels lv = levels_of(a.status);
   const uint32_t s = lv.start[lvl];
   uint32_t e = lv.start[lvl + 1];
   if (e > a.cap) e = (uint32_t)a.cap;
-  for (uint32_t k = s + blockIdx.x * blockDim.x + threadIdx.x; k < e;
-       k += gridDim.x * blockDim.x) {
-    double cen[3], side;
-    node_centre(lvl, a.prefix[k], cen, &side);
-    double sm[D], sx[D], sy[D], sz[D];
-    uint32_t sc[D];
-#pragma unroll
-    for (int t = 0; t < D; ++t) { sm[t] = sx[t] = sy[t] = sz[t] = 0.0; sc[t] = 0; }
-    const uint32_t nch = a.nchild[k];
-    const uint32_t f = a.first[k], c = a.count[k];
-    if (nch == 0) {
-#pragma unroll
-      for (int q = 0; q < D; ++q)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) lacc[q][j][tid] = 0.0;
-      // leaf centre in physical units; body records are offsets from it in box units
-      const double cxL = cen[0] * a.L, cyL = cen[1] * a.L, czL = cen[2] * a.L;
-      const float invLf = (float)a.invL;
-      for (uint32_t b = f; b < f + c; ++b) {
-        const double xp = a.spos[b], yp = a.spos[a.n + b], zp = a.spos[2 * a.n + b];
-        const float m = a.smass[b];
-        const int t = a.stype[b];
-        a.body[b] = make_float4((float)(xp - cxL) * invLf, (float)(yp - cyL) * invLf,
-                                (float)(zp - czL) * invLf, m);
-        a.bleaf[b] = k;
-        const double md = (double)m;
-        lacc[t][0][tid] += md;
-        lacc[t][1][tid] = fma(md, xp, lacc[t][1][tid]);
-        lacc[t][2][tid] = fma(md, yp, lacc[t][2][tid]);
-        lacc[t][3][tid] = fma(md, zp, lacc[t][3][tid]);
-#pragma unroll
-        for (int q = 0; q < D; ++q) sc[q] += t == q ? 1u : 0u;
-      }
-      // to box units (exact when the box is a power of two)
-#pragma unroll
-      for (int q = 0; q < D; ++q) {
-        sm[q] = lacc[q][0][tid];
-        sx[q] = lacc[q][1][tid] * a.invL;
-        sy[q] = lacc[q][2][tid] * a.invL;
-        sz[q] = lacc[q][3][tid] * a.invL;
-      }
-    } else {
-      const uint32_t c0 = a.child[k];
-      for (uint32_t j = 0; j < nch; ++j) {
-        const uint32_t ch = c0 + j;
-#pragma unroll
-        for (int q = 0; q < D; ++q) {
-          const double4 v = *reinterpret_cast<const double4*>(a.m64 + ((size_t)ch * D + q) * 4);
-          sm[q] += v.x;
-          sx[q] += v.y;
-          sy[q] += v.z;
-          sz[q] += v.w;
-          sc[q] += a.cnt[(size_t)ch * D + q];
-        }
-      }
-    }
-    double mt = 0, xt = 0, yt = 0, zt = 0;
-#pragma unroll
-    for (int q = 0; q < D; ++q) {
-      *reinterpret_cast<double4*>(a.m64 + ((size_t)k * D + q) * 4) = make_double4(sm[q], sx[q], sy[q], sz[q]);
-      a.cnt[(size_t)k * D + q] = sc[q];
-      float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (sm[q] > 0.0) {
-        const float im = 1.0f / (float)sm[q];
-        r = make_float4((float)fma(-sm[q], cen[0], sx[q]) * im, (float)fma(-sm[q], cen[1], sy[q]) * im,
-                        (float)fma(-sm[q], cen[2], sz[q]) * im, (float)sm[q]);
-      }
-      a.mono[(size_t)k * D + q] = r;
-      mt += sm[q];
-      xt += sx[q];
-      yt += sy[q];
-      zt += sz[q];
-    }
-    a.geo[k] = make_float4((float)cen[0], (float)cen[1], (float)cen[2], (float)(0.5 * side));
-    float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (mt > 0.0) {
-      const float im = 1.0f / (float)mt;
-      r = make_float4((float)fma(-mt, cen[0], xt) * im, (float)fma(-mt, cen[1], yt) * im,
-                      (float)fma(-mt, cen[2], zt) * im, (float)mt);
-    }
-    a.com[k] = r;
-    a.link[k] = make_int4(nch ? (int)a.child[k] : -1, (int)nch, (int)f, (int)c);
+  for (uint32_t k = s + blockIdx.x * blockDim.x + threadIdx.x; k < e; k += gridDim.x * blockDim.x)
+    mono_node<D>(lvl, k, a, lacc, threadIdx.x);
+}
+
+// Every level of a small tree, bottom-up, in one launch: one cluster of
+// kClusterBlocks blocks with the hardware cluster barrier between levels.
+template <int D>
+__global__ void __cluster_dims__(kClusterBlocks, 1, 1) __launch_bounds__(kMonoThreads)
+k_monopoles_cluster(int lmax, MonoArgs a) {
+  __shared__ double lacc[D][4][kMonoThreads];
+  // the flag is read before any level and never written here: every block
+  // returns, or none does
+  if (a.status[ST_FLAGS] & SF_NODE_OVERFLOW) return;
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  Levels lv = levels_of(a.status);
+  for (int l = lmax; l >= 0; --l) {
+    const uint32_t s = lv.start[l];
+    uint32_t e = lv.start[l + 1];
+    if (e > a.cap) e = (uint32_t)a.cap;
+    for (uint32_t k = s + blockIdx.x * blockDim.x + threadIdx.x; k < e; k += gridDim.x * blockDim.x)
+      mono_node<D>(l, k, a, lacc, threadIdx.x);
+    cluster.sync();
   }
 }
 
@@ -377,8 +518,21 @@ int reduce_monopoles(ng_ctx* c) {
   a.invL = 1.0 / c->L;
   a.L = c->L;
   const int lmax = std::min(std::max(c->level_cap, 0), kMaxLevel);   // deeper levels are empty
-  c->launches += lmax + 1;
   stage_mark(c, NG_STAGE_MONOPOLES);
+  if (c->n <= kClusterMaxBodies) {
+    switch (c->p.D) {
+      case 1: k_monopoles_cluster<1><<<kClusterBlocks, kMonoThreads, 0, c->stream>>>(lmax, a); break;
+      case 2: k_monopoles_cluster<2><<<kClusterBlocks, kMonoThreads, 0, c->stream>>>(lmax, a); break;
+      case 3: k_monopoles_cluster<3><<<kClusterBlocks, kMonoThreads, 0, c->stream>>>(lmax, a); break;
+      case 4: k_monopoles_cluster<4><<<kClusterBlocks, kMonoThreads, 0, c->stream>>>(lmax, a); break;
+      case 5: k_monopoles_cluster<5><<<kClusterBlocks, kMonoThreads, 0, c->stream>>>(lmax, a); break;
+      default: k_monopoles_cluster<6><<<kClusterBlocks, kMonoThreads, 0, c->stream>>>(lmax, a); break;
+    }
+    c->launches += 1;
+    NG_CUDA(c, cudaGetLastError());
+    return NG_OK;
+  }
+  c->launches += lmax + 1;
   for (int l = lmax; l >= 0; --l) {
     const int64_t nodes = std::min<int64_t>(c->cap_nodes, level_bound(l, c->n));
     const int grid = (int)std::max<int64_t>(
