@@ -5,11 +5,12 @@
 // Each simulation's sort, tree and PM stages run on one of several worker
 // streams (fork/join inside one captured CUDA graph, so small simulations
 // overlap on the device); the short-range walk of all simulations that share
-// one law table (laid out for 6 species; simulations of any species count
-// whose laws agree on their species pairs share it) is ONE persistent launch
-// whose warps pull (simulation, group) items from a single work queue; the
-// closing kick runs per simulation. The step is captured once and replayed.
+// one law table (one row per distinct law of its members, whatever their
+// species counts) is ONE persistent launch whose warps pull (simulation,
+// group) items from a single work queue; the closing kick runs per
+// simulation. The step is captured once and replayed.
 #include <algorithm>
+#include <array>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -24,8 +25,10 @@ struct WalkClass {
   std::vector<int> members;          // simulation indices
   std::vector<WalkDesc> h;           // host descriptors (kept alive for the graph)
   DevBuf d, pre;                     // device descriptors, group prefix + work counter
-  // the class's law table, laid out for kMaxD lists (variable-D launches)
-  std::vector<float> htab;
+  // the class's law table: one row of ncut + 1 segments per distinct law of
+  // its members (each member's descriptor maps its species pairs to rows)
+  std::vector<std::vector<float>> laws;
+  std::vector<float> htab;           // the rows, concatenated (uploaded to tab)
   int ncut = 0;
   double dr = 0;
   DevBuf tab;
@@ -39,6 +42,7 @@ struct ng_batch {
   std::vector<cudaEvent_t> joins;
   cudaEvent_t fork = nullptr;
   std::vector<WalkClass> classes;
+  std::vector<std::array<int8_t, kMaxD * kMaxD>> lawmap;   // per simulation: row of pair (s, t)
   cudaGraphExec_t exec = nullptr;
   std::vector<const void*> sig;      // pointers, sizes and dt the graph was captured for
   uint64_t gen = 0;
@@ -70,22 +74,42 @@ int from_sim(ng_batch* b, int i, int code) {
   return bfail(b, code, "simulation %d: %s", i, ng_last_error(b->sims[i]));
 }
 
-// A simulation can join a walk class when the class's table (laid out for
-// kMaxD lists) holds its laws on its own D x D block and the table spacing,
-// cut-off and accumulation agree; the first member, of the largest species
-// count, defines the table.
-bool fits_class(const WalkClass& k, const ng_ctx* rep, const ng_ctx* c,
-                const std::vector<float>& h, int ncut, double dr) {
-  if (c->p.accumulate_fp64 != rep->p.accumulate_fp64 || c->rcut != rep->rcut ||
-      ncut != k.ncut || dr != k.dr || h.size() != k.htab.size())
+// Segments per law of a batch class table (the accuracy of a D = 4 table),
+// fewer when the first member's laws would not fit the table budget.
+constexpr int kBatchSegments = 511;
+constexpr size_t kClassTableBytes = 64 * 1024;
+
+// A simulation joins a walk class when the cut-off, accumulation and segment
+// spacing agree and the class table, with the member's laws not yet in it
+// appended, stays within the budget; map receives the rows of the member's
+// species pairs.
+bool join_class(WalkClass& k, const ng_ctx* rep, const ng_ctx* c, int ncut, double dr,
+                const std::vector<float>& rows, std::array<int8_t, kMaxD * kMaxD>& map) {
+  if (c->p.accumulate_fp64 != rep->p.accumulate_fp64 || c->rcut != rep->rcut || ncut != k.ncut ||
+      dr != k.dr || (c->p.table_size > 0 && c->p.table_size != ncut))
     return false;
-  const int D = c->p.D, pad = walk_tab_pad(kMaxD);
-  for (int t = 0; t < D; ++t)
-    for (int r = 0; r <= ncut; ++r)
-      for (int sp = 0; sp < D; ++sp) {
-        const size_t o = (((size_t)t * (ncut + 1) + r) * pad + sp) * 2;
-        if (h[o] != k.htab[o] || h[o + 1] != k.htab[o + 1]) return false;
-      }
+  const size_t row = (size_t)(ncut + 1) * 2;
+  std::vector<int> id(c->nlaws, -1);
+  size_t added = 0;
+  for (int u = 0; u < c->nlaws; ++u) {
+    const float* r = rows.data() + (size_t)u * row;
+    for (size_t v = 0; v < k.laws.size() && id[u] < 0; ++v)
+      if (std::equal(r, r + row, k.laws[v].data())) id[u] = (int)v;
+    if (id[u] < 0) ++added;
+  }
+  if ((k.laws.size() + added) * row * sizeof(float) > kClassTableBytes && !k.laws.empty()) return false;
+  for (int u = 0; u < c->nlaws; ++u) {
+    if (id[u] >= 0) continue;
+    const float* r = rows.data() + (size_t)u * row;
+    id[u] = (int)k.laws.size();
+    k.laws.emplace_back(r, r + row);
+    // a law repeated within this member maps to the row just added
+    for (int w = u + 1; w < c->nlaws; ++w)
+      if (id[w] < 0 && std::equal(r, r + row, rows.data() + (size_t)w * row)) id[w] = id[u];
+  }
+  map.fill(0);
+  for (int s = 0; s < c->p.D; ++s)
+    for (int t = 0; t < c->p.D; ++t) map[s * kMaxD + t] = (int8_t)id[c->tabid[s][t]];
   return true;
 }
 
@@ -142,31 +166,35 @@ int ng_batch_create(ng_batch** out, int nsim, const ng_params* params, void* str
   for (int i = 0; i < nsim; ++i) order[i] = i;
   std::stable_sort(order.begin(), order.end(),
                    [&](int x, int y) { return b->sims[x]->p.D > b->sims[y]->p.D; });
+  b->lawmap.resize(nsim);
   for (int i : order) {
     ng_ctx* c = b->sims[i];
-    const int ncut = walk_table_entries(kMaxD, c->p.table_size);
-    const double dr = c->rcut / (ncut - 0.5);
-    std::vector<float> h = walk_table(c, kMaxD, ncut, dr);
     bool placed = false;
     for (WalkClass& k : b->classes) {
-      if (fits_class(k, b->sims[k.members[0]], c, h, ncut, dr)) {
+      const std::vector<float> rows = law_segments(c, k.ncut, k.dr);
+      if (join_class(k, b->sims[k.members[0]], c, k.ncut, k.dr, rows, b->lawmap[i])) {
         k.members.push_back(i);
         placed = true;
         break;
       }
     }
     if (!placed) {
+      // a new class, its segment count set by its first member's laws
+      int ncut = c->p.table_size > 0 ? c->p.table_size : kBatchSegments;
+      if (c->p.table_size <= 0)
+        ncut = (int)std::min<size_t>(ncut, kClassTableBytes / (8 * (size_t)c->nlaws) - 1);
       b->classes.emplace_back();
       WalkClass& k = b->classes.back();
       k.D = c->p.D;
-      k.members.push_back(i);
-      k.htab = std::move(h);
       k.ncut = ncut;
-      k.dr = dr;
+      k.dr = c->rcut / (ncut - 0.5);
+      k.members.push_back(i);
+      join_class(k, c, c, k.ncut, k.dr, law_segments(c, k.ncut, k.dr), b->lawmap[i]);
     }
   }
   for (WalkClass& k : b->classes) {
     std::sort(k.members.begin(), k.members.end());
+    for (const std::vector<float>& r : k.laws) k.htab.insert(k.htab.end(), r.begin(), r.end());
     ng_ctx* rep = b->sims[k.members[0]];
     int r = ensure(rep, k.tab, k.htab.size() * sizeof(float));
     if (r == NG_OK &&
@@ -348,6 +376,9 @@ int ng_batch_step(ng_batch* b, const int64_t* n, double* const* pos, float* cons
       for (size_t j = 0; j < k.members.size(); ++j) {
         ng_ctx* c = b->sims[k.members[j]];
         fill_walk_desc_dr(c, acc[k.members[j]], c->p.pm_mesh > 0, k.dr, &k.h[j]);
+        const std::array<int8_t, kMaxD * kMaxD>& m = b->lawmap[k.members[j]];
+        for (int ss = 0; ss < kMaxD; ++ss)
+          for (int tt = 0; tt < kMaxD; ++tt) k.h[j].tabid[ss][tt] = m[ss * kMaxD + tt];
       }
       ng_ctx* rep = b->sims[k.members[0]];
       int r = ensure(rep, k.d, k.h.size() * sizeof(WalkDesc));

@@ -154,18 +154,23 @@ __device__ __forceinline__ uint64_t sort_key(double x, double y, double z, uint8
 // type offsets read back from the last pass's) are laid out by it.
 constexpr int kRadixTile = 2048;
 
-// Entries per row of the walk's law table: the passive species count rounded
-// up to a power of two (a row of the table of list species t holds the law of
-// every passive species s; see build_tables).
+// Entries per row of a single simulation's law table: the passive species
+// count rounded up to a power of two (a row of the table of list species t
+// holds the law of every passive species s; see walk_table).
 __host__ __device__ constexpr int walk_tab_pad(int D) { return D <= 1 ? 1 : D == 2 ? 2 : D <= 4 ? 4 : 8; }
 __host__ __device__ constexpr int walk_tab_shift(int D) { return D <= 1 ? 0 : D == 2 ? 1 : D <= 4 ? 2 : 3; }
 
+// Warps per walk block (one block per SM): registers and the per-warp lists
+// bound them. The variable-species instance of batches, laid out for six
+// species, runs 24 warps when its law table is small (a few distinct laws).
 __host__ __device__ constexpr int walk_warps(int D) { return D <= 3 ? 24 : D == 4 ? 24 : D == 5 ? 20 : 16; }
+constexpr int kVardWarps = 24;
 
 // Per-simulation inputs of the walk (device memory, one per simulation).
 // The law table of a walk launch (device copy).
+// (batch classes: one row of segments per distinct law of the members)
 struct WalkTable {
-  const float2* tab;        // [list species t][ncut + 1][walk_tab_pad(D)]
+  const float2* tab;        // [law][ncut + 1] segments {c0 - k c1, c1}
   int ncut;
   int count;                // float2 entries
 };
@@ -204,7 +209,10 @@ struct WalkLaunch {
   int ndesc;
   const uint32_t* gprefix;  // [ndesc + 1] group prefix
   uint32_t* work;           // work-queue counter
-  const float2* tab;        // [list species t][ncut + 1][walk_tab_pad(D)] segment {c0, c1}
+  // law table, segments {c0 - k c1, c1}: single simulations
+  // [list species t][ncut + 1][walk_tab_pad(D)] (entry s: passive species s);
+  // variable-species launches [law][ncut + 1] (a lane's row: tabid[s][t])
+  const float2* tab;
   int tab_entries;          // ncut + 1
   int ncut;
   int tab_count;            // float2 entries of the whole table
@@ -392,10 +400,13 @@ int type_order(ng_ctx* c);
 
 // Host short-range law tables (double precision closed forms).
 int build_tables(ng_ctx* c);
-// The walk's law table of a context laid out for Dl >= D lists (rows of
-// walk_tab_pad(Dl) entries; pairs outside D x D zero), ncut segments of dr.
-std::vector<float> walk_table(const ng_ctx* c, int Dl, int ncut, double dr);
-int walk_table_entries(int Dl, int table_size);   // default segment count for Dl lists
+// The linear segments of a context's distinct laws, [law][ncut + 1] float2
+// (c->tabid numbers the laws), ncut segments of dr.
+std::vector<float> law_segments(const ng_ctx* c, int ncut, double dr);
+// The same segments laid out for the walk of a single simulation:
+// [list species t][ncut + 1][walk_tab_pad(D)], entry s the law of (s, t).
+std::vector<float> walk_table(const ng_ctx* c, int ncut, double dr);
+int walk_table_entries(int D, int table_size);   // default segments per law for D species
 
 // Short-range force factor T(rho) of Sec. 2.4.1 in FP64: the acceleration from
 // a source of active mass M is G M T(rho) d / rho^3. Newtonian part:

@@ -19,9 +19,10 @@
 //
 // Inner loop per (body, record): q = |d|^2 + eps^2, inv = rsqrt(q); the
 // table index k = rint(rho), rho = q * inv, is read from the float bits of
-// q*inv + 2^23; the table holds one linear segment per index, stored as
-// {c0 - k c1, c1} so that its value is (c0 - k c1) + rho c1 (zero past the
-// cut-off); the force is m * value * inv^3 * d, summed over one species list;
+// q*inv + 2^23; the table holds linear segments per law (laid out per list
+// species with one entry per passive species; in variable-species launches
+// one row per distinct law), stored as {c0 - k c1, c1} so that its value is
+// (c0 - k c1) + rho c1 (zero past the cut-off); the force is m * value * inv^3 * d, summed over one species list;
 // each list's sum is scaled by the coupling G[s][t] of the body's species s
 // and the list's species t and added to one accumulator per body.
 #include <type_traits>
@@ -88,7 +89,7 @@ __device__ __forceinline__ float2 lds_f2(uint32_t addr) {
 // is then the largest (lists for D species, the law table laid out for D),
 // and each work item uses its simulation's own count DESC(D) <= D.
 template <int D, bool ACC64, bool REL, bool VARD>
-__global__ void __launch_bounds__(walk_warps(D) * 32, 1) k_walk(WalkLaunch L) {
+__global__ void __launch_bounds__((VARD ? kVardWarps : walk_warps(D)) * 32, 1) k_walk(WalkLaunch L) {
   using Acc = typename std::conditional<ACC64, double, float>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2* tab = reinterpret_cast<float2*>(smem_raw);
@@ -207,13 +208,15 @@ __global__ void __launch_bounds__(walk_warps(D) * 32, 1) k_walk(WalkLaunch L) {
 #pragma unroll
         for (int q = 0; q < D; ++q) cnt = (q == t) ? lc[q] : cnt;
         {
-          // shared address of segment k for passive species s is
-          // tb + 8 pad * (float bits of k + 2^23), mod 2^32, so the index
-          // needs no subtraction
-          constexpr int kRowShift = 3 + walk_tab_shift(D);
+          // shared address of segment k of this lane's law (passive s,
+          // active t) is tb + 8 pad * (float bits of k + 2^23), mod 2^32, so
+          // the index needs no subtraction (pad = 1 for the one-row-per-law
+          // table of variable-species launches)
+          constexpr int kRowShift = 3 + (VARD ? 0 : walk_tab_shift(D));
+          const float2* row = VARD ? tab + DESC(tabid)[s][t] * L.tab_entries
+                                   : tab + (t * L.tab_entries << walk_tab_shift(D)) + s;
           const uint32_t tb =
-              (uint32_t)__cvta_generic_to_shared(tab + (t * L.tab_entries << walk_tab_shift(D)) + s) -
-              ((uint32_t)kMagicBits << kRowShift);
+              (uint32_t)__cvta_generic_to_shared(row) - ((uint32_t)kMagicBits << kRowShift);
           float* lt4 = reinterpret_cast<float*>(ws->list[t]);
           // pad to an even count with a massless record (zero force); full
           // quads of records, then at most one pair
@@ -522,7 +525,7 @@ static size_t walk_smem(int tab_count, int nwarps) {
 
 template <int D, bool ACC64, bool REL, bool VARD>
 static int launch_walk_d(ng_ctx* c, cudaStream_t stream, const WalkLaunch& L, int64_t groups) {
-  int nwarps = walk_warps(D);
+  int nwarps = VARD ? kVardWarps : walk_warps(D);
   while (nwarps > 1 && walk_smem<D>(L.tab_count, nwarps) > c->smem_optin) --nwarps;
   const size_t smem = walk_smem<D>(L.tab_count, nwarps);
   if (smem > c->smem_optin)
