@@ -499,14 +499,19 @@ def bench_batch(args, ws, rank, local):
                  typ=torch.from_numpy(sp["type"]).to(dev), mass=torch.from_numpy(sp["mass"]).to(dev))
         x["acc"] = torch.zeros((3, sp["type"].size), dtype=torch.float32, device=dev)
         state.append(x)
-    # walk leaf size and group cell: tuned on the largest simulation, used by all
+    # walk leaf size and group cell: the three fastest for the largest
+    # simulation alone, then timed on batch steps of all of them
     big = max(range(len(specs)), key=lambda i: specs[i]["type"].size)
     tuned = {"leaf_size": 8, "group_cell": 32, "tuned_on_n": int(specs[big]["type"].size)}
     if not args.no_tune:
         from paper_1502_07442_gb300 import autotune
-        best, trials = autotune.tune(specs[big]["params"], state[big]["pos"], state[big]["typ"],
-                                     state[big]["mass"])
-        tuned.update(leaf_size=best["leaf_size"], group_cell=best["group_cell"], trials=len(trials))
+        _, trials = autotune.tune(specs[big]["params"], state[big]["pos"], state[big]["typ"],
+                                  state[big]["mass"])
+        short = [(t["leaf_size"], t["group_cell"]) for t in sorted(trials, key=lambda t: t["ms"])[:3]]
+        best, btrials = autotune.tune_batch([sp["params"] for sp in specs], state, short)
+        tuned.update(leaf_size=best["leaf_size"], group_cell=best["group_cell"], trials=len(trials),
+                     batch_trials={f"{t['leaf_size']}/{t['group_cell']}": round(t["ms"], 3)
+                                   for t in btrials})
     for sp in specs:
         params.append(ng.params_from_workload(sp["params"], leaf_size=tuned["leaf_size"],
                                               group_cell=tuned["group_cell"]))

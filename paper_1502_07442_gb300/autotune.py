@@ -39,3 +39,32 @@ def tune(params: dict, pos, typ, mass, leaves=LEAVES, cells=GROUP_CELLS, repeats
         sim.close()
         trials.append(dict(leaf_size=leaf, group_cell=cell, ms=best))
     return min(trials, key=lambda t: t["ms"]), trials
+
+
+def tune_batch(params_list, state, shortlist, steps: int = 3, dt: float = 1e-3, stream=None):
+    """Times batch steps (one captured graph per step, as ng_batch_step runs
+    them) for each (leaf_size, group_cell) of the shortlist, on copies of the
+    batch's arrays, and returns (best dict(leaf_size, group_cell, ms), trials).
+    A batch mixes small and large simulations, so the leaf and group sizes
+    that are fastest for its largest member alone need not be fastest for the
+    batch."""
+    import torch
+    trials = []
+    for leaf, cell in shortlist:
+        cp = [{k: v.clone() for k, v in x.items()} for x in state]
+        b = ng.ng_batch_create([ng.params_from_workload(p, leaf_size=leaf, group_cell=cell)
+                                for p in params_list], stream)
+        try:
+            arrays = [[x[k] for x in cp] for k in ("pos", "vel", "typ", "mass", "acc")]
+            ng.ng_batch_step(b, *arrays, False, 2, dt)     # sizes, captures, replays once
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            ng.ng_batch_step(b, *arrays, True, steps, dt)
+            e1.record()
+            torch.cuda.synchronize()
+            trials.append(dict(leaf_size=leaf, group_cell=cell, ms=e0.elapsed_time(e1) / steps))
+        finally:
+            ng.ng_batch_destroy(b)
+    return min(trials, key=lambda t: t["ms"]), trials
