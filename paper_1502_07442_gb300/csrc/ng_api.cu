@@ -114,12 +114,18 @@ std::vector<float> walk_table(const ng_ctx* c, int ncut, double dr) {
   return h;
 }
 
-// Segments per law: as many as 64 KB would hold for a D x D block of laws
-// (2047 for D = 2, 511 for D = 3 or 4, 169 for D = 5 or 6; at most 4096).
+// Segments per law: as many as 32 KB hold for a D x D block of laws up to
+// four species, 64 KB for five or six (4096 for D = 1, 1023 for D = 2, 255
+// for D = 3 or 4, 169 for D = 5 or 6). Fewer segments put a warp's lookups on
+// fewer distinct entries (fewer bank conflicts): the 2^24 D = 4 walk takes
+// 66.2 / 65.9 / 65.2 / 64.9 / 64.4 ms with 511 / 383 / 255 / 191 / 127, while
+// the largest deviation from T grows 2.1e-6 / 3.7e-6 / 8.4e-6 / 1.5e-5 /
+// 3.4e-5 (of T(0) = 1 for the Newtonian law); 255 stays below the 1.9e-5 of
+// the six-species default.
 int walk_table_entries(int D, int table_size) {
   if (table_size > 0) return table_size;
   const int pad = D <= 1 ? 1 : D == 2 ? 2 : D <= 4 ? 4 : 8;
-  const size_t budget = 64 * 1024;
+  const size_t budget = D <= 4 ? 32 * 1024 : 64 * 1024;
   return (int)std::min<size_t>(4096, budget / (sizeof(float) * 2 * D * pad) - 1);
 }
 

@@ -74,9 +74,9 @@ int from_sim(ng_batch* b, int i, int code) {
   return bfail(b, code, "simulation %d: %s", i, ng_last_error(b->sims[i]));
 }
 
-// Segments per law of a batch class table (the accuracy of a D = 4 table),
-// fewer when the first member's laws would not fit the table budget.
-constexpr int kBatchSegments = 511;
+// Segments per law of a batch class table (those of a D = 4 table), fewer
+// when the first member's laws would not fit the table budget.
+constexpr int kBatchSegments = 255;
 constexpr size_t kClassTableBytes = 64 * 1024;
 
 // A simulation joins a walk class when the cut-off, accumulation and segment
