@@ -211,9 +211,12 @@ __global__ void k_kick_drift(int64_t m, float* __restrict__ vel, const float* __
     float v = fmaf(a, h, vel[i]);
     if (nkick == 2) v = fmaf(a, h, v);
     vel[i] = v;
-    const double x = fma((double)v, dt, pos[i]);
+    double x = fma((double)v, dt, pos[i]);
     const long long b = __double_as_longlong(x);
-    pos[i] = pow2 && b >= 0 && b < __double_as_longlong(L) ? x : x - L * floor(pow2 ? x * invL : x / L);
+    // the wrap is the rare case: a branch keeps its FP64 floor (and the
+    // division of a box that is not a power of two) off the common path
+    if (!(pow2 && b >= 0 && b < __double_as_longlong(L))) x -= L * floor(pow2 ? x * invL : x / L);
+    pos[i] = x;
   }
 }
 
