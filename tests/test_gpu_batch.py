@@ -2,9 +2,10 @@
 (sort/tree/PM on worker streams, one walk launch for all species counts)
 matches the same simulation advanced alone through ng_step, and, in direct
 summation, the FP64 oracle's integration. The batch's walk reads the class's
-law table (laid out for six species, its own segment count), so batch and
-alone differ at the table's accuracy (~1e-5 of a force): 99 % of bodies
-within 1e-4 of their displacement / velocity change, all within 1e-2."""
+law table (one row per distinct law of its members, its own segment count),
+so batch and alone differ at the table's accuracy (~1e-5 of a force): 99 %
+of bodies within 1e-4 of their displacement / velocity change, all within
+1e-2."""
 import numpy as np
 import pytest
 
@@ -131,3 +132,61 @@ def test_batch_members_match_the_oracle(ng):
         rv = _rel_change(x["vel"].cpu().numpy().astype(np.float64), vo, w["vel"].astype(np.float64))
         assert np.percentile(rx, 99) <= 1e-4, np.percentile(rx, 99)
         assert np.percentile(rv, 99) <= 1e-4, np.percentile(rv, 99)
+
+
+def _mixed_laws(theta):
+    """Yukawa members (D = 3: six distinct laws; D = 2: three) and Newtonian
+    members (one law, the same row for both): ten rows in one class table."""
+    sims = []
+    for n, D, seed, yuk in [(4000, 3, 91, True), (3000, 2, 92, True), (5000, 4, 93, False),
+                            (2000, 1, 94, False)]:
+        w = small_clustered(n, D, seed, yukawa=yuk, mesh=32)
+        w["params"] = dict(w["params"], theta=theta)
+        rng = inputs.rng_for(seed + 100)
+        w["vel"] = (0.01 * rng.standard_normal((3, n))).astype(np.float32)
+        sims.append(w)
+    return sims
+
+
+def test_batch_with_mixed_laws(ng):
+    """Each member's species pairs map to the right rows of the shared table:
+    in direct summation (theta = 0) three KDK steps of every member match the
+    oracle's integration, and with the walk (theta = 0.5) every member matches
+    the same simulation stepped alone."""
+    import torch
+    import oracle
+    from common import oracle_params
+    sims = _mixed_laws(0.0)
+    b = ng.ng_batch_create([ng_params(w["params"]) for w in sims])
+    assert ng.ng_batch_walk_launches(b) == 1
+    m = [_dev(w) for w in sims]
+    ng.ng_batch_step(b, [x["pos"] for x in m], [x["vel"] for x in m], [x["typ"] for x in m],
+                     [x["mass"] for x in m], [x["acc"] for x in m], False, 3, 1e-3)
+    torch.cuda.synchronize()
+    ng.ng_batch_destroy(b)
+    for w, x in zip(sims, m):
+        xo, vo, _ = oracle.kdk(oracle_params(w["params"]), w["pos"], w["vel"].astype(np.float64),
+                               w["type"], w["mass"], 3, 1e-3)
+        rx = _rel_change(x["pos"].cpu().numpy(), xo, w["pos"])
+        rv = _rel_change(x["vel"].cpu().numpy().astype(np.float64), vo, w["vel"].astype(np.float64))
+        assert np.percentile(rx, 99) <= 1e-4, np.percentile(rx, 99)
+        assert np.percentile(rv, 99) <= 1e-4, np.percentile(rv, 99)
+    sims = _mixed_laws(0.5)
+    alone = []
+    for w in sims:
+        a = _dev(w)
+        s = ng.Simulation(ng_params(w["params"]))
+        ng.ng_step(s.ctx, a["pos"], a["vel"], a["typ"], a["mass"], a["acc"], False, 3, 1e-3)
+        torch.cuda.synchronize()
+        alone.append({k: v.cpu().numpy() for k, v in a.items()})
+        s.close()
+    b = ng.ng_batch_create([ng_params(w["params"]) for w in sims])
+    m = [_dev(w) for w in sims]
+    ng.ng_batch_step(b, [x["pos"] for x in m], [x["vel"] for x in m], [x["typ"] for x in m],
+                     [x["mass"] for x in m], [x["acc"] for x in m], False, 3, 1e-3)
+    torch.cuda.synchronize()
+    ng.ng_batch_destroy(b)
+    for w, x, ref in zip(sims, m, alone):
+        rv = _rel_change(x["vel"].cpu().numpy().astype(np.float64), ref["vel"].astype(np.float64),
+                         w["vel"].astype(np.float64))
+        assert np.percentile(rv, 99) <= 1e-4 and rv.max() <= 1e-2, (np.percentile(rv, 99), rv.max())
