@@ -33,28 +33,59 @@ __global__ void k_cic_deposit(int64_t n, const uint32_t* __restrict__ order,
                               float* __restrict__ rho) {
   const size_t N3 = (size_t)N * N * N;
   const int mask = N - 1;
-  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n;
-       j += (int64_t)gridDim.x * blockDim.x) {
-    const uint32_t k = order[j];
+  const int lane = threadIdx.x & 31;
+  const uint32_t below = (1u << lane) - 1u;
+  // whole warps step together (the shuffles below need every lane)
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t base = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); base < n;
+       base += stride) {
+    const int64_t j = base + lane;
+    const bool valid = j < n;
+    const uint32_t k = valid ? order[j] : 0u;
     const double ux = spos[k] * cells_per_len, uy = spos[n + k] * cells_per_len,
                  uz = spos[2 * n + k] * cells_per_len;
     const double fx0 = floor(ux), fy0 = floor(uy), fz0 = floor(uz);
     const float fx = (float)(ux - fx0), fy = (float)(uy - fy0), fz = (float)(uz - fz0);
     const int ix = (int)fx0 & mask, iy = (int)fy0 & mask, iz = (int)fz0 & mask;
     const int jx = (ix + 1) & mask, jy = (iy + 1) & mask, jz = (iz + 1) & mask;
-    float* r = rho + (size_t)stype[k] * N3;
-    const float m = smass[k];
+    const size_t off = (size_t)stype[k] * N3;
+    const float m = valid ? smass[k] : 0.f;
     const float wx0 = 1.f - fx, wy0 = 1.f - fy, wz0 = 1.f - fz;
     const size_t X0 = (size_t)ix * N * N, X1 = (size_t)jx * N * N;
     const size_t Y0 = (size_t)iy * N, Y1 = (size_t)jy * N;
-    atomicAdd(r + X0 + Y0 + iz, m * wx0 * wy0 * wz0);
-    atomicAdd(r + X0 + Y0 + jz, m * wx0 * wy0 * fz);
-    atomicAdd(r + X0 + Y1 + iz, m * wx0 * fy * wz0);
-    atomicAdd(r + X0 + Y1 + jz, m * wx0 * fy * fz);
-    atomicAdd(r + X1 + Y0 + iz, m * fx * wy0 * wz0);
-    atomicAdd(r + X1 + Y0 + jz, m * fx * wy0 * fz);
-    atomicAdd(r + X1 + Y1 + iz, m * fx * fy * wz0);
-    atomicAdd(r + X1 + Y1 + jz, m * fx * fy * fz);
+    float w[8] = {m * wx0 * wy0 * wz0, m * wx0 * wy0 * fz, m * wx0 * fy * wz0, m * wx0 * fy * fz,
+                  m * fx * wy0 * wz0,  m * fx * wy0 * fz,  m * fx * fy * wz0,  m * fx * fy * fz};
+    // bodies in type-major Morton order: the bodies of one mesh cell and
+    // species are consecutive, so consecutive lanes with the same cell form
+    // runs; each run's weights are summed in registers and its last lane
+    // adds them (one atomic per corner and run instead of per body)
+    const size_t cell = valid ? off + X0 + Y0 + iz : ~(size_t)lane;
+    const size_t prev = __shfl_up_sync(0xffffffffu, cell, 1);
+    const uint32_t heads = __ballot_sync(0xffffffffu, lane == 0 || prev != cell);
+    bool tail = true;
+    if (heads != 0xffffffffu) {
+      const int head = 31 - __clz(heads & (below | (1u << lane)));
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          const float t = __shfl_up_sync(0xffffffffu, w[c], d);
+          if (lane - d >= head) w[c] += t;
+        }
+      }
+      tail = lane == 31 || ((heads >> (lane + 1)) & 1u);
+    }
+    if (valid && tail) {
+      float* r = rho + off;
+      atomicAdd(r + X0 + Y0 + iz, w[0]);
+      atomicAdd(r + X0 + Y0 + jz, w[1]);
+      atomicAdd(r + X0 + Y1 + iz, w[2]);
+      atomicAdd(r + X0 + Y1 + jz, w[3]);
+      atomicAdd(r + X1 + Y0 + iz, w[4]);
+      atomicAdd(r + X1 + Y0 + jz, w[5]);
+      atomicAdd(r + X1 + Y1 + iz, w[6]);
+      atomicAdd(r + X1 + Y1 + jz, w[7]);
+    }
   }
 }
 
