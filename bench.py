@@ -51,6 +51,14 @@ DEFAULT_WORKLOAD = "clustered16m_d4_yukawa"
 # library's default), whatever leaf size the timed walk runs with: the count
 # of the per-particle walk grows with the leaf size, the work to be done does not.
 REF_LEAF = 8
+# Walk shape (leaf size, group cell) of served requests: requests of 2^17
+# bodies or more, whose walks fill the GPU and bound the saturated serving
+# loop, take leaf 32 / cell 128 (their 10-step integrations, timed one at a
+# time: 643 ms summed at leaf 8 / cell 32, 598 ms at 32 / 128); smaller ones
+# keep the library default.
+SERVE_LARGE_N = 1 << 17
+SERVE_LARGE_SHAPE = (32, 128)
+SERVE_SMALL_SHAPE = (8, 32)
 
 
 def job_totals(units, ms, world):
@@ -584,8 +592,13 @@ def bench_serve(args, ws, rank, local):
         rs = 1.25 / mesh
         prm = dict(D=D, G=coup["G"], law=coup["law"], ya=coup["ya"], yl=coup["yl"], box=1.0,
                    eps=0.02 / n ** (1 / 3), rs=rs, rcut=4.5 * rs, theta=0.5, pm_mesh=mesh)
+        # walk shape by request size (the plain calls and the serving loop
+        # both take it from the request's parameters)
+        shape = SERVE_LARGE_SHAPE if n >= SERVE_LARGE_N else SERVE_SMALL_SHAPE
         pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
-        pool.append(dict(n=n, params=ng.params_from_workload(prm), pos=pin(pos), typ=pin(typ),
+        pool.append(dict(n=n, params=ng.params_from_workload(prm, leaf_size=shape[0],
+                                                             group_cell=shape[1]),
+                         pos=pin(pos), typ=pin(typ),
                          mass=pin(np.full(n, 1.0 / n, np.float32)),
                          acc=torch.zeros((3, n), dtype=torch.float32).pin_memory(),
                          pos_out=torch.zeros((3, n), dtype=torch.float64).pin_memory(),
@@ -683,7 +696,9 @@ def bench_serve(args, ws, rank, local):
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "serve2000", "requests": nreq, "rate_per_s": 200, "slots": 16,
                        "budget_bytes": 120 << 30, "mix": "50% force, 50% 10-step KDK",
-                       "n_range_log2": [10, 20]},
+                       "n_range_log2": [10, 20],
+                       "walk_shape": {"n_from": SERVE_LARGE_N, "large": list(SERVE_LARGE_SHAPE),
+                                      "small": list(SERVE_SMALL_SHAPE)}},
             "one_at_a_time": {"plain_calls_requests_per_s": nreq / wpl,
                               "serving_one_slot_requests_per_s": nreq / w1},
             "speedup_vs_plain_calls": wpl / wk, "speedup_vs_one_slot": w1 / wk,
