@@ -294,6 +294,7 @@ int alloc_nodes(ng_ctx* c, int64_t cap) {
   NG_TRY(ensure(c, c->n_com, cap * 16));
   NG_TRY(ensure(c, c->n_link, cap * 16));
   NG_TRY(ensure(c, c->n_mono, cap * D * 16));
+  NG_TRY(ensure(c, c->mono_bins, (3 * kMonoBins + 1) * sizeof(uint32_t)));
   c->cap_nodes = cap;
   (void)node_bytes;
   return NG_OK;
@@ -708,7 +709,7 @@ int ng_destroy(ng_ctx* c) {
                     &c->spos, &c->smass, &c->stype, &c->body, &c->bleaf,
                     &c->tperm, &c->scan_part, &c->n_level, &c->n_prefix, &c->n_first,
                     &c->n_count, &c->n_child, &c->n_nchild, &c->n_tmp, &c->n_m64,
-                    &c->n_cnt, &c->n_geo, &c->n_com, &c->n_link, &c->n_mono, &c->groups, &c->gsize, &c->grank,
+                    &c->n_cnt, &c->n_geo, &c->n_com, &c->n_link, &c->n_mono, &c->mono_bins, &c->groups, &c->gsize, &c->grank,
                     &c->status, &c->counter, &c->aold, &c->io_pos, &c->io_vel, &c->io_type, &c->io_mass,
                     &c->io_acc, &c->lattice, &c->rho, &c->rhok, &c->phi,
                     &c->walk_desc, &c->walk_prefix, &c->spos_alt, &c->smass_alt, &c->stype_alt,

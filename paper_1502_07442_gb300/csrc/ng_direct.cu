@@ -68,10 +68,8 @@ __global__ void __launch_bounds__(128) k_direct64(DirectArgs a) {
       }
       const uint32_t nd = stack[--sp];
       const uint64_t pre = a.prefix[nd];
-      const double side = 1.0 / (double)(1u << a.level[nd]);
-      const double c[3] = {((double)morton_compact3(pre >> 2) + 0.5) * side,
-                           ((double)morton_compact3(pre >> 1) + 0.5) * side,
-                           ((double)morton_compact3(pre) + 0.5) * side};
+      double c[3], side;
+      node_centre(a.level[nd], pre, c, &side);
       const double half = 0.5 * side;
       double g2 = 0.0;
 #pragma unroll

@@ -25,6 +25,13 @@ constexpr int kCapturedDepthMargin = 2;  // captured steps build this far below 
 // one launch per level and phase, over the whole GPU).
 constexpr int kClusterBlocks = 8;
 constexpr int64_t kClusterMaxBodies = 32768;
+// Monopoles of trees of kBinnedMonoBodies bodies or more are reduced in an
+// order binned by the work of a node: leaves by body count (0..64, one more
+// bin for the larger leaves of a tree stopped at a level cap), internal nodes
+// by level and child count.
+constexpr int kLeafBins = 66;
+constexpr int kMonoBins = kLeafBins + (kMaxLevel + 1) * 8;
+constexpr int64_t kBinnedMonoBodies = 1 << 20;   // smaller trees: level order
 constexpr int kWarp = 32;
 
 // Status words in device memory (ctx->status).
@@ -74,6 +81,24 @@ __device__ __forceinline__ uint32_t morton_compact3(uint64_t v) {
   v = (v ^ (v >> 16)) & 0x1f00000000ffffull;
   v = (v ^ (v >> 32)) & 0x1fffffull;
   return (uint32_t)v;
+}
+
+// (2 i + 1) 2^-(lvl + 1), the centre of cell i of level lvl in box units:
+// exact in FP64, and formed from its bits with integer operations only
+// (FP64 issues at 1/64 of the FP32 rate here).
+__device__ __forceinline__ double cell_centre(uint32_t i, int lvl) {
+  const uint32_t v = 2u * i + 1u;            // odd, below 2^22
+  const int p = 31 - __clz(v);               // v = 1.f 2^p
+  const uint64_t mant = ((uint64_t)v << (52 - p)) & ((1ull << 52) - 1);
+  return __longlong_as_double((long long)(((uint64_t)(1023 + p - (lvl + 1)) << 52) | mant));
+}
+
+// Centre (box units) and side 2^-lvl of a node from its level and Morton prefix.
+__device__ __forceinline__ void node_centre(int lvl, uint64_t pre, double c[3], double* side) {
+  c[0] = cell_centre(morton_compact3(pre >> 2), lvl);
+  c[1] = cell_centre(morton_compact3(pre >> 1), lvl);
+  c[2] = cell_centre(morton_compact3(pre), lvl);
+  *side = __longlong_as_double((long long)(1023 - lvl) << 52);
 }
 
 // A box-unit offset wrapped to its nearest periodic image, rounded once.
@@ -256,6 +281,7 @@ struct ng_ctx {
   int64_t ngroups = 0, ngroups_n = -1;   // walk groups of the last checked build, for n = ngroups_n
   ng::DevBuf n_level, n_prefix, n_first, n_count, n_child, n_nchild, n_tmp;
   ng::DevBuf n_m64, n_cnt, n_geo, n_com, n_link, n_mono;
+  ng::DevBuf mono_bins;   // uint32[3 kMonoBins + 1]: nodes, cursors and starts per monopole bin
   ng::DevBuf groups;
   ng::DevBuf gsize, grank;          // group size at its first body, rank of each group start
   ng::DevBuf status;     // uint32[ST_COUNT]

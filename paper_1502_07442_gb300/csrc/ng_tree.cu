@@ -1,7 +1,8 @@
 // Tree stage (Sec. 2.2): canonical Morton-prefix octree built breadth-first
 // one level per launch (node ranges stay on the device, no host round trip),
-// per-node per-species monopoles reduced bottom-up in double precision with
-// warp shuffles, and the walk groups.
+// per-node per-species monopoles reduced in double precision (one thread per
+// node: every leaf in one launch, then the internal nodes level by level,
+// bottom-up), and the walk groups.
 //
 // Canonical tree: nodes are the non-empty Morton cells reachable from the
 // root; a cell is a leaf iff it holds <= leaf_size bodies or is at level 20;
@@ -326,14 +327,6 @@ int build_octree(ng_ctx* c) {
 
 // --------------------------------------------------------- monopoles
 
-// Centre (box units) of a node from its level and Morton prefix.
-__device__ __forceinline__ void node_centre(int lvl, uint64_t pre, double c[3], double* side) {
-  const double s = 1.0 / (double)(1u << lvl);
-  c[0] = ((double)morton_compact3(pre >> 2) + 0.5) * s;
-  c[1] = ((double)morton_compact3(pre >> 1) + 0.5) * s;
-  c[2] = ((double)morton_compact3(pre) + 0.5) * s;
-  *side = s;
-}
 
 struct MonoArgs {
   const uint8_t* level;
@@ -459,6 +452,84 @@ __device__ __forceinline__ void mono_node(int lvl, uint32_t k, const MonoArgs& a
   a.link[k] = make_int4(nch ? (int)a.child[k] : -1, (int)nch, (int)f, (int)c);
 }
 
+// Trees of kBinnedMonoBodies bodies or more: one thread per node, in an
+// order binned by the node's work. A leaf loops over its bodies and an
+// internal node over its children, so a warp runs as long as its longest
+// loop; FP64 issues at 1/64 of the FP32 rate here and a warp instruction
+// costs the same with idle lanes. Taken in level (Morton) order, the leaves
+// of a warp hold 1 to leaf_size bodies and a warp ran 2.5 times the
+// iterations its bodies need (2^24 clustered bodies, leaf 32); binned, the
+// threads of a warp have equal loop counts. All leaves are reduced by one
+// launch (a leaf needs no other node), then the internal nodes level by
+// level, bottom-up. Each node is still summed by one thread in its own order,
+// so the results do not depend on the binning.
+static_assert(kMonoBins <= 256, "the bin scan takes one bin per thread of a 256-thread block");
+
+__device__ __forceinline__ int mono_bin(uint32_t lvl, uint32_t nch, uint32_t cnt) {
+  return nch == 0 ? (int)min(cnt, (uint32_t)(kLeafBins - 1)) : kLeafBins + (int)lvl * 8 + (int)nch - 1;
+}
+
+// bins[0, kMonoBins): nodes per bin (zeroed before the launch)
+__global__ void __launch_bounds__(256) k_mono_hist(uint32_t* status, int64_t cap,
+                                                   const uint8_t* __restrict__ level,
+                                                   const uint8_t* __restrict__ nchild,
+                                                   const uint32_t* __restrict__ count, uint32_t* bins) {
+  __shared__ uint32_t h[kMonoBins];
+  if (status[ST_FLAGS] & SF_NODE_OVERFLOW) return;   // truncated tree: do not read it
+  for (int i = threadIdx.x; i < kMonoBins; i += blockDim.x) h[i] = 0;
+  __syncthreads();
+  uint32_t total = levels_of(status).start[kMaxLevel + 1];
+  if (total > cap) total = (uint32_t)cap;
+  for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < total; k += gridDim.x * blockDim.x)
+    atomicAdd(&h[mono_bin(level[k], nchild[k], count[k])], 1u);
+  __syncthreads();
+  for (int i = threadIdx.x; i < kMonoBins; i += blockDim.x)
+    if (h[i]) atomicAdd(&bins[i], h[i]);
+}
+
+// order[]: node indices grouped by bin. bins[kMonoBins, 2 kMonoBins): cursors
+// (zeroed before the launch); block 0 writes the bin starts to
+// bins[2 kMonoBins, 3 kMonoBins] (the last entry: all nodes). Each block
+// places one contiguous chunk of nodes, reserving its share of every bin with
+// one atomic per bin. Launched with 256 threads.
+__global__ void __launch_bounds__(256) k_mono_order(uint32_t* status, int64_t cap,
+                                                    const uint8_t* __restrict__ level,
+                                                    const uint8_t* __restrict__ nchild,
+                                                    const uint32_t* __restrict__ count, uint32_t* bins,
+                                                    uint32_t* order) {
+  __shared__ uint32_t lh[kMonoBins];
+  __shared__ uint32_t base[kMonoBins];
+  __shared__ uint32_t warp_tot[8];
+  __shared__ uint32_t all;
+  if (status[ST_FLAGS] & SF_NODE_OVERFLOW) return;
+  const int tid = threadIdx.x;
+  // bin starts: exclusive scan of the bin counts
+  const uint32_t v = tid < kMonoBins ? bins[tid] : 0u;
+  const uint32_t inc = block_inclusive_scan<256>(v, warp_tot, &all);
+  if (tid < kMonoBins) {
+    base[tid] = inc - v;
+    lh[tid] = 0;
+    if (blockIdx.x == 0) bins[2 * kMonoBins + tid] = inc - v;
+  }
+  if (blockIdx.x == 0 && tid == 0) bins[3 * kMonoBins] = all;
+  __syncthreads();
+  uint32_t total = levels_of(status).start[kMaxLevel + 1];
+  if (total > cap) total = (uint32_t)cap;
+  const uint32_t chunk = (total + gridDim.x - 1) / gridDim.x;
+  const uint32_t k0 = min(total, blockIdx.x * chunk), k1 = min(total, k0 + chunk);
+  for (uint32_t k = k0 + tid; k < k1; k += blockDim.x)
+    atomicAdd(&lh[mono_bin(level[k], nchild[k], count[k])], 1u);
+  __syncthreads();
+  if (tid < kMonoBins && lh[tid]) base[tid] += atomicAdd(&bins[kMonoBins + tid], lh[tid]);
+  __syncthreads();
+  for (uint32_t k = k0 + tid; k < k1; k += blockDim.x)
+    order[atomicAdd(&base[mono_bin(level[k], nchild[k], count[k])], 1u)] = k;
+}
+
+// Trees below kBinnedMonoBodies bodies: one launch per level, bottom-up, one
+// thread per node of the level in level order. Their levels hold few nodes,
+// so the three launches of the binned order cost more than its convergence
+// saves (batches of 2^12..2^18-body simulations: 7.74 against 8.11 ms).
 template <int D>
 __global__ void __launch_bounds__(kMonoThreads) k_monopoles(int lvl, MonoArgs a) {
   __shared__ double lacc[D][4][kMonoThreads];
@@ -469,6 +540,32 @@ __global__ void __launch_bounds__(kMonoThreads) k_monopoles(int lvl, MonoArgs a)
   if (e > a.cap) e = (uint32_t)a.cap;
   for (uint32_t k = s + blockIdx.x * blockDim.x + threadIdx.x; k < e; k += gridDim.x * blockDim.x)
     mono_node<D>(lvl, k, a, lacc, threadIdx.x);
+}
+
+// Every leaf of the tree: order[0, start of the first internal bin).
+template <int D>
+__global__ void __launch_bounds__(kMonoThreads) k_mono_leaves(MonoArgs a, const uint32_t* __restrict__ bins,
+                                                              const uint32_t* __restrict__ order) {
+  __shared__ double lacc[D][4][kMonoThreads];
+  if (a.status[ST_FLAGS] & SF_NODE_OVERFLOW) return;
+  const uint32_t e = bins[2 * kMonoBins + kLeafBins];
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < e; i += gridDim.x * blockDim.x) {
+    const uint32_t k = order[i];
+    mono_node<D>(a.level[k], k, a, lacc, threadIdx.x);
+  }
+}
+
+// The internal nodes of level lvl (their children are done).
+template <int D>
+__global__ void __launch_bounds__(kMonoThreads) k_mono_internal(int lvl, MonoArgs a,
+                                                                const uint32_t* __restrict__ bins,
+                                                                const uint32_t* __restrict__ order) {
+  __shared__ double lacc[D][4][kMonoThreads];
+  if (a.status[ST_FLAGS] & SF_NODE_OVERFLOW) return;
+  const uint32_t* start = bins + 2 * kMonoBins + kLeafBins + lvl * 8;
+  const uint32_t s = start[0], e = start[8];
+  for (uint32_t i = s + blockIdx.x * blockDim.x + threadIdx.x; i < e; i += gridDim.x * blockDim.x)
+    mono_node<D>(lvl, order[i], a, lacc, threadIdx.x);
 }
 
 // Every level of a small tree, bottom-up, in one launch: one cluster of
@@ -532,18 +629,55 @@ int reduce_monopoles(ng_ctx* c) {
     NG_CUDA(c, cudaGetLastError());
     return NG_OK;
   }
-  c->launches += lmax + 1;
-  for (int l = lmax; l >= 0; --l) {
+  if (c->n < kBinnedMonoBodies) {
+    c->launches += lmax + 1;
+    for (int l = lmax; l >= 0; --l) {
+      const int64_t nodes = std::min<int64_t>(c->cap_nodes, level_bound(l, c->n));
+      const int grid = (int)std::max<int64_t>(
+          1, std::min<int64_t>((int64_t)c->nsm * 16, (nodes + kMonoThreads - 1) / kMonoThreads));
+      switch (c->p.D) {
+        case 1: k_monopoles<1><<<grid, kMonoThreads, 0, c->stream>>>(l, a); break;
+        case 2: k_monopoles<2><<<grid, kMonoThreads, 0, c->stream>>>(l, a); break;
+        case 3: k_monopoles<3><<<grid, kMonoThreads, 0, c->stream>>>(l, a); break;
+        case 4: k_monopoles<4><<<grid, kMonoThreads, 0, c->stream>>>(l, a); break;
+        case 5: k_monopoles<5><<<grid, kMonoThreads, 0, c->stream>>>(l, a); break;
+        default: k_monopoles<6><<<grid, kMonoThreads, 0, c->stream>>>(l, a); break;
+      }
+    }
+    NG_CUDA(c, cudaGetLastError());
+    return NG_OK;
+  }
+  // the tree build's per-level scratch (n_tmp, one word per node) is free
+  // once the tree is built: it holds the binned node order
+  uint32_t* bins = as<uint32_t>(c->mono_bins);
+  uint32_t* order = as<uint32_t>(c->n_tmp);
+  NG_CUDA(c, cudaMemsetAsync(bins, 0, 2 * kMonoBins * sizeof(uint32_t), c->stream));
+  const int sgrid = work_grid(c, c->cap_nodes, 4);
+  k_mono_hist<<<sgrid, 256, 0, c->stream>>>(a.status, a.cap, a.level, a.nchild, a.count, bins);
+  k_mono_order<<<sgrid, 256, 0, c->stream>>>(a.status, a.cap, a.level, a.nchild, a.count, bins, order);
+  const int lgrid = (int)std::max<int64_t>(
+      1, std::min<int64_t>((int64_t)c->nsm * 16, (c->cap_nodes + kMonoThreads - 1) / kMonoThreads));
+  switch (c->p.D) {
+    case 1: k_mono_leaves<1><<<lgrid, kMonoThreads, 0, c->stream>>>(a, bins, order); break;
+    case 2: k_mono_leaves<2><<<lgrid, kMonoThreads, 0, c->stream>>>(a, bins, order); break;
+    case 3: k_mono_leaves<3><<<lgrid, kMonoThreads, 0, c->stream>>>(a, bins, order); break;
+    case 4: k_mono_leaves<4><<<lgrid, kMonoThreads, 0, c->stream>>>(a, bins, order); break;
+    case 5: k_mono_leaves<5><<<lgrid, kMonoThreads, 0, c->stream>>>(a, bins, order); break;
+    default: k_mono_leaves<6><<<lgrid, kMonoThreads, 0, c->stream>>>(a, bins, order); break;
+  }
+  // nodes at level lmax are leaves
+  c->launches += 3 + lmax;
+  for (int l = lmax - 1; l >= 0; --l) {
     const int64_t nodes = std::min<int64_t>(c->cap_nodes, level_bound(l, c->n));
     const int grid = (int)std::max<int64_t>(
         1, std::min<int64_t>((int64_t)c->nsm * 16, (nodes + kMonoThreads - 1) / kMonoThreads));
     switch (c->p.D) {
-      case 1: k_monopoles<1><<<grid, kMonoThreads, 0, c->stream>>>(l, a); break;
-      case 2: k_monopoles<2><<<grid, kMonoThreads, 0, c->stream>>>(l, a); break;
-      case 3: k_monopoles<3><<<grid, kMonoThreads, 0, c->stream>>>(l, a); break;
-      case 4: k_monopoles<4><<<grid, kMonoThreads, 0, c->stream>>>(l, a); break;
-      case 5: k_monopoles<5><<<grid, kMonoThreads, 0, c->stream>>>(l, a); break;
-      default: k_monopoles<6><<<grid, kMonoThreads, 0, c->stream>>>(l, a); break;
+      case 1: k_mono_internal<1><<<grid, kMonoThreads, 0, c->stream>>>(l, a, bins, order); break;
+      case 2: k_mono_internal<2><<<grid, kMonoThreads, 0, c->stream>>>(l, a, bins, order); break;
+      case 3: k_mono_internal<3><<<grid, kMonoThreads, 0, c->stream>>>(l, a, bins, order); break;
+      case 4: k_mono_internal<4><<<grid, kMonoThreads, 0, c->stream>>>(l, a, bins, order); break;
+      case 5: k_mono_internal<5><<<grid, kMonoThreads, 0, c->stream>>>(l, a, bins, order); break;
+      default: k_mono_internal<6><<<grid, kMonoThreads, 0, c->stream>>>(l, a, bins, order); break;
     }
   }
   NG_CUDA(c, cudaGetLastError());

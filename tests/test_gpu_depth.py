@@ -136,3 +136,63 @@ def test_batch_replay_deeper_than_its_cap(ng):
     torch.cuda.synchronize()
     assert np.isfinite(acc[1].cpu().numpy()).all()
     ng.ng_batch_destroy(b)
+
+
+def test_capped_replay_large_tree_binned_monopoles(ng):
+    """Trees of 2^20 bodies or more reduce their monopoles in an order binned
+    by each node's work, with one bin for the leaves above the leaf size that
+    a level cap leaves. A step captured on uniform bodies is replayed after
+    8192 of them were packed into a cube of side 1e-4: the capped tree then
+    holds a leaf far above the leaf size. Every node's species counts and
+    masses are exact sums of its bodies (equal FP32 masses add exactly in
+    FP64), and the replayed force on a sample of cube and background bodies
+    meets the tree-mode rule against the direct TreePM force (Sec. 2.2,
+    Sec. 2.4)."""
+    import torch
+    n = (1 << 20) + 8192
+    rng = inputs.rng_for(73)
+    coup = inputs.newton_couplings(2, rng)
+    mesh = 32
+    rs = 1.25 / mesh
+    prm = dict(D=2, G=coup["G"], law=coup["law"], ya=coup["ya"], yl=coup["yl"], box=1.0,
+               eps=1e-5, rs=rs, rcut=4.5 * rs, theta=0.5, pm_mesh=mesh, leaf_size=8)
+    uniform = rng.random((3, n))
+    packed = uniform.copy()
+    packed[:, :8192] = 0.3 + 1e-4 * (rng.random((3, 8192)) - 0.5)
+    typ = inputs.species_uniform(n, 2, rng)
+    m32 = np.float32(1.0 / n)
+    mass = np.full(n, m32, np.float32)
+    dev = torch.device("cuda:0")
+    pos = torch.from_numpy(uniform.copy()).to(dev)
+    vel = torch.zeros((3, n), dtype=torch.float32, device=dev)
+    acc = torch.zeros((3, n), dtype=torch.float32, device=dev)
+    typ_d = torch.from_numpy(typ).to(dev)
+    mass_d = torch.from_numpy(mass).to(dev)
+    sim = ng.Simulation(ng_params(prm))
+    dt = 1e-6
+    ng.ng_step(sim.ctx, pos, vel, typ_d, mass_d, acc, False, 2, dt)   # captured on uniform bodies
+    # at rest with a zero opening kick the drift leaves every position as it
+    # is, so the replayed step's force is the force at the packed positions
+    pos.copy_(torch.from_numpy(packed))
+    vel.zero_()
+    acc.zero_()
+    ng.ng_step(sim.ctx, pos, vel, typ_d, mass_d, acc, True, 1, dt)    # replayed, capped
+    torch.cuda.synchronize()
+    assert np.array_equal(pos.cpu().numpy(), packed)
+    T = ng.ng_tree_export(sim.ctx, 2)
+    leaf = T["nchild"] == 0
+    assert (T["count"][leaf] > 8).any()                # the cap kept an oversize leaf
+    assert np.array_equal(T["cnt"].sum(axis=1), T["count"])
+    assert np.array_equal(T["mass"], T["cnt"].astype(np.float64) * float(m32))
+    assert np.array_equal(T["cnt"][0], np.bincount(typ, minlength=2))
+    got = acc.cpu().numpy().astype(np.float64)
+    sim.close()
+    sample = np.concatenate([np.arange(0, 8192, 41), 8192 + rng.choice(n - 8192, 300, replace=False)])
+    op = oracle_params(prm)
+    long_ = oracle.pm(op, packed, typ, mass)[:, sample]
+    ref = oracle.direct(op, packed, typ, mass, tgt=sample) + long_
+    tree, _ = oracle.tree_walk(op, packed, typ, mass, tgt=sample)
+    e_gpu, _ = rel_err(got[:, sample], ref)
+    e_cpu, _ = rel_err(tree + long_, ref)
+    assert np.percentile(e_gpu, 99) <= 1.1 * np.percentile(e_cpu, 99) + 1e-5, (
+        np.percentile(e_gpu, 99), np.percentile(e_cpu, 99))
