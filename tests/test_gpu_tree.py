@@ -131,3 +131,44 @@ def test_tree_queries_after_single_steps(ng):
         assert np.array_equal(tree[k], tree_f[k]), k
     sim.close()
     fresh.close()
+
+
+def _large(D, leaf, seed):
+    w = small_clustered((1 << 20) + 777, D, seed, leaf=leaf)
+    rng = inputs.rng_for(seed + 1)
+    n = w["type"].size
+    w["mass"] = (rng.uniform(0.5, 1.5, n) / n).astype(np.float32)   # unequal masses
+    if leaf == 1:
+        w["pos"][:, 1000:1400] = w["pos"][:, 999:1000]              # 400 duplicates: level-20 leaf
+    return w
+
+
+@pytest.mark.parametrize("D,leaf", [(6, 64), (1, 1)], ids=["d6_leaf64", "d1_leaf1"])
+def test_binned_monopoles_large_trees(ng, D, leaf):
+    """Trees of 2^20 bodies or more take the binned monopole order (leaves by
+    body count up to the largest leaf size, one bin above it; internal nodes
+    by level and child count): six species with 64-body leaves, and one
+    species with 1-body leaves whose duplicates end in a level-20 leaf above
+    the leaf size. The tree is bit-exact and the FP64 monopoles, with unequal
+    masses, within the summation-order bound of the oracle's (Sec. 2.2)."""
+    import torch
+    w = _large(D, leaf, 61 + D)
+    prm = w["params"]
+    pos, typ, mass = device_arrays(w)
+    sim = ng.Simulation(ng_params(prm))
+    ng.ng_build_tree(sim.ctx, pos, typ, mass)
+    torch.cuda.synchronize()
+    T = ng.ng_tree_export(sim.ctx, D)
+    sim.close()
+    R = oracle.tree(oracle_params(prm), w["pos"], w["type"], w["mass"])
+    for f in ("level", "prefix", "first", "count", "nchild", "child_first", "cnt"):
+        assert np.array_equal(T[f], R[f].astype(T[f].dtype)), f
+    leaf_counts = T["count"][T["nchild"] == 0]
+    assert (leaf_counts > (32 if leaf == 64 else 1)).any()
+    # FP64 sums of n terms in another order: n ulps of the sum of |terms|
+    m = R["mass"]
+    bound_m = 2.0 ** -53 * (R["cnt"].astype(np.float64) + 2) * m
+    assert np.all(np.abs(T["mass"] - m) <= bound_m)
+    dcom = np.abs(T["com"] - R["com"]).max(axis=2)
+    bound = 2.0 ** -53 * 4 * (R["cnt"].astype(np.float64) + 2)
+    assert np.all(dcom <= bound)
