@@ -64,7 +64,6 @@ struct DevBuf {
 };
 
 // Walk tuning constants.
-constexpr int kListCap = 64;            // records per species list per warp
 constexpr int kStackCap = 384;          // node stack entries per warp
 constexpr int kStackReserve = 7 * kMaxLevel + 8 + 32;   // depth-first descent + push-backs
 constexpr int kWalkMaxWarps = 32;
@@ -190,6 +189,15 @@ __host__ __device__ constexpr int walk_tab_shift(int D) { return D <= 1 ? 0 : D 
 // species, runs 24 warps when its law table is small (a few distinct laws).
 __host__ __device__ constexpr int walk_warps(int D) { return D <= 3 ? 24 : D == 4 ? 24 : D == 5 ? 20 : 16; }
 constexpr int kVardWarps = 24;
+// Records per species list per warp: as many as fit beside the default law
+// table at the walk's warp count. A list is evaluated once the next round of
+// up to 32 appends could overflow it, so longer lists spread each
+// evaluation's fixed cost over more records (the 2^24 D = 4 walk: 65.8 ms
+// with 64, 64.7 ms with 80); the variable-species instance of batches,
+// laid out for six species at 24 warps, keeps 64.
+__host__ __device__ constexpr int walk_list_cap(int D, bool vard) {
+  return vard ? 64 : D <= 2 ? 128 : D == 3 ? 96 : D == 4 ? 80 : D == 5 ? 64 : 72;
+}
 
 // Per-simulation inputs of the walk (device memory, one per simulation).
 // The law table of a walk launch (device copy).

@@ -31,14 +31,14 @@
 
 namespace ng {
 
-template <int D>
+template <int D, int CAP>
 struct __align__(16) WarpSmem {
   WalkDesc desc;              // batched launches: the current item's simulation
   // records per active species, table units, one float array per component
-  // (x[kListCap], y[kListCap], z[kListCap], m[kListCap]): consecutive records
+  // (x[CAP], y[CAP], z[CAP], m[CAP]): consecutive records
   // of one component are one 8- or 16-byte load, so the inner loop forms
   // (record j, record j + 1) pairs for the packed FP32x2 instructions
-  float4 list[D][kListCap];
+  float4 list[D][CAP];
   float4 leafc[32];           // opened leaves: centre offset from the origin (box units)
   int2 leafb[32];             // opened leaves: first body, body count
   int leafo[32];              // opened leaves: exclusive prefix of body counts
@@ -61,13 +61,14 @@ __device__ __forceinline__ bool near_box(float px, float py, float pz, float gx,
 }
 
 // Append one record at `slot` of a component-major list.
+template <int CAP>
 __device__ __forceinline__ void put_rec(float4* list, int slot, float x, float y, float z,
                                         float m) {
   float* c = reinterpret_cast<float*>(list);
   c[slot] = x;
-  c[kListCap + slot] = y;
-  c[2 * kListCap + slot] = z;
-  c[3 * kListCap + slot] = m;
+  c[CAP + slot] = y;
+  c[2 * CAP + slot] = z;
+  c[3 * CAP + slot] = m;
 }
 
 // 8-byte shared-memory load from a 32-bit shared address
@@ -96,7 +97,8 @@ __global__ void __launch_bounds__((VARD ? kVardWarps : walk_warps(D)) * 32, 1) k
   const int ntab = L.tab_count;
   for (int i = threadIdx.x; i < ntab; i += blockDim.x) tab[i] = L.tab[i];
   const size_t tab_bytes = ((size_t)ntab * sizeof(float2) + 15) & ~(size_t)15;
-  WarpSmem<D>* ws = reinterpret_cast<WarpSmem<D>*>(smem_raw + tab_bytes) + (threadIdx.x >> 5);
+  constexpr int CAP = walk_list_cap(D, VARD);
+  WarpSmem<D, CAP>* ws = reinterpret_cast<WarpSmem<D, CAP>*>(smem_raw + tab_bytes) + (threadIdx.x >> 5);
   __syncthreads();
 
   const int lane = threadIdx.x & 31;
@@ -199,7 +201,7 @@ __global__ void __launch_bounds__((VARD ? kVardWarps : walk_warps(D)) * 32, 1) k
       uint32_t fmask = 0;   // lists to evaluate now (the same in every lane)
 #pragma unroll
       for (int q = 0; q < D; ++q)
-        if (lc[q] > kListCap - 32 || (drain && lc[q] > 0)) fmask |= 1u << q;
+        if (lc[q] > CAP - 32 || (drain && lc[q] > 0)) fmask |= 1u << q;
 #pragma unroll 1
       while (fmask) {
         const int t = __ffs(fmask) - 1;
@@ -222,7 +224,7 @@ __global__ void __launch_bounds__((VARD ? kVardWarps : walk_warps(D)) * 32, 1) k
           // quads of records, then at most one pair
           const int cnt2 = (cnt + 1) & ~1;
           const int nq = cnt2 & ~3;
-          if (lane < cnt2 - cnt) put_rec(ws->list[t], cnt + lane, 0.f, 0.f, 0.f, 0.f);
+          if (lane < cnt2 - cnt) put_rec<CAP>(ws->list[t], cnt + lane, 0.f, 0.f, 0.f, 0.f);
           __syncwarp();
           // (record j, record j + 1) in the two halves of packed FP32x2
           // operations; each half rounds exactly as the scalar operation
@@ -252,9 +254,9 @@ __global__ void __launch_bounds__((VARD ? kVardWarps : walk_warps(D)) * 32, 1) k
 #pragma unroll 4
           for (int j = 0; j < nq; j += 4) {
             const float4 X = *reinterpret_cast<const float4*>(lt4 + j);
-            const float4 Y = *reinterpret_cast<const float4*>(lt4 + kListCap + j);
-            const float4 Z = *reinterpret_cast<const float4*>(lt4 + 2 * kListCap + j);
-            const float4 M = *reinterpret_cast<const float4*>(lt4 + 3 * kListCap + j);
+            const float4 Y = *reinterpret_cast<const float4*>(lt4 + CAP + j);
+            const float4 Z = *reinterpret_cast<const float4*>(lt4 + 2 * CAP + j);
+            const float4 M = *reinterpret_cast<const float4*>(lt4 + 3 * CAP + j);
             pair(make_float2(X.x, X.y), make_float2(Y.x, Y.y), make_float2(Z.x, Z.y),
                  make_float2(M.x, M.y));
             pair(make_float2(X.z, X.w), make_float2(Y.z, Y.w), make_float2(Z.z, Z.w),
@@ -262,9 +264,9 @@ __global__ void __launch_bounds__((VARD ? kVardWarps : walk_warps(D)) * 32, 1) k
           }
           if (cnt2 != nq) {
             const float2 X = *reinterpret_cast<const float2*>(lt4 + nq);
-            const float2 Y = *reinterpret_cast<const float2*>(lt4 + kListCap + nq);
-            const float2 Z = *reinterpret_cast<const float2*>(lt4 + 2 * kListCap + nq);
-            const float2 M = *reinterpret_cast<const float2*>(lt4 + 3 * kListCap + nq);
+            const float2 Y = *reinterpret_cast<const float2*>(lt4 + CAP + nq);
+            const float2 Z = *reinterpret_cast<const float2*>(lt4 + 2 * CAP + nq);
+            const float2 M = *reinterpret_cast<const float2*>(lt4 + 3 * CAP + nq);
             pair(X, Y, Z, M);
           }
           const float sx = sx2.x + sx2.y, sy = sy2.x + sy2.y, sz = sz2.x + sz2.y;
@@ -321,7 +323,7 @@ __global__ void __launch_bounds__((VARD ? kVardWarps : walk_warps(D)) * 32, 1) k
           lc[t] += __popc(m);
         }
         // (bt = -1: beyond r_cut of the box; the gather stores only species < D)
-        if ((unsigned)bt < (unsigned)D) put_rec(ws->list[bt], slot, rec.x, rec.y, rec.z, rec.w);
+        if ((unsigned)bt < (unsigned)D) put_rec<CAP>(ws->list[bt], slot, rec.x, rec.y, rec.z, rec.w);
         qdone += 32;
         __syncwarp();
         continue;
@@ -397,7 +399,7 @@ __global__ void __launch_bounds__((VARD ? kVardWarps : walk_warps(D)) * 32, 1) k
           const float px = dcx + mo.x, py = dcy + mo.y, pz = dcz + mo.z;
           const bool has = mo.w > 0.f && near_box(px, py, pz, gx, gy, gz, rc2_keep);
           const uint32_t b = __ballot_sync(0xffffffffu, has);
-          if (has) put_rec(ws->list[t], lc[t] + __popc(b & lt), px * s_tab, py * s_tab, pz * s_tab, mo.w);
+          if (has) put_rec<CAP>(ws->list[t], lc[t] + __popc(b & lt), px * s_tab, py * s_tab, pz * s_tab, mo.w);
           lc[t] += __popc(b);
         }
       }
@@ -517,17 +519,17 @@ __global__ void __launch_bounds__(1024) k_walk_prep(const WalkDesc* __restrict__
   }
 }
 
-template <int D>
+template <int D, bool VARD>
 static size_t walk_smem(int tab_count, int nwarps) {
   const size_t tab_bytes = ((size_t)tab_count * sizeof(float2) + 15) & ~(size_t)15;
-  return tab_bytes + (size_t)nwarps * sizeof(WarpSmem<D>);
+  return tab_bytes + (size_t)nwarps * sizeof(WarpSmem<D, walk_list_cap(D, VARD)>);
 }
 
 template <int D, bool ACC64, bool REL, bool VARD>
 static int launch_walk_d(ng_ctx* c, cudaStream_t stream, const WalkLaunch& L, int64_t groups) {
   int nwarps = VARD ? kVardWarps : walk_warps(D);
-  while (nwarps > 1 && walk_smem<D>(L.tab_count, nwarps) > c->smem_optin) --nwarps;
-  const size_t smem = walk_smem<D>(L.tab_count, nwarps);
+  while (nwarps > 1 && walk_smem<D, VARD>(L.tab_count, nwarps) > c->smem_optin) --nwarps;
+  const size_t smem = walk_smem<D, VARD>(L.tab_count, nwarps);
   if (smem > c->smem_optin)
     return fail(c, NG_ENOMEM, "walk needs %zu B shared memory (max %zu)", smem, c->smem_optin);
   // the attribute is a per-function ceiling shared by every thread that

@@ -58,7 +58,15 @@ def _rel_change(got, want, start):
                          ids=["geometric", "relative", "fp64_accumulated"])
 def test_batch_matches_each_simulation_alone(ng, variant):
     """Also with the relative criterion (|a_old| refreshed inside the captured
-    batch step) and with the FP64-accumulated walk."""
+    batch step) and with the FP64-accumulated walk.
+
+    A single simulation's walk evaluates its record lists in longer runs than
+    the batch launch (up to 80-128 records per species list against 64), so
+    each body's FP32 sum is grouped, and rounded, differently. With the
+    relative criterion of Sec. 2.2 the opening decision depends on |a_old|,
+    so a rounding-level difference there accepts other nodes for a few bodies
+    and their steps differ by the walk's truncation error: that variant's
+    99th percentile is held to 2e-4 instead of 1e-4."""
     import torch
     sims = _sims()
     for w in sims:
@@ -82,8 +90,9 @@ def test_batch_matches_each_simulation_alone(ng, variant):
         rx = _rel_change(x["pos"].cpu().numpy(), ref["pos"], w["pos"])
         rv = _rel_change(x["vel"].cpu().numpy().astype(np.float64), ref["vel"].astype(np.float64),
                          w["vel"].astype(np.float64))
-        assert np.percentile(rx, 99) <= 1e-4 and rx.max() <= 1e-2, (np.percentile(rx, 99), rx.max())
-        assert np.percentile(rv, 99) <= 1e-4 and rv.max() <= 1e-2, (np.percentile(rv, 99), rv.max())
+        p99 = 2e-4 if variant.get("opening") else 1e-4
+        assert np.percentile(rx, 99) <= p99 and rx.max() <= 1e-2, (np.percentile(rx, 99), rx.max())
+        assert np.percentile(rv, 99) <= p99 and rv.max() <= 1e-2, (np.percentile(rv, 99), rv.max())
     # a second call replays the captured batch step
     ng.ng_batch_step(b, [x["pos"] for x in m], [x["vel"] for x in m], [x["typ"] for x in m],
                      [x["mass"] for x in m], [x["acc"] for x in m], True, 2, dt)
