@@ -456,6 +456,23 @@ def main():
         # bodies have moved on since, so their steps hold more interactions
         pos.copy_(hp["pos"])
         ecount0 = algorithmic()
+        # the host link's rate on these pinned buffers (boxes differ): every
+        # input to the device, then the outputs back (the same values, so the
+        # host state is unchanged)
+        dt_ = dict(pos=pos, vel=vel, typ=typ, mass=mass, acc=acc)
+        link = {}
+        for name, keys, nbytes in (("h2d_gbs", ("pos", "vel", "typ", "mass", "acc"), h2d),
+                                   ("d2h_gbs", ("pos", "vel", "acc"), d2h)):
+            g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            g0.record(stream)
+            for k in keys:
+                if name == "h2d_gbs":
+                    dt_[k].copy_(hp[k], non_blocking=True)
+                else:
+                    hp[k].copy_(dt_[k], non_blocking=True)
+            g1.record(stream)
+            torch.cuda.synchronize()
+            link[name] = round(nbytes / (g0.elapsed_time(g1) / 1e3) / 1e9, 1)
         barrier()
         f0.record(stream)
         for _ in range(ksteps):
@@ -469,7 +486,7 @@ def main():
         ecount, ems = job_totals(0.5 * (ecount0 + algorithmic()), ems, ws)
         e2e = {"value": ecount * ksteps / (ems / 1e3), "unit": "interactions/s",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-               "ms_per_step": ems / ksteps, "interactions_per_step": ecount}
+               "ms_per_step": ems / ksteps, "interactions_per_step": ecount, "host_link": link}
     ref.close()
 
     cpu = None
