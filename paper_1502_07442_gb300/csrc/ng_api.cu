@@ -321,6 +321,14 @@ int reserve(ng_ctx* c, int64_t n) {
   NG_TRY(ensure(c, c->walk_desc, sizeof(WalkDesc)));
   NG_TRY(ensure(c, c->walk_prefix, 4 * sizeof(uint32_t)));
   if (c->p.opening == NG_OPEN_RELATIVE) NG_TRY(ensure(c, c->aold, (size_t)n * sizeof(float)));
+  if (c->p.pm_mesh > 0 && !c->pm_stream) {
+    if (cudaStreamCreateWithFlags(&c->pm_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(c, NG_ECUDA, "PM stream creation failed");
+    }
+  }
   return pm_reserve(c);
 }
 
@@ -405,6 +413,37 @@ int force_stages(ng_ctx* c, float* acc) {
   } else {
     NG_TRY(launch_tree_force(c, acc, false, false));
   }
+  NG_TRY(update_aold(c, acc));
+  return NG_OK;
+}
+
+// The tree stages and the forces of a captured step. The PM stages read only
+// the sorted bodies and their type-major order, and the tree stages write
+// nothing they read, so PM runs on pm_stream beside the octree, monopoles and
+// groups (latency- and FP64-bound launches beside bandwidth-bound ones); the
+// walk, which adds the short-range force to the long-range one, waits for it.
+int tree_force_overlapped(ng_ctx* c, float* acc) {
+  if (c->p.pm_mesh <= 0 || !c->pm_stream) {
+    NG_TRY(tree_stages(c));
+    return force_stages(c, acc);
+  }
+  NG_TRY(type_order(c));
+  NG_CUDA(c, cudaEventRecord(c->ev_fork, c->stream));
+  NG_CUDA(c, cudaStreamWaitEvent(c->pm_stream, c->ev_fork, 0));
+  cudaStream_t main = c->stream;
+  c->stream = c->pm_stream;
+  const int r = pm_force(c, acc, false);
+  c->stream = main;
+  NG_CUDA(c, cudaEventRecord(c->ev_join, c->pm_stream));
+  if (r != NG_OK) {
+    cudaStreamWaitEvent(c->stream, c->ev_join, 0);   // a capture stays joined
+    return r;
+  }
+  NG_TRY(build_octree(c));
+  NG_TRY(reduce_monopoles(c));
+  NG_TRY(build_groups(c));
+  NG_CUDA(c, cudaStreamWaitEvent(c->stream, c->ev_join, 0));
+  NG_TRY(launch_tree_force(c, acc, true, false));
   NG_TRY(update_aold(c, acc));
   return NG_OK;
 }
@@ -631,9 +670,12 @@ int resident_step_once(ng_ctx* c, int64_t n, double dt, bool checked) {
   NG_TRY(launch_kick_drift(c, n, as<float>(c->rvel_alt), as<float>(c->racc), 0.5 * dt, 1,
                            as<double>(c->spos_alt), dt));
   NG_TRY(sort_resident(c, n));
-  if (checked) NG_TRY(tree_checked(c));
-  else NG_TRY(tree_stages(c));
-  NG_TRY(force_stages(c, as<float>(c->racc)));
+  if (checked) {
+    NG_TRY(tree_checked(c));
+    NG_TRY(force_stages(c, as<float>(c->racc)));
+  } else {
+    NG_TRY(tree_force_overlapped(c, as<float>(c->racc)));
+  }
   NG_TRY(launch_kick(c, n, as<float>(c->rvel), as<float>(c->racc), 0.5 * dt));
   return NG_OK;
 }
@@ -696,6 +738,9 @@ int ng_destroy(ng_ctx* c) {
   if (c->step_exec) cudaGraphExecDestroy(c->step_exec);
   if (c->step_exec_b) cudaGraphExecDestroy(c->step_exec_b);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  if (c->pm_stream) cudaStreamDestroy(c->pm_stream);
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
   for (int s = 0; s <= NG_NSTAGES; ++s)
     if (c->stage_ev[s]) cudaEventDestroy(c->stage_ev[s]);
   {

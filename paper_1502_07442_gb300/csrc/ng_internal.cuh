@@ -329,6 +329,10 @@ struct ng_ctx {
 
   // step graph (captured on a private stream, replayed on the caller's)
   cudaStream_t cap_stream = nullptr;
+  // captured steps run the PM stages on pm_stream beside the tree stages
+  // (fork after the type-major order, join before the walk)
+  cudaStream_t pm_stream = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   uint64_t alloc_gen = 0;          // bumped whenever a device buffer is (re)allocated
   uint64_t graph_gen = 0;
   cudaGraphExec_t step_exec = nullptr;
@@ -509,6 +513,7 @@ int build_checked(ng_ctx* c, int64_t n, const double* pos, const uint8_t* type, 
 int tree_checked(ng_ctx* c);                   // tree stages of the sorted bodies, capacity grown
 int tree_stages(ng_ctx* c);
 int force_stages(ng_ctx* c, float* acc);
+int tree_force_overlapped(ng_ctx* c, float* acc);
 int launch_kick(ng_ctx* c, int64_t n, float* vel, const float* acc, double h);
 // nkick (1 or 2) kicks of h, then the drift (one launch, same rounding as the two)
 int launch_kick_drift(ng_ctx* c, int64_t n, float* vel, const float* acc, double h, int nkick,
