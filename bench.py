@@ -460,19 +460,21 @@ def main():
         # input to the device, then the outputs back (the same values, so the
         # host state is unchanged)
         dt_ = dict(pos=pos, vel=vel, typ=typ, mass=mass, acc=acc)
-        link = {}
-        for name, keys, nbytes in (("h2d_gbs", ("pos", "vel", "typ", "mass", "acc"), h2d),
-                                   ("d2h_gbs", ("pos", "vel", "acc"), d2h)):
-            g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            g0.record(stream)
-            for k in keys:
-                if name == "h2d_gbs":
-                    dt_[k].copy_(hp[k], non_blocking=True)
-                else:
-                    hp[k].copy_(dt_[k], non_blocking=True)
-            g1.record(stream)
-            torch.cuda.synchronize()
-            link[name] = round(nbytes / (g0.elapsed_time(g1) / 1e3) / 1e9, 1)
+        link = {"h2d_gbs": 0.0, "d2h_gbs": 0.0}
+        for _ in range(3):                                     # best of three passes
+            for name, keys, nbytes in (("h2d_gbs", ("pos", "vel", "typ", "mass", "acc"), h2d),
+                                       ("d2h_gbs", ("pos", "vel", "acc"), d2h)):
+                g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                g0.record(stream)
+                for k in keys:
+                    if name == "h2d_gbs":
+                        dt_[k].copy_(hp[k], non_blocking=True)
+                    else:
+                        hp[k].copy_(dt_[k], non_blocking=True)
+                g1.record(stream)
+                torch.cuda.synchronize()
+                rate = round(nbytes / (g0.elapsed_time(g1) / 1e3) / 1e9, 1)
+                link[name] = max(link[name], rate)
         barrier()
         f0.record(stream)
         for _ in range(ksteps):
