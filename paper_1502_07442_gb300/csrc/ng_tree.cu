@@ -415,7 +415,7 @@ __device__ __forceinline__ void mono_node(int lvl, uint32_t k, const MonoArgs& a
       const uint32_t ch = c0 + j;
 #pragma unroll
       for (int q = 0; q < D; ++q) {
-        const double4 v = *reinterpret_cast<const double4*>(a.m64 + ((size_t)ch * D + q) * 4);
+        const double4_32a v = *reinterpret_cast<const double4_32a*>(a.m64 + ((size_t)ch * D + q) * 4);
         sm[q] += v.x;
         sx[q] += v.y;
         sy[q] += v.z;
@@ -427,7 +427,9 @@ __device__ __forceinline__ void mono_node(int lvl, uint32_t k, const MonoArgs& a
   double mt = 0, xt = 0, yt = 0, zt = 0;
 #pragma unroll
   for (int q = 0; q < D; ++q) {
-    *reinterpret_cast<double4*>(a.m64 + ((size_t)k * D + q) * 4) = make_double4(sm[q], sx[q], sy[q], sz[q]);
+    // 32-byte records from a cudaMalloc base: one aligned 32-byte access each
+    *reinterpret_cast<double4_32a*>(a.m64 + ((size_t)k * D + q) * 4) =
+        make_double4_32a(sm[q], sx[q], sy[q], sz[q]);
     a.cnt[(size_t)k * D + q] = sc[q];
     float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
     if (sm[q] > 0.0) {
