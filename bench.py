@@ -110,8 +110,8 @@ def walk_traffic(workload, n_override, leaf, cell):
 
 
 def measured_peaks():
-    """Measured peaks (MEASURED_PEAKS.json beside this file), else the
-    profiling recipe's fallback copy bandwidth."""
+    """Measured peaks of this GPU model (MEASURED_PEAKS.json beside this
+    file), else a copy bandwidth measured earlier on the same model."""
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
             m = json.load(fh)
